@@ -1,0 +1,97 @@
+"""Angular collision kernels b(cos theta) and their constants.  Oracle: test infrastructure.
+
+All kernels are described by g(theta) = sin(theta) b(cos theta) on (0, pi].
+
+* ``family`` (parameter s in [0, 1)): g = c_s sin^(-1-2s)(theta/2), so that
+  g ~ theta^(-1-nu) with nu = 2s (Sec. 2.1, eq. bb).  c_s is fixed by
+  lambda = 1/6 (Sec. 5.1, eq. KK3), lambda = (pi/2) int_0^pi sin^2(theta) g dtheta,
+  which gives c_s = 1 / (12 pi B(1-s, 3/2)).  s = 0 is the paper's b6 and
+  s = 1/2 its b7 (eqs. b6, b7).
+* ``b5``: the cutoff kernel b = 1/(4 pi) (eq. b5).
+* ``b8``: b = 5 cos(theta/2) / (192 pi sin(theta) sin^(5/2)(theta/2)) (eq. b8).
+
+Part I of the split of Sec. 4.1 needs three moments over [0, eps]:
+A1 = int g (1 - cos), A2 = int g (1 - cos)^2, A3 = int g sin^2.
+They are evaluated exactly (power series in sin(eps/2) or closed forms).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+
+def beta_fn(a: float, b: float) -> float:
+    return math.exp(math.lgamma(a) + math.lgamma(b) - math.lgamma(a + b))
+
+
+@dataclass(frozen=True)
+class Kernel:
+    name: str          # "family", "b5", "b8"
+    s: float = 0.0     # family parameter (nu = 2 s)
+
+    @property
+    def c(self) -> float:
+        if self.name == "family":
+            return 1.0 / (12.0 * math.pi * beta_fn(1.0 - self.s, 1.5))
+        if self.name == "b5":
+            return 1.0 / (4.0 * math.pi)
+        if self.name == "b8":
+            return 5.0 / (192.0 * math.pi)
+        raise ValueError(self.name)
+
+    @property
+    def kid(self) -> int:
+        return {"family": 0, "b5": 1, "b8": 2}[self.name]
+
+    def g(self, theta):
+        """sin(theta) * b(cos theta)."""
+        import numpy as np
+        th = np.asarray(theta, dtype=np.float64)
+        h = np.sin(0.5 * th)
+        if self.name == "family":
+            return self.c * h ** (-1.0 - 2.0 * self.s)
+        if self.name == "b5":
+            return self.c * np.sin(th)
+        return self.c * np.cos(0.5 * th) * h ** (-2.5)
+
+    def taylor_moments(self, eps: float):
+        """(A1, A2, A3) over [0, eps] (Sec. 4.1, part I after Taylor expansion)."""
+        W = math.sin(0.5 * eps)
+        if self.name == "family":
+            def int_sin_pow(alpha):
+                # int_0^eps sin^alpha(theta/2) dtheta = 2 int_0^asin(W) sin^alpha u du
+                #   = 2 sum_n binom(2n, n) 4^-n W^(alpha + 2n + 1) / (alpha + 2n + 1)
+                tot, coef, n = 0.0, 1.0, 0
+                while True:
+                    term = coef * W ** (alpha + 2 * n + 1) / (alpha + 2 * n + 1)
+                    tot += term
+                    if abs(term) < 1e-30 * abs(tot) or n > 60:
+                        break
+                    n += 1
+                    coef *= (2 * n - 1) / (2 * n)
+                return 2.0 * tot
+            c = self.c
+            A1 = 2.0 * c * int_sin_pow(1.0 - 2.0 * self.s)
+            A2 = 4.0 * c * int_sin_pow(3.0 - 2.0 * self.s)
+        elif self.name == "b5":
+            omc = 2.0 * W * W  # 1 - cos(eps)
+            A1 = self.c * omc ** 2 / 2.0
+            A2 = self.c * omc ** 3 / 3.0
+        else:
+            K = self.c
+            A1 = 8.0 * K * W ** 0.5
+            A2 = 8.0 * K * 0.4 * W ** 2.5
+        A3 = 2.0 * A1 - A2  # sin^2 = 2 (1 - cos) - (1 - cos)^2
+        return A1, A2, A3
+
+    def lam(self) -> float:
+        """lambda = (1/4) int_S2 (1 - (sigma.qhat)^2) b dsigma (Sec. 5.1) by closed form."""
+        if self.name == "family":
+            return 2.0 * math.pi * self.c * beta_fn(1.0 - self.s, 1.5)
+        if self.name == "b5":
+            return (math.pi / 2.0) * self.c * 4.0 / 3.0
+        return 2.0 * math.pi * self.c * beta_fn(0.25, 2.0)
+
+
+def kernel_from(name: str, s: float = 0.0) -> Kernel:
+    return Kernel(name, float(s))
