@@ -1,0 +1,136 @@
+/*
+ * bz -- fast Fourier spectral evaluation of the non-cutoff Boltzmann collision
+ * operator (Hu & Qi, arXiv 2004.11239) on one NVIDIA GB300 (sm_103a).
+ *
+ * C ABI.  Plain pointers and sizes only.  Every function returns a bz_status;
+ * nothing is thrown or printed.  Device pointers are CUDA device addresses on the
+ * plan's device (for example torch.Tensor.data_ptr()); `stream` is a cudaStream_t
+ * passed as void* (NULL = the legacy default stream).  Calls are asynchronous on
+ * `stream` unless stated otherwise.  A plan is not re-entrant: do not run two calls
+ * on one plan concurrently on different streams.
+ *
+ * Data layout.  A Fourier coefficient array (fhat, Qhat) holds N^3 complex values,
+ * C-order [k1][k2][k3], FFT-natural index order: array index i along an axis is
+ * the signed mode k = i for i < N/2 and k = i - N otherwise (the modes are
+ * -N/2 .. N/2-1; Sec. 2 writes -N/2..N/2, read here as N modes).  The coefficients
+ * follow Sec. 2: f_N(v) = sum_k fhat_k exp(i pi k.v / L) on [-L, L]^3.
+ * dtype BZ_C64 = interleaved float (re, im); BZ_C128 = interleaved double.
+ *
+ * The operator (Sec. 4, eqs. GG1, approxG, realQ; terms p = i*M + j):
+ *   Qhat_k = sum_p c_p F(k, r_i, qhat_j) sum_{l+m=k (mod N)} fhat_l beta_p(m) fhat_m,
+ *   c_p = w_i w_j r_i^gamma r_i^2,  beta_p(m) = exp(-i pi r_i m.qhat_j / L),
+ *   F(k,r,qhat) = int_{S^2} b(sigma.qhat) (exp(i pi r k.(qhat - sigma)/(2L)) - 1) dsigma
+ *   (Sec. 2.1, eq. FF), computed by the split of Sec. 4.1 (Taylor part on [0, eps],
+ *   quadrature on [eps, pi], exact phi integral).  The inner sum is the circular
+ *   convolution computed by one inverse 3D FFT of beta_p fhat, a product with
+ *   h = IFFT(fhat), and one forward 3D FFT per term (Sec. 4: "a few FFTs").
+ */
+#ifndef BZ_H
+#define BZ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BZ_OK = 0,
+    BZ_ERR_ARG = 1,          /* invalid argument (sizes, pointers, aliasing)          */
+    BZ_ERR_OOM = 2,          /* device or host allocation failed                      */
+    BZ_ERR_CUDA = 3,         /* a CUDA runtime call failed                            */
+    BZ_ERR_TIMEOUT = 4,      /* a bounded device or host wait ran out                 */
+    BZ_ERR_NONFINITE = 5,    /* NaN or Inf detected in a result                       */
+    BZ_ERR_BUSY = 6,         /* not admissible now / result not ready yet             */
+    BZ_ERR_UNSUPPORTED = 7   /* parameter combination not implemented                 */
+} bz_status;
+
+enum { BZ_C64 = 0, BZ_C128 = 1 };
+
+/* Angular kernels, given by g(theta) = sin(theta) b(cos theta):
+ *   BZ_KERNEL_FAMILY: g = c_s sin^(-1-2s)(theta/2), 0 <= s < 1 (singularity theta^(-1-nu),
+ *                     nu = 2s, Sec. 2.1 eq. bb); c_s = 1/(12 pi B(1-s, 3/2)) so that
+ *                     lambda = 1/6 (Sec. 5.1).  s = 0 is eq. b6, s = 1/2 is eq. b7.
+ *   BZ_KERNEL_B5:     b = 1/(4 pi), the cutoff kernel of eq. b5.
+ *   BZ_KERNEL_B8:     b = 5 cos(theta/2) / (192 pi sin(theta) sin^(5/2)(theta/2)), eq. b8. */
+enum { BZ_KERNEL_FAMILY = 0, BZ_KERNEL_B5 = 1, BZ_KERNEL_B8 = 2 };
+
+enum { BZ_PREC_FP32 = 0 };
+
+typedef struct bz_plan bz_plan;
+
+typedef struct {
+    int N;            /* modes per axis: 8, 16, 24, 32, 48 or 64                      */
+    double L;         /* half-width of the periodic box [-L, L]^3 (Sec. 2)             */
+    double R;         /* radius of the |q| ball, radial rule on [0, R] (Sec. 2, 4)     */
+    double gamma;     /* Phi(|q|) = |q|^gamma (Sec. 1, eq. Bb)                        */
+    double s;         /* BZ_KERNEL_FAMILY order, nu = 2 s                              */
+    int N_rho;        /* Gauss-Legendre points in |q| (Sec. 4)                         */
+    int M;            /* sphere points: 12 = icosahedron; 2n^2 or n^2 = product rule    */
+    int kernel;       /* BZ_KERNEL_*                                                   */
+    int precision;    /* BZ_PREC_FP32                                                  */
+    double eps;       /* Taylor/quadrature split angle; <= 0 selects pi/1000 (Sec. 4.1) */
+    const double *sphere_xyz;  /* optional host array [M][3] of unit vectors, or NULL  */
+    const double *sphere_w;    /* optional host array [M] of weights (sum 4 pi)         */
+    int chunk_terms;  /* terms per pipeline chunk; <= 0 selects automatically          */
+} bz_plan_desc;
+
+/* Creates a plan: quadrature terms, the FP64 F table (computed on the device, stored
+ * FP32 as alpha_p = c_p F / N^3), twiddle vectors and workspace, on the current CUDA
+ * device.  Synchronous.  Sec. 4, eq. approxG; Sec. 4.1.
+ * Errors: BZ_ERR_ARG for unsupported N, N_rho < 1, s outside [0, 1), a sphere rule
+ * that does not exist for M; BZ_ERR_OOM; BZ_ERR_CUDA.  *out is NULL on error. */
+bz_status bz_plan_create(bz_plan **out, int N, double L, double R, double gamma,
+                         double s, int N_rho, int M);
+bz_status bz_plan_create_ex(bz_plan **out, const bz_plan_desc *desc);
+void bz_plan_destroy(bz_plan *plan);
+
+/* Number of quadrature terms P = N_rho * M; bytes of the alpha table. */
+bz_status bz_plan_info(const bz_plan *plan, int *P, size_t *alpha_bytes, size_t *workspace_bytes);
+
+/* Copies the term list to host arrays of length P (any may be NULL):
+ * r[p], w_r[p], qhat[3p..3p+2], w_q[p], c[p] = w_r w_q r^(gamma+2).  Synchronous. */
+bz_status bz_plan_terms(const bz_plan *plan, double *r, double *w_r, double *qhat,
+                        double *w_q, double *c);
+
+/* Qhat = Q(fhat, fhat) over all terms (eq. realQ).  fhat and Qhat are device arrays
+ * of N^3 complex values of the given dtype; fhat != Qhat (BZ_ERR_ARG otherwise).
+ * Arithmetic: FP32 FFTs and products, FP64 accumulation over terms. */
+bz_status bz_collide(bz_plan *plan, const void *fhat, void *Qhat, int dtype, void *stream);
+
+/* As bz_collide, restricted to terms p0 <= p < p1 (0 <= p0 <= p1 <= P). */
+bz_status bz_collide_terms(bz_plan *plan, int p0, int p1, const void *fhat, void *Qhat,
+                           int dtype, void *stream);
+
+/* Classical RK4 (Sec. 5.2) for d fhat/dt = Q(fhat, fhat): nsteps steps of size dt,
+ * fhat updated in place (device, dtype), *t advanced by nsteps*dt on the host.
+ * The stage state is FP32.  workspace may be NULL (the plan's own is used). */
+bz_status bz_step_rk(bz_plan *plan, void *fhat, int dtype, double *t, double dt, int nsteps,
+                     void *workspace, void *stream);
+
+/* Moments of f_N over [-L, L]^3 in FP64: out[0] = mass = (2L)^3 Re fhat_0 (Sec. 4 remark),
+ * out[1..3] = momentum, out[4] = energy int |v|^2 f_N dv (exact integrals of the
+ * trigonometric basis).  out is a host array of 5 doubles; synchronous on stream. */
+bz_status bz_moments(bz_plan *plan, const void *fhat, int dtype, double out[5], void *stream);
+
+/* F(k, r_i, qhat_j) in FP64 for `count` entries (device arrays): k_idx[3e..3e+2] array
+ * indices in [0, N), term[e] in [0, P); out[2e], out[2e+1] = re, im.  Uses the same
+ * device code as the plan's table (before the FP32 store).  Synchronous. */
+bz_status bz_ftable_entries(bz_plan *plan, int count, const int *k_idx, const int *term,
+                            double *out);
+
+/* Copies alpha_p (FP32 complex, c_p F / N^3) for terms p0 <= p < p1 into the device array
+ * dst ((p1-p0) * N^3 complex64). */
+bz_status bz_plan_alpha(const bz_plan *plan, int p0, int p1, void *dst, void *stream);
+
+const char *bz_status_str(bz_status s);
+
+/* Number of kernel launches issued by the last bz_collide / bz_collide_terms /
+ * bz_step_rk call on this plan. */
+int bz_plan_last_launches(const bz_plan *plan);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BZ_H */

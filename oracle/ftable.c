@@ -18,7 +18,8 @@
  *           I = 2 pi [ i x A1 - x^2 A2 / 2 - y^2 A3 / 4 ].
  *   part II (t in [eps, pi]): 2 pi int g [exp(i x (1-cos t)) J0(y sin t) - 1] dt
  *           by composite Gauss-Legendre: panels [eps 2^j, eps 2^(j+1)] up to 0.5,
- *           then equal panels of width <= min(0.5, 6 / z) with z = a |k|_max.
+ *           then equal panels up to pi; every panel is at most min(0.5, 6 / z)
+ *           wide, z = a |k|_max (graded panels are split to meet that).
  *           (The paper uses an adaptive quadrature here; any rule converged to
  *           rounding gives the same table.)
  *
@@ -57,17 +58,22 @@ static int part2_rule(double eps, double zmax, int npts, const double *glx, cons
     int n = 0;
     double lo = eps;
     const double tg = 0.5;
+    double width = fmin(0.5, 6.0 / fmax(zmax, 1e-300));
     while (lo < tg) {
         double hi = fmin(2.0 * lo, tg);
-        for (int q = 0; q < npts && n < cap; ++q) {
-            double t = 0.5 * (hi - lo) * glx[q] + 0.5 * (hi + lo);
-            th[n] = t;
-            wg[n] = 0.5 * (hi - lo) * glw[q] * kernel_g(t, kid, s, c);
-            n++;
+        int nsub = (int)ceil((hi - lo) / width);   /* keep each panel within the oscillation limit */
+        double dsub = (hi - lo) / nsub;
+        for (int sp = 0; sp < nsub; ++sp) {
+            double a = lo + sp * dsub, b = lo + (sp + 1) * dsub;
+            for (int q = 0; q < npts && n < cap; ++q) {
+                double t = 0.5 * (b - a) * glx[q] + 0.5 * (b + a);
+                th[n] = t;
+                wg[n] = 0.5 * (b - a) * glw[q] * kernel_g(t, kid, s, c);
+                n++;
+            }
         }
         lo = hi;
     }
-    double width = fmin(0.5, 6.0 / fmax(zmax, 1e-300));
     int npan = (int)ceil((M_PI - tg) / width);
     double dw = (M_PI - tg) / npan;
     for (int pn = 0; pn < npan; ++pn) {
@@ -79,6 +85,7 @@ static int part2_rule(double eps, double zmax, int npts, const double *glx, cons
             n++;
         }
     }
+    if (n >= cap) return -1;   /* rule does not fit: report instead of truncating */
     for (int q = 0; q < n; ++q) {
         double h = sin(0.5 * th[q]);
         cth[q] = 2.0 * h * h;  /* 1 - cos(t) */
@@ -122,6 +129,7 @@ int oracle_ftable(int N, double L, int P, const double *r, const double *qhat,
         double *wg = th + RULE_CAP, *cth = th + 2 * RULE_CAP, *sth = th + 3 * RULE_CAP;
         double a = M_PI * r[p] / (2.0 * L);
         int n = part2_rule(eps, a * kmax, npts, glx, glw, kid, s, c, th, wg, cth, sth, RULE_CAP);
+        if (n < 0) { err = 1; free(th); continue; }
         const double *qh = qhat + 3 * p;
         int k1 = i1 < N / 2 ? i1 : i1 - N;
         for (int i2 = 0; i2 < N; ++i2) {
@@ -154,6 +162,7 @@ int oracle_fentries(int count, const int *k, const double *r, const double *qhat
         double *wg = th + RULE_CAP, *cth = th + 2 * RULE_CAP, *sth = th + 3 * RULE_CAP;
         double a = M_PI * r[e] / (2.0 * L);
         int n = part2_rule(eps, a * kmax, npts, glx, glw, kid, s, c, th, wg, cth, sth, RULE_CAP);
+        if (n < 0) { err = 1; free(th); continue; }
         const double *qh = qhat + 3 * e;
         const int *kk = k + 3 * e;
         double kap = kk[0] * qh[0] + kk[1] * qh[1] + kk[2] * qh[2];
