@@ -1,0 +1,335 @@
+"""Throughput of the collision operator on one GB300: Q(f,f) evaluations per second.
+
+Workload (default "rk4_n32"): the RK4 relaxation of the BKW solution, N = 32, N_rho = 32,
+M = 32 (product sphere rule), gamma = 0, s = 0.5 (nu = 1), R = 6, L = (3 + sqrt 2) R / 4,
+dt = 0.01, starting at t = 6.5.  One step = one RK4 step = 4 collides (P = 1024 terms each).
+Inputs stay in HBM; the alpha table (268 MB) is larger than L2, so every collide streams it.
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle on the host
+cores on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (N, N_rho, M, gamma, s, R, dt, description)
+    "rk4_n32": dict(N=32, N_rho=32, M=32, gamma=0.0, s=0.5, R=6.0, dt=0.01, t0=6.5,
+                    data="bkw", desc="RK4 step of the BKW solution, N=32, N_rho=32, M=32, "
+                                     "gamma=0, s=0.5, R=6, L=(3+sqrt2)R/4, dt=0.01, t0=6.5"),
+    "single_n64": dict(N=64, N_rho=64, M=64, gamma=-1.0, s=0.5, R=None, L=10.0, dt=None,
+                       data="c3", desc="single collide, N=64, N_rho=64, M=64, gamma=-1, s=0.5, "
+                                       "L=10, bi-Gaussian plus 1% noise"),
+    "single_n16": dict(N=16, N_rho=16, M=12, gamma=0.0, s=0.5, R=None, L=10.0, dt=None,
+                       data="c1", desc="single collide, N=16, N_rho=16, M=12, gamma=0, s=0.5, "
+                                       "L=10, two Maxwellians at +-2 e1"),
+}
+METRIC = "Q(f,f) evals/s"
+
+
+def _geometry(w):
+    import bz_inputs as bi
+    if w.get("R") is not None:
+        R = w["R"]
+        L = bi.L_from_R(R)
+    else:
+        L = w["L"]
+        R = bi.R_from_L(L)
+    return L, R
+
+
+def _fhat(w, L):
+    import bz_inputs as bi
+    N = w["N"]
+    if w["data"] == "bkw":
+        return bi.bkw_fhat(N, L, bi.bkw_K(w["t0"]))
+    if w["data"] == "c3":
+        return bi.bigaussian_noise_c3(N, L)
+    return bi.two_maxwellians_c1(N, L)
+
+
+def _flops_per_term(N):
+    """Algorithmic FP32 flops of one term: 2 3D FFTs (5 n log2 n, n = N^3), the twiddle,
+    product and weight multiplies (6 flops each per mode) and the accumulation (2)."""
+    n = N ** 3
+    return {"plane_inv": 10 * n * math.log2(N) + 6 * n,
+            "pencil": 10 * n * math.log2(N) + 6 * n,
+            "plane_fwd": 10 * n * math.log2(N) + 6 * n,
+            "reduce": 2 * n}
+
+
+def _bytes_per_term(N):
+    """Algorithmic bytes per term moved by each kernel (complex64 = 8 B per mode)."""
+    n = N ** 3
+    return {"plane_inv": 2 * 8 * n,      # read fhat, write S
+            "pencil": 3 * 8 * n,         # read S, read h, write S
+            "plane_fwd": 3 * 8 * n,      # read S, read alpha, write S
+            "reduce": 8 * n}             # read S
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples every 200 ms during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        if self.path and os.path.exists(self.path):
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) >= 9:
+                    rows.append(f)
+            os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_oracle_sample(w, L, R, n_terms=16, reps=1):
+    """Times the FP64 oracle on `n_terms` terms of one collide; returns seconds per full collide."""
+    import numpy as np
+    from oracle import kernels, spectral
+    N, P = w["N"], w["N_rho"] * w["M"]
+    sel = np.linspace(0, P - 1, n_terms).astype(int)
+    plan = spectral.OraclePlan(N, L, R, w["gamma"], kernels.Kernel("family", w["s"]), w["N_rho"],
+                               w["M"], terms=sel)
+    f = _fhat(w, L)
+    best = float("inf")
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        h = spectral.dft3(f, +1)
+        for p in sel:
+            g = spectral.dft3(f * plan.beta(p), +1)
+            U = spectral.dft3(h * g, -1) / N ** 3
+            _ = plan.alpha(p) * U
+        best = min(best, time.perf_counter() - t0)
+    return best * P / n_terms
+
+
+def run_reference(args, w):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    L, R = _geometry(w)
+    cpu_oracle_sample(w, L, R, n_terms=2)       # builds the oracle library, warms up
+    times = []
+    for i in range(args.warmup + args.steps):
+        t = cpu_oracle_sample(w, L, R, n_terms=8)
+        if i >= args.warmup:
+            times.append(t)
+    sec_per_collide = statistics.median(times)
+    value = 1.0 / sec_per_collide
+    sample = f"8 of {w['N_rho'] * w['M']} terms of one N={w['N']} collide per step, extrapolated"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "evals/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sec_per_collide * (4 if w["dt"] else 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload, "desc": w["desc"]},
+            "cpu_baseline": {"value": value, "unit": "evals/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args, w):
+    import numpy as np
+    import torch
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import paper_2004_11239_gb300 as bz
+
+    L, R = _geometry(w)
+    N = w["N"]
+    plan = bz.bz_plan_create(N, L, R, w["gamma"], w["s"], w["N_rho"], w["M"])
+    f_host = _fhat(w, L)
+    f = torch.from_numpy(f_host).to("cuda")
+    q = torch.empty_like(f)
+    st = torch.cuda.current_stream()
+    is_rk = w["dt"] is not None
+    evals_per_step = 4 if is_rk else 1
+
+    def step():
+        if is_rk:
+            bz.bz_step_rk(plan, f, 0.0, w["dt"], 1, st)
+        else:
+            bz.bz_collide(plan, f, q, st)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    launches_per_step = bz.bz_plan_last_launches(plan)
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    # timed region: K steps, per-kernel events recorded by the library
+    bz.bz_plan_set_timing(plan, launches_per_step * args.steps + 16)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        e0.record(st)
+        for _ in range(args.steps):
+            step()
+        e1.record(st)
+        torch.cuda.synchronize()
+        barrier()
+    ms = e0.elapsed_time(e1)
+    kern = {name: bz.bz_plan_timing(plan, kind) for name, kind in bz.KERNEL_KINDS.items()}
+    bz.bz_plan_set_timing(plan, 0)
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = evals_per_step * args.steps * ws / (ms / 1e3)
+
+    # end to end through the public API with host buffers (pinned), copies inside the region
+    h_in = torch.from_numpy(f_host).pin_memory()
+    h_out = torch.empty_like(h_in).pin_memory()
+    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e2.record(st)
+    for _ in range(args.steps):
+        f.copy_(h_in, non_blocking=True)
+        step()
+        h_out.copy_(f if is_rk else q, non_blocking=True)
+    e3.record(st)
+    torch.cuda.synchronize()
+    ms_e2e = e2.elapsed_time(e3)
+    nbytes = f.numel() * f.element_size()
+    e2e = {"value": evals_per_step * args.steps * ws / (ms_e2e / 1e3), "unit": "evals/s",
+           "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+
+    # roofline of the dominant kernel
+    peaks, src = _peaks()
+    dom = max(("plane_inv", "pencil", "plane_fwd", "reduce"), key=lambda k: kern[k][1])
+    n_launch, ms_k = kern[dom]
+    terms_per_launch = (w["N_rho"] * w["M"]) * evals_per_step * args.steps / max(n_launch, 1)
+    avg_s = ms_k / 1e3 / max(n_launch, 1)
+    fl = _flops_per_term(N)[dom] * terms_per_launch
+    by = _bytes_per_term(N)[dom] * terms_per_launch
+    clocks = clk.summary()
+    sm_clock = peaks.get("sm_max_mhz", 2070.0)
+    alu_peak = 152 * 128 * 2 * sm_clock * 1e6 / 1e12      # FP32 FMA lanes x 2 flops x clock
+    alu = {"bound": "alu", "achieved": fl / avg_s / 1e12, "peak": alu_peak, "unit": "TFLOP/s"}
+    hbm = {"bound": "hbm", "achieved": by / avg_s / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
+    for r in (alu, hbm):
+        r["frac"] = r["achieved"] / r["peak"]
+    roof = max((alu, hbm), key=lambda r: r["frac"])
+    other = hbm if roof is alu else alu
+    roof.update({"kernel": dom, "traffic": None, "peak_source": f"{src}" if roof is hbm else
+                 "derived: 152 SMs x 128 FP32 lanes x 2 x sm_max_mhz", "launches": n_launch,
+                 "avg_launch_us": avg_s * 1e6, "also": {k: other[k] for k in ("bound", "achieved", "peak", "unit", "frac")}})
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        P = w["N_rho"] * w["M"]
+        per_term = cpu_oracle_sample(w, L, R, n_terms=2) / P
+        n_terms = int(max(4, min(P, 15.0 / max(per_term, 1e-6))))   # about 15 s of oracle work
+        sec = cpu_oracle_sample(w, L, R, n_terms=n_terms)
+        cpu = {"value": 1.0 / sec, "unit": "evals/s", "cores": 1, "kind": "oracle",
+               "sample": f"{n_terms} of {P} terms of one collide (FP64 oracle, one thread), "
+                         "extrapolated to all terms; F-table build excluded"}
+
+    line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": w["desc"], "P": w["N_rho"] * w["M"],
+                       "collides_per_step": evals_per_step,
+                       "l2": "inputs larger than L2: the alpha table of %d MB streams every collide"
+                             % (plan.alpha_bytes >> 20)},
+            "clocks": clocks, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
+            "roofline": roof, "kernels_ms": {k: v[1] for k, v in kern.items()},
+            "cpu_baseline": cpu}
+    if rank == 0:
+        print(json.dumps(line))
+    plan.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="rk4_n32", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, w)
+    return run_ours(args, w)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -104,8 +104,10 @@ bz_status bz_collide_terms(bz_plan *plan, int p0, int p1, const void *fhat, void
                            int dtype, void *stream);
 
 /* Classical RK4 (Sec. 5.2) for d fhat/dt = Q(fhat, fhat): nsteps steps of size dt,
- * fhat updated in place (device, dtype), *t advanced by nsteps*dt on the host.
- * The stage state is FP32.  workspace may be NULL (the plan's own is used). */
+ * fhat updated in place (device, dtype), *t (host, may be NULL) advanced by nsteps*dt.
+ * The step state and the stage combination are FP64 on the device; each stage's
+ * collide input is rounded to FP32.  workspace is reserved and may be NULL (the
+ * plan's own workspace is used). */
 bz_status bz_step_rk(bz_plan *plan, void *fhat, int dtype, double *t, double dt, int nsteps,
                      void *workspace, void *stream);
 
@@ -125,6 +127,19 @@ bz_status bz_ftable_entries(bz_plan *plan, int count, const int *k_idx, const in
 bz_status bz_plan_alpha(const bz_plan *plan, int p0, int p1, void *dst, void *stream);
 
 const char *bz_status_str(bz_status s);
+
+/* Kernel kinds reported by bz_plan_timing. */
+enum { BZ_K_PLANE_INV = 0, BZ_K_PENCIL = 1, BZ_K_PLANE_FWD = 2, BZ_K_REDUCE = 3, BZ_K_OTHER = 4 };
+
+/* Per-kernel timing.  With max_launches > 0, the next max_launches pipeline launches of
+ * this plan are each bracketed by a pair of CUDA events recorded on the launch stream
+ * (events are created here, not during the launches); 0 turns timing off.  Resets the
+ * totals.  Launches beyond max_launches are not timed. */
+bz_status bz_plan_set_timing(bz_plan *plan, int max_launches);
+
+/* Totals since bz_plan_set_timing for one kernel kind: number of timed launches and
+ * their summed device time in milliseconds.  Waits for the recorded events. */
+bz_status bz_plan_timing(bz_plan *plan, int kind, long *launches, double *ms);
 
 /* Number of kernel launches issued by the last bz_collide / bz_collide_terms /
  * bz_step_rk call on this plan. */

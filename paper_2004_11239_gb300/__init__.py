@@ -1,0 +1,269 @@
+"""Python binding of libbz (include/bz.h): argument marshalling only.
+
+Every computation runs in the CUDA library; importing this module raises if the
+built library is missing.  Device arrays are torch tensors (complex64 or
+complex128, contiguous, on the plan's device); streams are torch.cuda.Stream
+objects (None = the current stream).
+
+Functions mirror the C names: bz_plan_create, bz_plan_create_ex, bz_plan_destroy,
+bz_plan_info, bz_plan_terms, bz_collide, bz_collide_terms, bz_step_rk, bz_moments,
+bz_ftable_entries, bz_plan_alpha, bz_plan_last_launches, bz_status_str.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+__all__ = [
+    "BZ_C64", "BZ_C128", "BZ_KERNEL_FAMILY", "BZ_KERNEL_B5", "BZ_KERNEL_B8", "BzError",
+    "bz_plan_create", "bz_plan_create_ex", "bz_plan_destroy", "bz_plan_info", "bz_plan_terms",
+    "bz_collide", "bz_collide_terms", "bz_step_rk", "bz_moments", "bz_ftable_entries",
+    "bz_plan_alpha", "bz_plan_last_launches", "bz_status_str", "library_path", "lib",
+    "bz_plan_set_timing", "bz_plan_timing",
+]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "_lib", "libbz.so")
+
+BZ_C64, BZ_C128 = 0, 1
+BZ_KERNEL_FAMILY, BZ_KERNEL_B5, BZ_KERNEL_B8 = 0, 1, 2
+BZ_PREC_FP32 = 0
+_STATUS = {0: "BZ_OK", 1: "BZ_ERR_ARG", 2: "BZ_ERR_OOM", 3: "BZ_ERR_CUDA", 4: "BZ_ERR_TIMEOUT",
+           5: "BZ_ERR_NONFINITE", 6: "BZ_ERR_BUSY", 7: "BZ_ERR_UNSUPPORTED"}
+
+
+class BzError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {_STATUS.get(code, code)}")
+        self.code = code
+
+
+class bz_plan_desc(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("L", ctypes.c_double), ("R", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("s", ctypes.c_double), ("N_rho", ctypes.c_int),
+                ("M", ctypes.c_int), ("kernel", ctypes.c_int), ("precision", ctypes.c_int),
+                ("eps", ctypes.c_double), ("sphere_xyz", ctypes.POINTER(ctypes.c_double)),
+                ("sphere_w", ctypes.POINTER(ctypes.c_double)), ("chunk_terms", ctypes.c_int)]
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def _load():
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(f"libbz.so is not built ({_LIB_PATH}); run __graft_entry__.build()")
+    L = ctypes.CDLL(_LIB_PATH)
+    vp, ip, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)
+    c_int, c_double, c_size = ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    sig = {
+        "bz_plan_create": [ctypes.POINTER(vp), c_int, c_double, c_double, c_double, c_double, c_int, c_int],
+        "bz_plan_create_ex": [ctypes.POINTER(vp), ctypes.POINTER(bz_plan_desc)],
+        "bz_plan_info": [vp, ip, ctypes.POINTER(c_size), ctypes.POINTER(c_size)],
+        "bz_plan_terms": [vp, dp, dp, dp, dp, dp],
+        "bz_collide": [vp, vp, vp, c_int, vp],
+        "bz_collide_terms": [vp, c_int, c_int, vp, vp, c_int, vp],
+        "bz_step_rk": [vp, vp, c_int, dp, c_double, c_int, vp, vp],
+        "bz_moments": [vp, vp, c_int, dp, vp],
+        "bz_ftable_entries": [vp, c_int, vp, vp, vp],
+        "bz_plan_alpha": [vp, c_int, c_int, vp, vp],
+    }
+    for name, args in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = c_int
+    L.bz_plan_set_timing.argtypes = [vp, c_int]
+    L.bz_plan_set_timing.restype = c_int
+    L.bz_plan_timing.argtypes = [vp, c_int, ctypes.POINTER(ctypes.c_long), dp]
+    L.bz_plan_timing.restype = c_int
+    L.bz_plan_destroy.argtypes = [vp]
+    L.bz_plan_destroy.restype = None
+    L.bz_plan_last_launches.argtypes = [vp]
+    L.bz_plan_last_launches.restype = c_int
+    L.bz_status_str.argtypes = [c_int]
+    L.bz_status_str.restype = ctypes.c_char_p
+    return L
+
+
+lib = _load()
+
+
+def _check(code: int, what: str):
+    if code != 0:
+        raise BzError(code, what)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dtype(t) -> int:
+    import torch
+    if t.dtype == torch.complex64:
+        return BZ_C64
+    if t.dtype == torch.complex128:
+        return BZ_C128
+    raise TypeError(f"unsupported dtype {t.dtype}")
+
+
+def _dev(t, n3: int):
+    if not t.is_cuda or not t.is_contiguous() or t.numel() != n3:
+        raise ValueError("expected a contiguous CUDA tensor of N^3 complex values")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Plan:
+    """Owning handle of a bz_plan (destroyed with the object or by close())."""
+
+    def __init__(self, handle: ctypes.c_void_p, N: int, L: float):
+        self.handle = handle
+        self.N = N
+        self.L = L
+        P = ctypes.c_int()
+        ab = ctypes.c_size_t()
+        wb = ctypes.c_size_t()
+        _check(lib.bz_plan_info(handle, ctypes.byref(P), ctypes.byref(ab), ctypes.byref(wb)), "bz_plan_info")
+        self.P, self.alpha_bytes, self.workspace_bytes = P.value, ab.value, wb.value
+
+    @property
+    def n3(self) -> int:
+        return self.N ** 3
+
+    def close(self):
+        if self.handle:
+            lib.bz_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def bz_plan_create(N: int, L: float, R: float, gamma: float, s: float, N_rho: int, M: int) -> Plan:
+    h = ctypes.c_void_p()
+    _check(lib.bz_plan_create(ctypes.byref(h), N, L, R, gamma, s, N_rho, M), "bz_plan_create")
+    return Plan(h, N, L)
+
+
+def bz_plan_create_ex(N: int, L: float, R: float, gamma: float, s: float, N_rho: int, M: int,
+                      kernel: int = BZ_KERNEL_FAMILY, eps: float = 0.0, sphere=None,
+                      chunk_terms: int = 0) -> Plan:
+    d = bz_plan_desc()
+    d.N, d.L, d.R, d.gamma, d.s, d.N_rho, d.M = N, L, R, gamma, s, N_rho, M
+    d.kernel, d.precision, d.eps, d.chunk_terms = kernel, BZ_PREC_FP32, eps, chunk_terms
+    keep = []
+    if sphere is not None:
+        import numpy as np
+        xyz = np.ascontiguousarray(sphere[0], dtype=np.float64)
+        w = np.ascontiguousarray(sphere[1], dtype=np.float64)
+        keep += [xyz, w]
+        d.sphere_xyz = xyz.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        d.sphere_w = w.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    h = ctypes.c_void_p()
+    _check(lib.bz_plan_create_ex(ctypes.byref(h), ctypes.byref(d)), "bz_plan_create_ex")
+    return Plan(h, N, L)
+
+
+def bz_plan_destroy(plan: Plan):
+    plan.close()
+
+
+def bz_plan_info(plan: Plan):
+    return plan.P, plan.alpha_bytes, plan.workspace_bytes
+
+
+def bz_plan_terms(plan: Plan):
+    """Returns numpy arrays r, w_r, qhat[P,3], w_q, c."""
+    import numpy as np
+    P = plan.P
+    r, wr, wq, c = (np.empty(P) for _ in range(4))
+    q = np.empty((P, 3))
+    f = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))  # noqa: E731
+    _check(lib.bz_plan_terms(plan.handle, f(r), f(wr), f(q), f(wq), f(c)), "bz_plan_terms")
+    return r, wr, q, wq, c
+
+
+def bz_collide(plan: Plan, fhat, Qhat, stream=None):
+    dt = _dtype(fhat)
+    if _dtype(Qhat) != dt:
+        raise TypeError("fhat and Qhat must have the same dtype")
+    _check(lib.bz_collide(plan.handle, _dev(fhat, plan.n3), _dev(Qhat, plan.n3), dt, _stream(stream)),
+           "bz_collide")
+
+
+def bz_collide_terms(plan: Plan, p0: int, p1: int, fhat, Qhat, stream=None):
+    dt = _dtype(fhat)
+    if _dtype(Qhat) != dt:
+        raise TypeError("fhat and Qhat must have the same dtype")
+    _check(lib.bz_collide_terms(plan.handle, p0, p1, _dev(fhat, plan.n3), _dev(Qhat, plan.n3), dt,
+                                _stream(stream)), "bz_collide_terms")
+
+
+def bz_step_rk(plan: Plan, fhat, t: float, dt: float, nsteps: int, stream=None) -> float:
+    tt = ctypes.c_double(t)
+    _check(lib.bz_step_rk(plan.handle, _dev(fhat, plan.n3), _dtype(fhat), ctypes.byref(tt), dt, nsteps,
+                          None, _stream(stream)), "bz_step_rk")
+    return tt.value
+
+
+def bz_moments(plan: Plan, fhat, stream=None):
+    out = (ctypes.c_double * 5)()
+    _check(lib.bz_moments(plan.handle, _dev(fhat, plan.n3), _dtype(fhat), out, _stream(stream)),
+           "bz_moments")
+    return list(out)
+
+
+def bz_ftable_entries(plan: Plan, k_idx, term):
+    """F in FP64 at device int32 tensors k_idx[E,3] (array indices) and term[E]; returns [E] complex128."""
+    import torch
+    E = term.numel()
+    out = torch.empty(E, dtype=torch.complex128, device=term.device)
+    _check(lib.bz_ftable_entries(plan.handle, E, ctypes.c_void_p(k_idx.data_ptr()),
+                                 ctypes.c_void_p(term.data_ptr()), ctypes.c_void_p(out.data_ptr())),
+           "bz_ftable_entries")
+    return out
+
+
+def bz_plan_alpha(plan: Plan, p0: int, p1: int, stream=None):
+    import torch
+    out = torch.empty((p1 - p0, plan.N, plan.N, plan.N), dtype=torch.complex64, device="cuda")
+    _check(lib.bz_plan_alpha(plan.handle, p0, p1, ctypes.c_void_p(out.data_ptr()), _stream(stream)),
+           "bz_plan_alpha")
+    return out
+
+
+def bz_plan_last_launches(plan: Plan) -> int:
+    return lib.bz_plan_last_launches(plan.handle)
+
+
+BZ_K_PLANE_INV, BZ_K_PENCIL, BZ_K_PLANE_FWD, BZ_K_REDUCE, BZ_K_OTHER = range(5)
+KERNEL_KINDS = {"plane_inv": 0, "pencil": 1, "plane_fwd": 2, "reduce": 3, "other": 4}
+
+
+def bz_plan_set_timing(plan: Plan, max_launches: int):
+    _check(lib.bz_plan_set_timing(plan.handle, max_launches), "bz_plan_set_timing")
+
+
+def bz_plan_timing(plan: Plan, kind: int):
+    """(launches, total milliseconds) for one kernel kind since bz_plan_set_timing."""
+    n = ctypes.c_long()
+    ms = ctypes.c_double()
+    _check(lib.bz_plan_timing(plan.handle, kind, ctypes.byref(n), ctypes.byref(ms)), "bz_plan_timing")
+    return n.value, ms.value
+
+
+def bz_status_str(code: int) -> str:
+    return lib.bz_status_str(code).decode()
+
+
+def default_R(L: float) -> float:
+    """R from L = (3 + sqrt 2) R / 4 (Sec. 2 anti-aliasing bound with R = 2S)."""
+    return 4.0 * L / (3.0 + math.sqrt(2.0))

@@ -1,0 +1,272 @@
+// C ABI of libbz: plan lifetime, collide, RK4, moments and table accessors (include/bz.h).
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "bz_internal.h"
+
+struct bz_plan {
+    bz::Plan p;
+};
+
+namespace {
+
+void free_timing(bz::Plan &p) {
+    for (cudaEvent_t e : p.tm.ev) cudaEventDestroy(e);
+    p.tm.ev.clear();
+    p.tm.kind.clear();
+    p.tm.used = 0;
+    p.tm.on = false;
+}
+
+void free_plan(bz::Plan &p) {
+    free_timing(p);
+    cudaFree(p.alpha); cudaFree(p.tw); cudaFree(p.rule_buf); cudaFree(p.rule_off);
+    cudaFree(p.term_dev); cudaFree(p.S); cudaFree(p.h); cudaFree(p.fin); cudaFree(p.acc);
+    cudaFree(p.rk); cudaFree(p.mom);
+    p.alpha = nullptr; p.tw = nullptr; p.rule_buf = nullptr; p.rule_off = nullptr;
+    p.term_dev = nullptr; p.S = nullptr; p.h = nullptr; p.fin = nullptr; p.acc = nullptr;
+    p.rk = nullptr; p.mom = nullptr;
+}
+
+template <class T> bz_status dmalloc(T **ptr, size_t bytes) {
+    if (cudaMalloc((void **)ptr, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        *ptr = nullptr;
+        return BZ_ERR_OOM;
+    }
+    return BZ_OK;
+}
+
+// Twiddle vectors beta_p per axis: tw[p][d][i] = exp(-i pi r_p q_{p,d} m_i / L), m_i signed.
+std::vector<float2> make_twiddles(const bz::Plan &pl) {
+    const int N = pl.N;
+    std::vector<float2> tw((size_t)pl.P * 3 * N);
+    for (int p = 0; p < pl.P; ++p)
+        for (int d = 0; d < 3; ++d)
+            for (int i = 0; i < N; ++i) {
+                int m = i < N / 2 ? i : i - N;
+                double ph = -M_PI * pl.terms.r[p] * pl.terms.q[3 * p + d] * m / pl.L;
+                tw[((size_t)p * 3 + d) * N + i] = make_float2((float)std::cos(ph), (float)std::sin(ph));
+            }
+    return tw;
+}
+
+bz_status create(bz_plan **out, const bz_plan_desc *d) {
+    if (!out || !d) return BZ_ERR_ARG;
+    *out = nullptr;
+    if (!bz::supported_N(d->N) || d->N_rho < 1 || d->M < 1 || !(d->L > 0) || !(d->R > 0))
+        return BZ_ERR_ARG;
+    if (d->precision != BZ_PREC_FP32) return BZ_ERR_UNSUPPORTED;
+    if (d->kernel < BZ_KERNEL_FAMILY || d->kernel > BZ_KERNEL_B8) return BZ_ERR_ARG;
+    bz_plan *h = new (std::nothrow) bz_plan();
+    if (!h) return BZ_ERR_OOM;
+    bz::Plan &pl = h->p;
+    pl.N = d->N; pl.L = d->L; pl.R = d->R; pl.gamma = d->gamma; pl.s = d->s;
+    pl.N_rho = d->N_rho; pl.M = d->M; pl.kernel = d->kernel; pl.precision = d->precision;
+    pl.eps = d->eps > 0 ? d->eps : M_PI / 1000.0;
+    cudaGetDevice(&pl.device);
+    bz_status s = bz::build_terms(pl, d->sphere_xyz, d->sphere_w);
+    if (s == BZ_OK) s = bz::build_kernel_constants(pl);
+    if (s != BZ_OK) { delete h; return s; }
+    bz::build_theta_rules(pl);
+
+    const int N = pl.N;
+    const size_t n3 = (size_t)N * N * N;
+    const size_t field = n3 * sizeof(float2);
+    int chunk = d->chunk_terms;
+    if (chunk <= 0) {
+        size_t target = (size_t)32 << 20;          // chunk scratch sized to stay in L2
+        chunk = (int)(target / field);
+        if (chunk < 1) chunk = 1;
+    }
+    if (chunk > pl.P) chunk = pl.P;
+    if (chunk > 65535) chunk = 65535;
+    pl.chunk = chunk;
+
+    if ((s = dmalloc(&pl.alpha, (size_t)pl.P * field)) != BZ_OK ||
+        (s = dmalloc(&pl.tw, (size_t)pl.P * 3 * N * sizeof(float2))) != BZ_OK ||
+        (s = dmalloc(&pl.S, (size_t)chunk * field)) != BZ_OK ||
+        (s = dmalloc(&pl.h, field)) != BZ_OK ||
+        (s = dmalloc(&pl.fin, field)) != BZ_OK ||
+        (s = dmalloc(&pl.acc, n3 * sizeof(double2))) != BZ_OK ||
+        (s = dmalloc(&pl.rk, 2 * n3 * sizeof(double2))) != BZ_OK ||
+        (s = dmalloc(&pl.mom, 8 * sizeof(double))) != BZ_OK) {
+        free_plan(pl);
+        delete h;
+        return s;
+    }
+    pl.ws_bytes = (size_t)chunk * field + 2 * field + 3 * n3 * sizeof(double2);
+    std::vector<float2> tw = make_twiddles(pl);
+    if (cudaMemcpy(pl.tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess ||
+        bz::collide_set_attributes(N) != cudaSuccess) {
+        free_plan(pl);
+        delete h;
+        return BZ_ERR_CUDA;
+    }
+    s = bz::ftable_build(pl);
+    if (s != BZ_OK) {
+        free_plan(pl);
+        delete h;
+        return s;
+    }
+    *out = h;
+    return BZ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+bz_status bz_plan_create(bz_plan **out, int N, double L, double R, double gamma, double s,
+                         int N_rho, int M) {
+    bz_plan_desc d;
+    std::memset(&d, 0, sizeof(d));
+    d.N = N; d.L = L; d.R = R; d.gamma = gamma; d.s = s; d.N_rho = N_rho; d.M = M;
+    d.kernel = BZ_KERNEL_FAMILY; d.precision = BZ_PREC_FP32; d.eps = 0.0;
+    return create(out, &d);
+}
+
+bz_status bz_plan_create_ex(bz_plan **out, const bz_plan_desc *desc) { return create(out, desc); }
+
+void bz_plan_destroy(bz_plan *plan) {
+    if (!plan) return;
+    free_plan(plan->p);
+    delete plan;
+}
+
+bz_status bz_plan_info(const bz_plan *plan, int *P, size_t *alpha_bytes, size_t *workspace_bytes) {
+    if (!plan) return BZ_ERR_ARG;
+    const bz::Plan &p = plan->p;
+    size_t n3 = (size_t)p.N * p.N * p.N;
+    if (P) *P = p.P;
+    if (alpha_bytes) *alpha_bytes = (size_t)p.P * n3 * sizeof(float2);
+    if (workspace_bytes) *workspace_bytes = p.ws_bytes;
+    return BZ_OK;
+}
+
+bz_status bz_plan_terms(const bz_plan *plan, double *r, double *w_r, double *qhat, double *w_q,
+                        double *c) {
+    if (!plan) return BZ_ERR_ARG;
+    const bz::HostTerms &T = plan->p.terms;
+    const int P = plan->p.P;
+    for (int p = 0; p < P; ++p) {
+        if (r) r[p] = T.r[p];
+        if (w_r) w_r[p] = T.wr[p];
+        if (w_q) w_q[p] = T.wq[p];
+        if (c) c[p] = T.c[p];
+        if (qhat) for (int d = 0; d < 3; ++d) qhat[3 * p + d] = T.q[3 * p + d];
+    }
+    return BZ_OK;
+}
+
+bz_status bz_collide_terms(bz_plan *plan, int p0, int p1, const void *fhat, void *Qhat, int dtype,
+                           void *stream) {
+    if (!plan || !fhat || !Qhat || fhat == Qhat) return BZ_ERR_ARG;
+    bz::Plan &pl = plan->p;
+    if (p0 < 0 || p1 < p0 || p1 > pl.P) return BZ_ERR_ARG;
+    if (dtype != BZ_C64 && dtype != BZ_C128) return BZ_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    int nl = 0;
+    bz_status s = bz::collide_range(pl, p0, p1, fhat, dtype, st, &nl);
+    if (s == BZ_OK) s = bz::write_output(pl, Qhat, dtype, st, &nl);
+    pl.last_launches = nl;
+    return s;
+}
+
+bz_status bz_collide(bz_plan *plan, const void *fhat, void *Qhat, int dtype, void *stream) {
+    if (!plan) return BZ_ERR_ARG;
+    return bz_collide_terms(plan, 0, plan->p.P, fhat, Qhat, dtype, stream);
+}
+
+bz_status bz_step_rk(bz_plan *plan, void *fhat, int dtype, double *t, double dt, int nsteps,
+                     void *workspace, void *stream) {
+    (void)workspace;
+    if (!plan || !fhat || nsteps < 0 || !std::isfinite(dt)) return BZ_ERR_ARG;
+    if (dtype != BZ_C64 && dtype != BZ_C128) return BZ_ERR_ARG;
+    int nl = 0;
+    bz_status s = bz::rk4_steps(plan->p, fhat, dtype, dt, nsteps, (cudaStream_t)stream, &nl);
+    plan->p.last_launches = nl;
+    if (s == BZ_OK && t) *t += dt * nsteps;
+    return s;
+}
+
+bz_status bz_moments(bz_plan *plan, const void *fhat, int dtype, double out[5], void *stream) {
+    if (!plan || !fhat || !out) return BZ_ERR_ARG;
+    if (dtype != BZ_C64 && dtype != BZ_C128) return BZ_ERR_ARG;
+    return bz::moments(plan->p, fhat, dtype, out, (cudaStream_t)stream);
+}
+
+bz_status bz_ftable_entries(bz_plan *plan, int count, const int *k_idx, const int *term,
+                            double *out) {
+    if (!plan || count < 0 || (count > 0 && (!k_idx || !term || !out))) return BZ_ERR_ARG;
+    return bz::ftable_entries(plan->p, count, k_idx, term, out);
+}
+
+bz_status bz_plan_alpha(const bz_plan *plan, int p0, int p1, void *dst, void *stream) {
+    if (!plan || !dst) return BZ_ERR_ARG;
+    const bz::Plan &pl = plan->p;
+    if (p0 < 0 || p1 < p0 || p1 > pl.P) return BZ_ERR_ARG;
+    size_t n3 = (size_t)pl.N * pl.N * pl.N;
+    if (cudaMemcpyAsync(dst, pl.alpha + (size_t)p0 * n3, (size_t)(p1 - p0) * n3 * sizeof(float2),
+                        cudaMemcpyDeviceToDevice, (cudaStream_t)stream) != cudaSuccess)
+        return BZ_ERR_CUDA;
+    return BZ_OK;
+}
+
+int bz_plan_last_launches(const bz_plan *plan) { return plan ? plan->p.last_launches : 0; }
+
+bz_status bz_plan_set_timing(bz_plan *plan, int max_launches) {
+    if (!plan || max_launches < 0) return BZ_ERR_ARG;
+    bz::Plan &pl = plan->p;
+    free_timing(pl);
+    for (int k = 0; k < bz::TK_COUNT; ++k) { pl.tm.ms[k] = 0.0; pl.tm.n[k] = 0; }
+    if (max_launches == 0) return BZ_OK;
+    pl.tm.ev.resize(2 * (size_t)max_launches);
+    for (size_t i = 0; i < pl.tm.ev.size(); ++i) {
+        if (cudaEventCreate(&pl.tm.ev[i]) != cudaSuccess) {
+            pl.tm.ev.resize(i);
+            free_timing(pl);
+            return BZ_ERR_CUDA;
+        }
+    }
+    pl.tm.kind.assign(max_launches, 0);
+    pl.tm.on = true;
+    return BZ_OK;
+}
+
+bz_status bz_plan_timing(bz_plan *plan, int kind, long *launches, double *ms) {
+    if (!plan || kind < 0 || kind >= bz::TK_COUNT) return BZ_ERR_ARG;
+    bz::Plan &pl = plan->p;
+    if (pl.tm.used > 0) {
+        if (cudaEventSynchronize(pl.tm.ev[2 * pl.tm.used - 1]) != cudaSuccess) return BZ_ERR_CUDA;
+        for (size_t i = 0; i < pl.tm.used; ++i) {
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, pl.tm.ev[2 * i], pl.tm.ev[2 * i + 1]) != cudaSuccess)
+                return BZ_ERR_CUDA;
+            pl.tm.ms[pl.tm.kind[i]] += t;
+            pl.tm.n[pl.tm.kind[i]] += 1;
+        }
+        pl.tm.used = 0;
+    }
+    if (launches) *launches = pl.tm.n[kind];
+    if (ms) *ms = pl.tm.ms[kind];
+    return BZ_OK;
+}
+
+const char *bz_status_str(bz_status s) {
+    switch (s) {
+        case BZ_OK: return "ok";
+        case BZ_ERR_ARG: return "invalid argument";
+        case BZ_ERR_OOM: return "out of memory";
+        case BZ_ERR_CUDA: return "CUDA error";
+        case BZ_ERR_TIMEOUT: return "timeout";
+        case BZ_ERR_NONFINITE: return "non-finite value";
+        case BZ_ERR_BUSY: return "busy";
+        case BZ_ERR_UNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+}  // extern "C"

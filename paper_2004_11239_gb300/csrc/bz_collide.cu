@@ -1,0 +1,265 @@
+// The per-term pipeline of eq. realQ (Sec. 4) in FP32 with FP64 accumulation over terms.
+//
+// For each chunk of T terms, four kernels run over a scratch buffer S[T][N^3] sized to
+// stay in L2:
+//   plane_inv  (planes k1):  S = IFFT_{axes 3,2}( beta_p(m) fhat_m )       twiddle + 2 axes
+//   pencil     (lines k1):   S = FFT_1( h . IFFT_1(S) )                     product in registers
+//   plane_fwd  (planes k1):  S = alpha_p . FFT_{axes 3,2}(S)                 weight in the epilogue
+//   reduce     (modes k):    acc += sum_t S[t]  (compensated FP32 over t, then FP64)
+// h = IFFT(fhat) is formed once per call by plane_inv without twiddles plus an
+// inverse-only pencil pass.  Inverse transforms are unnormalised; alpha carries N^-3.
+#include <cstdio>
+
+#include "bz_fft.cuh"
+#include "bz_internal.h"
+
+namespace bz {
+
+template <int N> struct Cfg {
+    static constexpr int PPC = N <= 8 ? 8 : (N <= 16 ? 16 : (N <= 32 ? 8 : 4));   // planes per CTA
+    static constexpr int LD = N + 1;                                              // padded row
+    static constexpr int THREADS = PPC * N;
+    static constexpr size_t SMEM = (size_t)PPC * N * LD * sizeof(float2);
+};
+
+// ---------------------------------------------------------------------------------------
+// plane_inv: one CTA holds PPC planes k1 of one term; N threads per plane.
+// ---------------------------------------------------------------------------------------
+template <int N>
+__global__ void __launch_bounds__(Cfg<N>::THREADS)
+k_plane_inv(const float2 *__restrict__ fin, const float2 *__restrict__ tw, float2 *__restrict__ S,
+            int p0, int use_tw) {
+    constexpr int PPC = Cfg<N>::PPC, LD = Cfg<N>::LD;
+    extern __shared__ float2 sm[];
+    const int lane = threadIdx.x % N, pid = threadIdx.x / N;
+    const int k1 = blockIdx.x * PPC + pid;
+    const int t = blockIdx.y;
+    float2 *s = sm + pid * N * LD;
+    const float2 *f = fin + (size_t)k1 * N * N;
+    const float2 *twp = tw + (size_t)(p0 + t) * 3 * N;
+    float2 t13 = make_float2(1.f, 0.f);
+    if (use_tw) t13 = cmul(twp[k1], twp[2 * N + lane]);
+    #pragma unroll 4
+    for (int i = 0; i < N; ++i) {
+        float2 v = f[i * N + lane];
+        if (use_tw) v = cmul(v, cmul(t13, twp[N + i]));
+        s[i * LD + lane] = v;
+    }
+    __syncthreads();
+    float2 x[N];
+    #pragma unroll
+    for (int j = 0; j < N; ++j) x[j] = s[lane * LD + j];
+    fft_inplace<N, +1>(x);                       // axis 3: k3 -> j3
+    #pragma unroll
+    for (int j = 0; j < N; ++j) s[lane * LD + j] = x[j];
+    __syncthreads();
+    #pragma unroll
+    for (int i = 0; i < N; ++i) x[i] = s[i * LD + lane];
+    fft_inplace<N, +1>(x);                       // axis 2: k2 -> j2
+    float2 *out = S + (size_t)t * N * N * N + (size_t)k1 * N * N;
+    #pragma unroll
+    for (int i = 0; i < N; ++i) out[i * N + lane] = x[i];
+}
+
+// ---------------------------------------------------------------------------------------
+// pencil: one thread per (j2, j3) line along axis 1 of one term.
+//   MODE 0: out = IFFT_1(S)                         (forms h)
+//   MODE 1: S = FFT_1( h . IFFT_1(S) )              (in place)
+// ---------------------------------------------------------------------------------------
+template <int N, int MODE>
+__global__ void __launch_bounds__(128)
+k_pencil(float2 *__restrict__ S, const float2 *__restrict__ h, float2 *__restrict__ out) {
+    constexpr int N2 = N * N;
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= N2) return;
+    float2 *base = S + (size_t)blockIdx.y * N * N2 + g;
+    float2 x[N];
+    #pragma unroll
+    for (int k = 0; k < N; ++k) x[k] = base[k * N2];
+    fft_inplace<N, +1>(x);                       // axis 1: k1 -> j1
+    if constexpr (MODE == 0) {
+        #pragma unroll
+        for (int j = 0; j < N; ++j) out[j * N2 + g] = x[j];
+    } else {
+        #pragma unroll
+        for (int j = 0; j < N; ++j) x[j] = cmul(x[j], h[j * N2 + g]);
+        fft_inplace<N, -1>(x);                   // axis 1: j1 -> k1
+        #pragma unroll
+        for (int k = 0; k < N; ++k) base[k * N2] = x[k];
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// plane_fwd: forward transform along axes 2 and 3, times alpha_p, in place.
+// ---------------------------------------------------------------------------------------
+template <int N>
+__global__ void __launch_bounds__(Cfg<N>::THREADS)
+k_plane_fwd(float2 *__restrict__ S, const float2 *__restrict__ alpha, int p0) {
+    constexpr int PPC = Cfg<N>::PPC, LD = Cfg<N>::LD;
+    extern __shared__ float2 sm[];
+    const int lane = threadIdx.x % N, pid = threadIdx.x / N;
+    const int k1 = blockIdx.x * PPC + pid;
+    const int t = blockIdx.y;
+    float2 *s = sm + pid * N * LD;
+    float2 *pl = S + (size_t)t * N * N * N + (size_t)k1 * N * N;
+    float2 x[N];
+    #pragma unroll
+    for (int i = 0; i < N; ++i) x[i] = pl[i * N + lane];     // column j3 = lane, over j2
+    fft_inplace<N, -1>(x);                                    // axis 2: j2 -> k2
+    #pragma unroll
+    for (int i = 0; i < N; ++i) s[i * LD + lane] = x[i];
+    __syncthreads();
+    #pragma unroll
+    for (int j = 0; j < N; ++j) x[j] = s[lane * LD + j];     // row k2 = lane, over j3
+    fft_inplace<N, -1>(x);                                    // axis 3: j3 -> k3
+    #pragma unroll
+    for (int j = 0; j < N; ++j) s[lane * LD + j] = x[j];
+    __syncthreads();
+    const float2 *al = alpha + (size_t)(p0 + t) * N * N * N + (size_t)k1 * N * N;
+    #pragma unroll 4
+    for (int i = 0; i < N; ++i) pl[i * N + lane] = cmul(s[i * LD + lane], al[i * N + lane]);
+}
+
+// ---------------------------------------------------------------------------------------
+// reduce: acc[k] += sum_t S[t][k], Kahan-compensated in FP32 over the chunk's terms (in
+// term order), then added to the FP64 accumulator.
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+k_reduce(const float2 *__restrict__ S, int T, int n3, double2 *__restrict__ acc) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n3) return;
+    float sr = 0.f, si = 0.f, cr = 0.f, ci = 0.f;
+    for (int t = 0; t < T; ++t) {
+        float2 v = S[(size_t)t * n3 + k];
+        float yr = v.x - cr, yi = v.y - ci;
+        float tr = sr + yr, ti = si + yi;
+        cr = (tr - sr) - yr;
+        ci = (ti - si) - yi;
+        sr = tr;
+        si = ti;
+    }
+    double2 a = acc[k];
+    a.x += (double)sr - (double)cr;
+    a.y += (double)si - (double)ci;
+    acc[k] = a;
+}
+
+__global__ void k_c128_to_c64(const double2 *__restrict__ in, float2 *__restrict__ out, int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = make_float2((float)in[i].x, (float)in[i].y);
+}
+
+__global__ void k_acc_to_c64(const double2 *__restrict__ in, float2 *__restrict__ out, int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = make_float2((float)in[i].x, (float)in[i].y);
+}
+
+// ---------------------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------------------
+int supported_N(int N) {
+    return N == 8 || N == 16 || N == 24 || N == 32 || N == 48 || N == 64;
+}
+
+template <int N> static cudaError_t set_attrs() {
+    cudaError_t e = cudaFuncSetAttribute(k_plane_inv<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)Cfg<N>::SMEM);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_plane_fwd<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)Cfg<N>::SMEM);
+}
+
+cudaError_t collide_set_attributes(int N) {
+    switch (N) {
+        case 8: return set_attrs<8>();
+        case 16: return set_attrs<16>();
+        case 24: return set_attrs<24>();
+        case 32: return set_attrs<32>();
+        case 48: return set_attrs<48>();
+        case 64: return set_attrs<64>();
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <int N>
+static bz_status run_chunks(Plan &pl, int p0, int p1, cudaStream_t st, int *launches) {
+    constexpr int PPC = Cfg<N>::PPC;
+    const int n3 = N * N * N;
+    const dim3 plane_grid1(N / PPC, 1);
+    // h = IFFT(fhat): planes without twiddles into S[0], then an inverse-only pencil pass
+    tm_begin(pl, st);
+    k_plane_inv<N><<<plane_grid1, Cfg<N>::THREADS, Cfg<N>::SMEM, st>>>(pl.fin, pl.tw, pl.S, 0, 0);
+    k_pencil<N, 0><<<dim3((N * N + 127) / 128, 1), 128, 0, st>>>(pl.S, nullptr, pl.h);
+    BZ_CUDA_TRY(cudaMemsetAsync(pl.acc, 0, (size_t)n3 * sizeof(double2), st));
+    tm_end(pl, st, TK_OTHER);
+    int nl = 2;
+    for (int c0 = p0; c0 < p1; c0 += pl.chunk) {
+        const int T = (p1 - c0) < pl.chunk ? (p1 - c0) : pl.chunk;
+        tm_begin(pl, st);
+        k_plane_inv<N><<<dim3(N / PPC, T), Cfg<N>::THREADS, Cfg<N>::SMEM, st>>>(pl.fin, pl.tw, pl.S, c0, 1);
+        tm_end(pl, st, TK_PLANE_INV);
+        tm_begin(pl, st);
+        k_pencil<N, 1><<<dim3((N * N + 127) / 128, T), 128, 0, st>>>(pl.S, pl.h, nullptr);
+        tm_end(pl, st, TK_PENCIL);
+        tm_begin(pl, st);
+        k_plane_fwd<N><<<dim3(N / PPC, T), Cfg<N>::THREADS, Cfg<N>::SMEM, st>>>(pl.S, pl.alpha, c0);
+        tm_end(pl, st, TK_PLANE_FWD);
+        tm_begin(pl, st);
+        k_reduce<<<(n3 + 255) / 256, 256, 0, st>>>(pl.S, T, n3, pl.acc);
+        tm_end(pl, st, TK_REDUCE);
+        nl += 4;
+    }
+    BZ_CUDA_TRY(cudaGetLastError());
+    if (launches) *launches += nl;
+    return BZ_OK;
+}
+
+bz_status load_input(Plan &pl, const void *fhat, int dtype, cudaStream_t st, int *launches) {
+    const int n3 = pl.N * pl.N * pl.N;
+    if (dtype == BZ_C64) {
+        BZ_CUDA_TRY(cudaMemcpyAsync(pl.fin, fhat, (size_t)n3 * sizeof(float2), cudaMemcpyDeviceToDevice, st));
+    } else if (dtype == BZ_C128) {
+        k_c128_to_c64<<<(n3 + 255) / 256, 256, 0, st>>>((const double2 *)fhat, pl.fin, n3);
+        BZ_CUDA_TRY(cudaGetLastError());
+        if (launches) *launches += 1;
+    } else {
+        return BZ_ERR_ARG;
+    }
+    return BZ_OK;
+}
+
+// Q over terms [p0, p1) of the FP32 input already in pl.fin; result in pl.acc (FP64).
+bz_status collide_core(Plan &pl, int p0, int p1, cudaStream_t st, int *launches) {
+    switch (pl.N) {
+        case 8: return run_chunks<8>(pl, p0, p1, st, launches);
+        case 16: return run_chunks<16>(pl, p0, p1, st, launches);
+        case 24: return run_chunks<24>(pl, p0, p1, st, launches);
+        case 32: return run_chunks<32>(pl, p0, p1, st, launches);
+        case 48: return run_chunks<48>(pl, p0, p1, st, launches);
+        case 64: return run_chunks<64>(pl, p0, p1, st, launches);
+    }
+    return BZ_ERR_ARG;
+}
+
+bz_status collide_range(Plan &pl, int p0, int p1, const void *fhat, int in_dtype, cudaStream_t st,
+                        int *launches) {
+    bz_status s = load_input(pl, fhat, in_dtype, st, launches);
+    if (s != BZ_OK) return s;
+    return collide_core(pl, p0, p1, st, launches);
+}
+
+bz_status write_output(Plan &pl, void *Qhat, int dtype, cudaStream_t st, int *launches) {
+    const int n3 = pl.N * pl.N * pl.N;
+    if (dtype == BZ_C128) {
+        BZ_CUDA_TRY(cudaMemcpyAsync(Qhat, pl.acc, (size_t)n3 * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+    } else if (dtype == BZ_C64) {
+        k_acc_to_c64<<<(n3 + 255) / 256, 256, 0, st>>>(pl.acc, (float2 *)Qhat, n3);
+        BZ_CUDA_TRY(cudaGetLastError());
+        if (launches) *launches += 1;
+    } else {
+        return BZ_ERR_ARG;
+    }
+    return BZ_OK;
+}
+
+}  // namespace bz

@@ -1,0 +1,105 @@
+// Internal declarations shared by the translation units of libbz (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include "../../include/bz.h"
+
+namespace bz {
+
+// One radial node's part-II theta rule (Sec. 4.1): nodes t_n on [eps, pi] with
+// weights W_n = w_n g(t_n), stored as (1 - cos t_n, sin t_n, W_n).
+struct ThetaRule {
+    std::vector<double> omc, sn, W;
+};
+
+struct HostTerms {
+    std::vector<double> r, wr, q, wq, c;   // per term p = i*M + j; q is [P][3]
+    std::vector<int> radial_index;          // i for each p
+};
+
+// Optional per-kernel CUDA-event timing (bz_plan_set_timing).
+enum { TK_PLANE_INV = 0, TK_PENCIL = 1, TK_PLANE_FWD = 2, TK_REDUCE = 3, TK_OTHER = 4, TK_COUNT = 5 };
+struct Timing {
+    bool on = false;
+    std::vector<cudaEvent_t> ev;    // pairs (start, end)
+    std::vector<int> kind;          // per pair
+    size_t used = 0;                // pairs recorded since the last collect
+    double ms[TK_COUNT] = {0, 0, 0, 0, 0};
+    long n[TK_COUNT] = {0, 0, 0, 0, 0};
+};
+
+struct Plan {
+    // parameters
+    int N = 0, N_rho = 0, M = 0, P = 0, kernel = 0, precision = 0, device = 0;
+    double L = 0, R = 0, gamma = 0, s = 0, eps = 0;
+    double A[3] = {0, 0, 0};        // part I kernel moments
+    double kc = 0;                  // kernel constant (c_s, 1/(4 pi), 5/(192 pi))
+    HostTerms terms;
+    std::vector<ThetaRule> rules;   // one per radial node
+    // device tables
+    float2 *alpha = nullptr;        // [P][N^3]  c_p F / N^3
+    float2 *tw = nullptr;           // [P][3][N] exp(-i pi r q_d m / L)
+    double *rule_buf = nullptr;     // concatenated (omc, sn, W) per radial node
+    int *rule_off = nullptr;        // [N_rho + 1] node offsets
+    int rule_max = 0;               // largest node count of one radial node
+    double *term_dev = nullptr;     // [P][5]: r, q0, q1, q2, c
+    // workspace
+    int chunk = 0;                  // terms per chunk
+    float2 *S = nullptr;            // [chunk][N^3]
+    float2 *h = nullptr;            // [N^3]
+    float2 *fin = nullptr;          // [N^3] FP32 input
+    double2 *acc = nullptr;         // [N^3] FP64 accumulator
+    double2 *rk = nullptr;          // [3][N^3] RK4 state (f0, fsum) + spare
+    double *mom = nullptr;          // moments scratch
+    size_t ws_bytes = 0;
+    int last_launches = 0;
+    Timing tm;
+};
+
+// Brackets one launch with events when timing is on (events are pre-created).
+inline void tm_begin(Plan &pl, cudaStream_t st) {
+    if (pl.tm.on && pl.tm.used < pl.tm.kind.size()) cudaEventRecord(pl.tm.ev[2 * pl.tm.used], st);
+}
+inline void tm_end(Plan &pl, cudaStream_t st, int kind) {
+    if (pl.tm.on && pl.tm.used < pl.tm.kind.size()) {
+        cudaEventRecord(pl.tm.ev[2 * pl.tm.used + 1], st);
+        pl.tm.kind[pl.tm.used++] = kind;
+    }
+}
+
+// bz_quad.cpp
+int gauss_legendre(int n, double a, double b, std::vector<double> &x, std::vector<double> &w);
+bz_status build_terms(Plan &pl, const double *sphere_xyz, const double *sphere_w);
+bz_status build_kernel_constants(Plan &pl);
+void build_theta_rules(Plan &pl);
+
+// bz_ftable.cu
+bz_status ftable_build(Plan &pl);
+bz_status ftable_entries(Plan &pl, int count, const int *k_idx, const int *term, double *out);
+
+// bz_collide.cu
+bz_status collide_range(Plan &pl, int p0, int p1, const void *fhat, int in_dtype,
+                        cudaStream_t st, int *launches);
+bz_status write_output(Plan &pl, void *Qhat, int dtype, cudaStream_t st, int *launches);
+bz_status load_input(Plan &pl, const void *fhat, int dtype, cudaStream_t st, int *launches);
+bz_status collide_core(Plan &pl, int p0, int p1, cudaStream_t st, int *launches);
+cudaError_t collide_set_attributes(int N);
+int supported_N(int N);
+
+// bz_rk.cu
+bz_status rk4_steps(Plan &pl, void *fhat, int dtype, double dt, int nsteps, cudaStream_t st,
+                    int *launches);
+bz_status moments(Plan &pl, const void *fhat, int dtype, double out[5], cudaStream_t st);
+
+}  // namespace bz
+
+#define BZ_CUDA_TRY(expr)                                   \
+    do {                                                    \
+        cudaError_t _e = (expr);                            \
+        if (_e != cudaSuccess) return BZ_ERR_CUDA;          \
+    } while (0)

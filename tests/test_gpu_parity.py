@@ -1,0 +1,165 @@
+"""CUDA path vs the FP64 oracle, through the C ABI (GPU).
+
+Bar (the FP32 pipeline): relative L-infinity error max|Q_gpu - Q_oracle| / max|Q_oracle|
+<= 1e-5.  The FP64 F table on the GPU matches the oracle's to 1e-10 of max|F| (both
+converged quadratures of the same split).  Every input is seeded (bz_inputs).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import bz_inputs as bi
+from oracle import kernels, spectral, ftable
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def bz():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__._libbuild().build()
+    import paper_2004_11239_gb300 as m
+    return m
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+def _gpu_collide(bz, plan, fhat, p0=None, p1=None, dtype=torch.complex128):
+    f = torch.from_numpy(np.asarray(fhat)).to("cuda", dtype=dtype)
+    q = torch.empty_like(f)
+    if p0 is None:
+        bz.bz_collide(plan, f, q)
+    else:
+        bz.bz_collide_terms(plan, p0, p1, f, q)
+    torch.cuda.synchronize()
+    return q.cpu().numpy().astype(np.complex128)
+
+
+KERNELS = [("family", 0.5, 0), ("family", 0.25, 0), ("family", 0.75, 0), ("b5", 0.0, 1), ("b8", 0.0, 2)]
+
+
+@pytest.mark.parametrize("name,s,kid", KERNELS)
+def test_ftable_fp64_entries_match_oracle(bz, name, s, kid):
+    N, L = 16, 10.0
+    R = bi.R_from_L(L)
+    plan = bz.bz_plan_create_ex(N, L, R, 0.0, s, 4, 12, kernel=kid)
+    r, wr, q, wq, c = bz.bz_plan_terms(plan)
+    u = bi.SplitMix64(17).uniform(3 * 64)
+    kidx = (u[:3 * 64].reshape(64, 3) * N).astype(np.int32)
+    terms = (bi.SplitMix64(18).uniform(64) * plan.P).astype(np.int32)
+    got = bz.bz_ftable_entries(plan, torch.from_numpy(kidx).cuda(), torch.from_numpy(terms).cuda()).cpu().numpy()
+    ks = bi.signed_modes(N)[kidx]
+    ref = ftable.fentries(N, L, ks, r[terms], q[terms], kernels.Kernel(name, s))
+    assert np.max(np.abs(got - ref)) <= 1e-10 * np.max(np.abs(ref))
+    # the FP32 alpha table stores c_p F / N^3
+    alpha = bz.bz_plan_alpha(plan, 0, plan.P).cpu().numpy().reshape(plan.P, -1)
+    flat = (kidx[:, 0] * N + kidx[:, 1]) * N + kidx[:, 2]
+    a_ref = c[terms] * ref / N ** 3
+    assert np.max(np.abs(alpha[terms, flat] - a_ref)) <= 1e-6 * np.max(np.abs(a_ref))
+    plan.close()
+
+
+@pytest.mark.parametrize("N,N_rho,M,gamma,name,s,kid,data", [
+    (8, 3, 12, -1.0, "family", 0.5, 0, "random"),
+    (16, 16, 12, 0.0, "family", 0.5, 0, "c1"),        # the N = 16 single-evaluation workload
+    (16, 4, 32, -1.0, "b8", 0.0, 2, "mixture"),
+    (24, 4, 12, 0.0, "family", 0.25, 0, "mixture"),
+    (32, 2, 32, -2.0, "family", 0.75, 0, "mixture"),
+    (48, 1, 12, 0.0, "b5", 0.0, 1, "mixture"),
+])
+def test_collide_matches_oracle(bz, N, N_rho, M, gamma, name, s, kid, data):
+    L = 10.0
+    R = bi.R_from_L(L)
+    if data == "random":
+        fhat = bi.random_fhat(N, seed=5, scale=1e-3)
+    elif data == "c1":
+        fhat = bi.two_maxwellians_c1(N, L)
+    else:
+        fhat = bi.random_mixture(N, L, seed=N)
+    plan = bz.bz_plan_create_ex(N, L, R, gamma, s, N_rho, M, kernel=kid)
+    got = _gpu_collide(bz, plan, fhat)
+    oplan = spectral.OraclePlan(N, L, R, gamma, kernels.Kernel(name, s), N_rho, M)
+    ref = spectral.collide(oplan, fhat)
+    assert _rel(got, ref) <= TOL
+    assert got[0, 0, 0] == 0           # F(0) = 0 exactly, hence Qhat_0 = 0 (Sec. 4 remark)
+    plan.close()
+
+
+def test_collide_n64_term_subset(bz):
+    """N = 64 with a ragged chunk: 12 terms through chunks of 5."""
+    N, L = 64, 10.0
+    R = bi.R_from_L(L)
+    fhat = bi.bigaussian_noise_c3(N, L)
+    plan = bz.bz_plan_create_ex(N, L, R, -1.0, 0.5, 1, 12, chunk_terms=5)
+    got = _gpu_collide(bz, plan, fhat)
+    oplan = spectral.OraclePlan(N, L, R, -1.0, kernels.Kernel("family", 0.5), 1, 12)
+    ref = spectral.collide(oplan, fhat)
+    assert _rel(got, ref) <= TOL
+    plan.close()
+
+
+def test_collide_terms_ranges_add_up_and_edge_cases(bz):
+    N, L = 16, 10.0
+    plan = bz.bz_plan_create_ex(N, L, bi.R_from_L(L), 0.0, 0.5, 5, 12, chunk_terms=7)
+    fhat = bi.random_mixture(N, L, seed=3)
+    full = _gpu_collide(bz, plan, fhat)
+    parts = _gpu_collide(bz, plan, fhat, 0, 13) + _gpu_collide(bz, plan, fhat, 13, plan.P)
+    assert _rel(parts, full) <= 1e-6
+    empty = _gpu_collide(bz, plan, fhat, 7, 7)
+    assert np.all(empty == 0)
+    f = torch.from_numpy(fhat).cuda()
+    with pytest.raises(bz.BzError):
+        bz.bz_collide(plan, f, f)                    # aliasing rejected
+    q = torch.empty_like(f)
+    with pytest.raises(bz.BzError):
+        bz.bz_collide_terms(plan, 3, plan.P + 1, f, q)
+    with pytest.raises(bz.BzError):
+        bz.bz_collide_terms(plan, 5, 4, f, q)
+    plan.close()
+
+
+def test_c64_and_c128_io_agree(bz):
+    N, L = 16, 10.0
+    plan = bz.bz_plan_create(N, L, bi.R_from_L(L), 0.0, 0.5, 4, 12)
+    fhat = bi.random_mixture(N, L, seed=9)
+    a = _gpu_collide(bz, plan, fhat, dtype=torch.complex128)
+    b = _gpu_collide(bz, plan, fhat.astype(np.complex64), dtype=torch.complex64)
+    assert _rel(b, a) <= 1e-6
+    plan.close()
+
+
+def test_moments_match_oracle(bz):
+    N, L = 32, 10.0
+    plan = bz.bz_plan_create(N, L, bi.R_from_L(L), 0.0, 0.5, 1, 12)
+    fhat = bi.random_mixture(N, L, seed=21, box=2.0)
+    got = bz.bz_moments(plan, torch.from_numpy(fhat).cuda())
+    ref = spectral.moments(fhat, L)
+    assert np.allclose(got, ref, rtol=1e-12, atol=1e-14)
+    plan.close()
+
+
+def test_rk4_matches_oracle_trajectory(bz):
+    N, L = 16, bi.L_from_R(6.0)
+    R = 6.0
+    plan = bz.bz_plan_create(N, L, R, 0.0, 0.5, 8, 12)
+    f0 = bi.bkw_fhat(N, L, bi.bkw_K(6.5))
+    f = torch.from_numpy(f0).cuda()
+    t = bz.bz_step_rk(plan, f, 6.5, 0.05, 4)
+    torch.cuda.synchronize()
+    assert abs(t - 6.7) < 1e-12
+    oplan = spectral.OraclePlan(N, L, R, 0.0, kernels.Kernel("family", 0.5), 8, 12)
+    ref = spectral.rk4(oplan, f0, 0.05, 4)
+    got = f.cpu().numpy()
+    # compare the change over the four steps (the state itself is dominated by f0)
+    assert _rel(got - f0, ref - f0) <= TOL
+    # mass is conserved exactly by the scheme (Qhat_0 = 0)
+    assert got[0, 0, 0] == f0[0, 0, 0]
+    plan.close()
