@@ -128,6 +128,30 @@ bz_status bz_plan_alpha(const bz_plan *plan, int p0, int p1, void *dst, void *st
 
 const char *bz_status_str(bz_status s);
 
+/* Allocation-free collide.  The paper has no counterpart: this entry point exists for
+ * callers that cannot let a library allocate device memory during a call (an application
+ * whose device memory is reserved up front by its own pool allocator, a latency-critical
+ * time loop that cannot pay the device synchronisation of cudaMalloc/cudaFree, a host
+ * that forbids a library to grow its footprint after start-up).
+ * Same result as bz_collide (within the FP32 pipeline's rounding; the term chunking
+ * differs), but every scratch buffer lives in one file-scope device array of
+ * BZ_NOALLOC_SCRATCH_BYTES that each GPU loading libbz holds until the process exits;
+ * nothing is allocated or freed.  The plan must have been created beforehand on the
+ * current device.
+ *   - Size limit: the array holds the FP32 input copy, h, the FP64 accumulator and at least
+ *     one term of scratch, i.e. 40 N^3 bytes (rounded up to 256-byte blocks); N = 64 does not
+ *     fit and returns BZ_ERR_ARG without touching Qhat.  N <= 48 fits.
+ *   - The first call on each device looks up the array's device address (cudaGetSymbolAddress)
+ *     with that device current; make that first call before any stream capture begins.
+ *   - All calls share the one array and it keeps the previous call's contents (the
+ *     accumulator is cleared on the stream at the start of every call).  Calls whose work
+ *     overlaps on the GPU (other streams, other host threads) race on the array: serialise them.
+ * Errors: BZ_ERR_ARG for NULL or aliased arrays, a bad dtype, a plan of another device or a
+ * plan too large for the array; BZ_ERR_CUDA if the address lookup or a launch fails. */
+#define BZ_NOALLOC_SCRATCH_BYTES (8u << 20)
+bz_status bz_collide_noalloc(const bz_plan *plan, const void *fhat, void *Qhat, int dtype,
+                             void *stream);
+
 /* Kernel kinds reported by bz_plan_timing. */
 enum { BZ_K_PLANE_INV = 0, BZ_K_PENCIL = 1, BZ_K_PLANE_FWD = 2, BZ_K_REDUCE = 3, BZ_K_OTHER = 4 };
 

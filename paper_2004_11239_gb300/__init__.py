@@ -20,7 +20,7 @@ __all__ = [
     "bz_plan_create", "bz_plan_create_ex", "bz_plan_destroy", "bz_plan_info", "bz_plan_terms",
     "bz_collide", "bz_collide_terms", "bz_step_rk", "bz_moments", "bz_ftable_entries",
     "bz_plan_alpha", "bz_plan_last_launches", "bz_status_str", "library_path", "lib",
-    "bz_plan_set_timing", "bz_plan_timing",
+    "bz_plan_set_timing", "bz_plan_timing", "bz_collide_noalloc",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -68,6 +68,7 @@ def _load():
         "bz_moments": [vp, vp, c_int, dp, vp],
         "bz_ftable_entries": [vp, c_int, vp, vp, vp],
         "bz_plan_alpha": [vp, c_int, c_int, vp, vp],
+        "bz_collide_noalloc": [vp, vp, vp, c_int, vp],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -205,6 +206,15 @@ def bz_collide_terms(plan: Plan, p0: int, p1: int, fhat, Qhat, stream=None):
         raise TypeError("fhat and Qhat must have the same dtype")
     _check(lib.bz_collide_terms(plan.handle, p0, p1, _dev(fhat, plan.n3), _dev(Qhat, plan.n3), dt,
                                 _stream(stream)), "bz_collide_terms")
+
+
+def bz_collide_noalloc(plan: Plan, fhat, Qhat, stream=None):
+    """bz_collide with its scratch in the library's fixed device array (no allocation)."""
+    dt = _dtype(fhat)
+    if _dtype(Qhat) != dt:
+        raise TypeError("fhat and Qhat must have the same dtype")
+    _check(lib.bz_collide_noalloc(plan.handle, _dev(fhat, plan.n3), _dev(Qhat, plan.n3), dt,
+                                  _stream(stream)), "bz_collide_noalloc")
 
 
 def bz_step_rk(plan: Plan, fhat, t: float, dt: float, nsteps: int, stream=None) -> float:

@@ -10,6 +10,10 @@ struct bz_plan {
     bz::Plan p;
 };
 
+namespace bz {
+const Plan *plan_internal(const bz_plan *plan) { return &plan->p; }
+}  // namespace bz
+
 namespace {
 
 void free_timing(bz::Plan &p) {
