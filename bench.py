@@ -66,7 +66,8 @@ def _flops_per_term(N):
     return {"plane_inv": 10 * n * math.log2(N) + 6 * n,
             "pencil": 10 * n * math.log2(N) + 6 * n,
             "plane_fwd": 10 * n * math.log2(N) + 6 * n,
-            "reduce": 2 * n}
+            "reduce": 2 * n,
+            "fused": 30 * n * math.log2(N) + 20 * n}
 
 
 def _bytes_per_term(N):
@@ -75,7 +76,8 @@ def _bytes_per_term(N):
     return {"plane_inv": 2 * 8 * n,      # read fhat, write S
             "pencil": 3 * 8 * n,         # read S, read h, write S
             "plane_fwd": 3 * 8 * n,      # read S, read alpha, write S
-            "reduce": 8 * n}             # read S
+            "reduce": 8 * n,             # read S
+            "fused": 2 * 8 * n}          # read alpha_p and fhat; the field stays on chip
 
 
 def _peaks():
@@ -268,9 +270,11 @@ def run_ours(args, w):
 
     # roofline of the dominant kernel
     peaks, src = _peaks()
-    dom = max(("plane_inv", "pencil", "plane_fwd", "reduce"), key=lambda k: kern[k][1])
+    dom = max(("plane_inv", "pencil", "plane_fwd", "reduce", "fused"), key=lambda k: kern[k][1])
     n_launch, ms_k = kern[dom]
     terms_per_launch = (w["N_rho"] * w["M"]) * evals_per_step * args.steps / max(n_launch, 1)
+    if dom == "reduce" and kern["fused"][0] > 0:
+        terms_per_launch = 0.0            # the partial-sum reduction is not a per-term kernel
     avg_s = ms_k / 1e3 / max(n_launch, 1)
     fl = _flops_per_term(N)[dom] * terms_per_launch
     by = _bytes_per_term(N)[dom] * terms_per_launch

@@ -58,6 +58,12 @@ enum { BZ_KERNEL_FAMILY = 0, BZ_KERNEL_B5 = 1, BZ_KERNEL_B8 = 2 };
 
 enum { BZ_PREC_FP32 = 0 };
 
+/* Collide pipelines.  FUSED: one thread-block cluster per term keeps the whole field in
+ * (distributed) shared memory from twiddle to weighted accumulation (N <= 32).  CHUNKED:
+ * four kernels per chunk of terms over an L2-sized scratch buffer (every N).  AUTO picks
+ * FUSED where it applies. */
+enum { BZ_PIPE_AUTO = 0, BZ_PIPE_FUSED = 1, BZ_PIPE_CHUNKED = 2 };
+
 typedef struct bz_plan bz_plan;
 
 typedef struct {
@@ -74,6 +80,7 @@ typedef struct {
     const double *sphere_xyz;  /* optional host array [M][3] of unit vectors, or NULL  */
     const double *sphere_w;    /* optional host array [M] of weights (sum 4 pi)         */
     int chunk_terms;  /* terms per pipeline chunk; <= 0 selects automatically          */
+    int pipeline;     /* BZ_PIPE_*; BZ_ERR_UNSUPPORTED if FUSED cannot run for this N     */
 } bz_plan_desc;
 
 /* Creates a plan: quadrature terms, the FP64 F table (computed on the device, stored
@@ -153,7 +160,8 @@ bz_status bz_collide_noalloc(const bz_plan *plan, const void *fhat, void *Qhat, 
                              void *stream);
 
 /* Kernel kinds reported by bz_plan_timing. */
-enum { BZ_K_PLANE_INV = 0, BZ_K_PENCIL = 1, BZ_K_PLANE_FWD = 2, BZ_K_REDUCE = 3, BZ_K_OTHER = 4 };
+enum { BZ_K_PLANE_INV = 0, BZ_K_PENCIL = 1, BZ_K_PLANE_FWD = 2, BZ_K_REDUCE = 3, BZ_K_OTHER = 4,
+       BZ_K_FUSED = 5 };
 
 /* Per-kernel timing.  With max_launches > 0, the next max_launches pipeline launches of
  * this plan are each bracketed by a pair of CUDA events recorded on the launch stream

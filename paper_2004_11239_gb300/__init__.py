@@ -29,6 +29,7 @@ _LIB_PATH = os.path.join(_HERE, "_lib", "libbz.so")
 BZ_C64, BZ_C128 = 0, 1
 BZ_KERNEL_FAMILY, BZ_KERNEL_B5, BZ_KERNEL_B8 = 0, 1, 2
 BZ_PREC_FP32 = 0
+BZ_PIPE_AUTO, BZ_PIPE_FUSED, BZ_PIPE_CHUNKED = 0, 1, 2
 _STATUS = {0: "BZ_OK", 1: "BZ_ERR_ARG", 2: "BZ_ERR_OOM", 3: "BZ_ERR_CUDA", 4: "BZ_ERR_TIMEOUT",
            5: "BZ_ERR_NONFINITE", 6: "BZ_ERR_BUSY", 7: "BZ_ERR_UNSUPPORTED"}
 
@@ -44,7 +45,8 @@ class bz_plan_desc(ctypes.Structure):
                 ("gamma", ctypes.c_double), ("s", ctypes.c_double), ("N_rho", ctypes.c_int),
                 ("M", ctypes.c_int), ("kernel", ctypes.c_int), ("precision", ctypes.c_int),
                 ("eps", ctypes.c_double), ("sphere_xyz", ctypes.POINTER(ctypes.c_double)),
-                ("sphere_w", ctypes.POINTER(ctypes.c_double)), ("chunk_terms", ctypes.c_int)]
+                ("sphere_w", ctypes.POINTER(ctypes.c_double)), ("chunk_terms", ctypes.c_int),
+                ("pipeline", ctypes.c_int)]
 
 
 def library_path() -> str:
@@ -156,10 +158,11 @@ def bz_plan_create(N: int, L: float, R: float, gamma: float, s: float, N_rho: in
 
 def bz_plan_create_ex(N: int, L: float, R: float, gamma: float, s: float, N_rho: int, M: int,
                       kernel: int = BZ_KERNEL_FAMILY, eps: float = 0.0, sphere=None,
-                      chunk_terms: int = 0) -> Plan:
+                      chunk_terms: int = 0, pipeline: int = BZ_PIPE_AUTO) -> Plan:
     d = bz_plan_desc()
     d.N, d.L, d.R, d.gamma, d.s, d.N_rho, d.M = N, L, R, gamma, s, N_rho, M
     d.kernel, d.precision, d.eps, d.chunk_terms = kernel, BZ_PREC_FP32, eps, chunk_terms
+    d.pipeline = pipeline
     keep = []
     if sphere is not None:
         import numpy as np
@@ -255,7 +258,7 @@ def bz_plan_last_launches(plan: Plan) -> int:
 
 
 BZ_K_PLANE_INV, BZ_K_PENCIL, BZ_K_PLANE_FWD, BZ_K_REDUCE, BZ_K_OTHER = range(5)
-KERNEL_KINDS = {"plane_inv": 0, "pencil": 1, "plane_fwd": 2, "reduce": 3, "other": 4}
+KERNEL_KINDS = {"plane_inv": 0, "pencil": 1, "plane_fwd": 2, "reduce": 3, "other": 4, "fused": 5}
 
 
 def bz_plan_set_timing(plan: Plan, max_launches: int):

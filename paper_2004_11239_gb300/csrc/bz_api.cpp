@@ -28,7 +28,8 @@ void free_plan(bz::Plan &p) {
     free_timing(p);
     cudaFree(p.alpha); cudaFree(p.tw); cudaFree(p.rule_buf); cudaFree(p.rule_off);
     cudaFree(p.term_dev); cudaFree(p.S); cudaFree(p.h); cudaFree(p.fin); cudaFree(p.acc);
-    cudaFree(p.rk); cudaFree(p.mom);
+    cudaFree(p.rk); cudaFree(p.mom); cudaFree(p.part);
+    p.part = nullptr;
     p.alpha = nullptr; p.tw = nullptr; p.rule_buf = nullptr; p.rule_off = nullptr;
     p.term_dev = nullptr; p.S = nullptr; p.h = nullptr; p.fin = nullptr; p.acc = nullptr;
     p.rk = nullptr; p.mom = nullptr;
@@ -63,6 +64,7 @@ bz_status create(bz_plan **out, const bz_plan_desc *d) {
     if (!bz::supported_N(d->N) || d->N_rho < 1 || d->M < 1 || !(d->L > 0) || !(d->R > 0))
         return BZ_ERR_ARG;
     if (d->precision != BZ_PREC_FP32) return BZ_ERR_UNSUPPORTED;
+    if (d->pipeline < BZ_PIPE_AUTO || d->pipeline > BZ_PIPE_CHUNKED) return BZ_ERR_ARG;
     if (d->kernel < BZ_KERNEL_FAMILY || d->kernel > BZ_KERNEL_B8) return BZ_ERR_ARG;
     bz_plan *h = new (std::nothrow) bz_plan();
     if (!h) return BZ_ERR_OOM;
@@ -108,6 +110,23 @@ bz_status create(bz_plan **out, const bz_plan_desc *d) {
         free_plan(pl);
         delete h;
         return BZ_ERR_CUDA;
+    }
+    // pipeline: the fused cluster kernel where it applies, else the chunked kernels
+    if (d->pipeline != BZ_PIPE_CHUNKED && N <= 32) {
+        int G = 0;
+        if (bz::fused_setup(N, &G) == cudaSuccess && G > 0 &&
+            dmalloc(&pl.part, (size_t)G * field) == BZ_OK) {
+            pl.use_fused = 1;
+            pl.fused_G = G;
+            pl.ws_bytes += (size_t)G * field;
+        } else {
+            cudaGetLastError();
+        }
+    }
+    if (d->pipeline == BZ_PIPE_FUSED && !pl.use_fused) {
+        free_plan(pl);
+        delete h;
+        return BZ_ERR_UNSUPPORTED;
     }
     s = bz::ftable_build(pl);
     if (s != BZ_OK) {

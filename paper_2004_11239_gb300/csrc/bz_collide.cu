@@ -232,6 +232,7 @@ bz_status load_input(Plan &pl, const void *fhat, int dtype, cudaStream_t st, int
 
 // Q over terms [p0, p1) of the FP32 input already in pl.fin; result in pl.acc (FP64).
 bz_status collide_core(Plan &pl, int p0, int p1, cudaStream_t st, int *launches) {
+    if (pl.use_fused) return collide_fused(pl, p0, p1, st, launches);
     switch (pl.N) {
         case 8: return run_chunks<8>(pl, p0, p1, st, launches);
         case 16: return run_chunks<16>(pl, p0, p1, st, launches);

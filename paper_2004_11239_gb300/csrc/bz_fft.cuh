@@ -86,7 +86,7 @@ constexpr TwTable make_tw_table() {
     return t;
 }
 
-__constant__ TwTable c_tw = make_tw_table();
+static __constant__ TwTable c_tw = make_tw_table();
 
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }

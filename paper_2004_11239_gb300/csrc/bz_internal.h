@@ -23,14 +23,14 @@ struct HostTerms {
 };
 
 // Optional per-kernel CUDA-event timing (bz_plan_set_timing).
-enum { TK_PLANE_INV = 0, TK_PENCIL = 1, TK_PLANE_FWD = 2, TK_REDUCE = 3, TK_OTHER = 4, TK_COUNT = 5 };
+enum { TK_PLANE_INV = 0, TK_PENCIL = 1, TK_PLANE_FWD = 2, TK_REDUCE = 3, TK_OTHER = 4, TK_FUSED = 5, TK_COUNT = 6 };
 struct Timing {
     bool on = false;
     std::vector<cudaEvent_t> ev;    // pairs (start, end)
     std::vector<int> kind;          // per pair
     size_t used = 0;                // pairs recorded since the last collect
-    double ms[TK_COUNT] = {0, 0, 0, 0, 0};
-    long n[TK_COUNT] = {0, 0, 0, 0, 0};
+    double ms[TK_COUNT] = {0, 0, 0, 0, 0, 0};
+    long n[TK_COUNT] = {0, 0, 0, 0, 0, 0};
 };
 
 struct Plan {
@@ -56,6 +56,10 @@ struct Plan {
     double2 *acc = nullptr;         // [N^3] FP64 accumulator
     double2 *rk = nullptr;          // [3][N^3] RK4 state (f0, fsum) + spare
     double *mom = nullptr;          // moments scratch
+    // fused cluster pipeline (N <= 32)
+    int use_fused = 0;              // 1: bz_collide runs k_fused
+    int fused_G = 0;                // resident clusters (persistent grid)
+    float2 *part = nullptr;         // [fused_G][N^3] per-cluster partial sums
     size_t ws_bytes = 0;
     int last_launches = 0;
     Timing tm;
@@ -88,6 +92,10 @@ bz_status collide_range(Plan &pl, int p0, int p1, const void *fhat, int in_dtype
 bz_status write_output(Plan &pl, void *Qhat, int dtype, cudaStream_t st, int *launches);
 bz_status load_input(Plan &pl, const void *fhat, int dtype, cudaStream_t st, int *launches);
 bz_status collide_core(Plan &pl, int p0, int p1, cudaStream_t st, int *launches);
+
+// bz_fused.cu
+cudaError_t fused_setup(int N, int *G);
+bz_status collide_fused(Plan &pl, int p0, int p1, cudaStream_t st, int *launches);
 cudaError_t collide_set_attributes(int N);
 int supported_N(int N);
 

@@ -67,15 +67,19 @@ def test_ftable_fp64_entries_match_oracle(bz, name, s, kid):
     plan.close()
 
 
-@pytest.mark.parametrize("N,N_rho,M,gamma,name,s,kid,data", [
+CASES = [
     (8, 3, 12, -1.0, "family", 0.5, 0, "random"),
     (16, 16, 12, 0.0, "family", 0.5, 0, "c1"),        # the N = 16 single-evaluation workload
     (16, 4, 32, -1.0, "b8", 0.0, 2, "mixture"),
     (24, 4, 12, 0.0, "family", 0.25, 0, "mixture"),
     (32, 2, 32, -2.0, "family", 0.75, 0, "mixture"),
     (48, 1, 12, 0.0, "b5", 0.0, 1, "mixture"),
-])
-def test_collide_matches_oracle(bz, N, N_rho, M, gamma, name, s, kid, data):
+]
+
+
+@pytest.mark.parametrize("pipe", ["auto", "chunked"])
+@pytest.mark.parametrize("N,N_rho,M,gamma,name,s,kid,data", CASES)
+def test_collide_matches_oracle(bz, N, N_rho, M, gamma, name, s, kid, data, pipe):
     L = 10.0
     R = bi.R_from_L(L)
     if data == "random":
@@ -84,11 +88,14 @@ def test_collide_matches_oracle(bz, N, N_rho, M, gamma, name, s, kid, data):
         fhat = bi.two_maxwellians_c1(N, L)
     else:
         fhat = bi.random_mixture(N, L, seed=N)
-    plan = bz.bz_plan_create_ex(N, L, R, gamma, s, N_rho, M, kernel=kid)
+    pipeline = bz.BZ_PIPE_AUTO if pipe == "auto" else bz.BZ_PIPE_CHUNKED
+    plan = bz.bz_plan_create_ex(N, L, R, gamma, s, N_rho, M, kernel=kid, pipeline=pipeline)
     got = _gpu_collide(bz, plan, fhat)
     oplan = spectral.OraclePlan(N, L, R, gamma, kernels.Kernel(name, s), N_rho, M)
     ref = spectral.collide(oplan, fhat)
-    assert _rel(got, ref) <= TOL
+    err = _rel(got, ref)
+    print(f"N={N} P={N_rho * M} {pipe}: rel_Linf={err:.2e}")
+    assert err <= TOL
     assert got[0, 0, 0] == 0           # F(0) = 0 exactly, hence Qhat_0 = 0 (Sec. 4 remark)
     plan.close()
 
@@ -106,9 +113,10 @@ def test_collide_n64_term_subset(bz):
     plan.close()
 
 
-def test_collide_terms_ranges_add_up_and_edge_cases(bz):
+@pytest.mark.parametrize("pipeline", [0, 2])
+def test_collide_terms_ranges_add_up_and_edge_cases(bz, pipeline):
     N, L = 16, 10.0
-    plan = bz.bz_plan_create_ex(N, L, bi.R_from_L(L), 0.0, 0.5, 5, 12, chunk_terms=7)
+    plan = bz.bz_plan_create_ex(N, L, bi.R_from_L(L), 0.0, 0.5, 5, 12, chunk_terms=7, pipeline=pipeline)
     fhat = bi.random_mixture(N, L, seed=3)
     full = _gpu_collide(bz, plan, fhat)
     parts = _gpu_collide(bz, plan, fhat, 0, 13) + _gpu_collide(bz, plan, fhat, 13, plan.P)
@@ -146,10 +154,11 @@ def test_moments_match_oracle(bz):
     plan.close()
 
 
-def test_rk4_matches_oracle_trajectory(bz):
+@pytest.mark.parametrize("pipeline", [0, 2])
+def test_rk4_matches_oracle_trajectory(bz, pipeline):
     N, L = 16, bi.L_from_R(6.0)
     R = 6.0
-    plan = bz.bz_plan_create(N, L, R, 0.0, 0.5, 8, 12)
+    plan = bz.bz_plan_create_ex(N, L, R, 0.0, 0.5, 8, 12, pipeline=pipeline)
     f0 = bi.bkw_fhat(N, L, bi.bkw_K(6.5))
     f = torch.from_numpy(f0).cuda()
     t = bz.bz_step_rk(plan, f, 6.5, 0.05, 4)
