@@ -34,6 +34,10 @@ WORKLOADS = {
     "single_n16": dict(N=16, N_rho=16, M=12, gamma=0.0, s=0.5, R=None, L=10.0, dt=None,
                        data="c1", desc="single collide, N=16, N_rho=16, M=12, gamma=0, s=0.5, "
                                        "L=10, two Maxwellians at +-2 e1"),
+    "batch_4096": dict(N=None, N_rho=None, M=32, gamma=None, s=None, R=None, L=10.0, dt=0.01,
+                       data="mixtures", desc="4096 instances (3072 at N=16, 1024 at N=32), N_rho=N, "
+                       "M=32, gamma in {0,-1}, s in {0.25,0.5,0.75}, two-Maxwellian mixtures, "
+                       "one RK4 step per bench step; grouped by (N, s) into batches"),
 }
 METRIC = "Q(f,f) evals/s"
 
@@ -320,6 +324,68 @@ def run_ours(args, w):
     return 0
 
 
+def run_batch(args, w):
+    """The batched workload: 4096 independent instances in six (N, s) groups, one RK4 step each."""
+    import numpy as np
+    import torch
+    import bz_inputs as bi
+    import paper_2004_11239_gb300 as bz
+    torch.cuda.set_device(0)
+    L = w["L"]
+    R = bi.R_from_L(L)
+    u = bi.SplitMix64(2024).uniform(2 * 4096)
+    svals, gvals = [0.25, 0.5, 0.75], [0.0, -1.0]
+    groups = {}
+    for i in range(4096):
+        N = 16 if i < 3072 else 32
+        s_ = svals[int(u[2 * i] * 3)]
+        g_ = gvals[int(u[2 * i + 1] * 2)]
+        groups.setdefault((N, s_), []).append((i, g_))
+    runs = []
+    for (N, s_), members in sorted(groups.items()):
+        plan = bz.bz_plan_create(N, L, R, 0.0, s_, N, w["M"])
+        batch = bz.bz_batch_create(plan, len(members), 0)
+        for slot, (i, g_) in enumerate(members):
+            if g_ != 0.0:
+                bz.bz_batch_set_gamma(batch, slot, g_)
+        f = np.stack([bi.random_mixture(N, L, seed=i) for i, _ in members]).astype(np.complex64)
+        fd = torch.from_numpy(f).cuda()
+        runs.append((N, s_, plan, batch, fd, list(range(len(members))), torch.cuda.Stream()))
+    def step():
+        for N, s_, plan, batch, fd, slots, st in runs:
+            bz.bz_batch_step_rk(batch, slots, fd, w["dt"], 1, st)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        torch.cuda.synchronize()
+        e0.record()
+        for *_, st in runs:
+            st.wait_event(e0)
+        for _ in range(args.steps):
+            step()
+        for *_, st in runs:
+            torch.cuda.current_stream().wait_stream(st)
+        e1.record()
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    wall = time.perf_counter() - t0
+    evals = 4 * 4096 * args.steps
+    launches = sum(bz.bz_batch_last_launches(r[3]) for r in runs) * args.steps
+    line = {"metric": METRIC, "value": evals / (ms / 1e3), "unit": "evals/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": {"workload": args.workload, "desc": w["desc"],
+                                            "groups": {f"N={k[0]},s={k[1]}": len(v) for k, v in sorted(groups.items())},
+                                            "terms_per_item": {f"N={r[0]},s={r[1]}": r[3].terms_per_item for r in runs}},
+            "clocks": clk.summary(), "gpu_launches": launches, "wall_s": wall}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -330,6 +396,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
+    if args.workload == "batch_4096":
+        return run_batch(args, w)
     if args.impl == "reference":
         return run_reference(args, w)
     return run_ours(args, w)

@@ -159,6 +159,37 @@ const char *bz_status_str(bz_status s);
 bz_status bz_collide_noalloc(const bz_plan *plan, const void *fhat, void *Qhat, int dtype,
                              void *stream);
 
+/* ---------------------------------------------------------------------------------------
+ * Batches: many independent instances of one plan geometry (same N, L, R, kernel, N_rho, M
+ * and F table; gamma per instance), standing in for the cells of a spatially
+ * inhomogeneous solver.  Instance state lives in slots 0..capacity-1 of caller arrays of
+ * capacity * N^3 complex values (dtype as above); every call names its active slots
+ * (host array, distinct, in [0, capacity)), so instances can join and leave between calls.
+ * gamma enters only through c_p (eq. approxG): slot b uses alpha_p r_i^(gamma_b - gamma_plan).
+ * An instance's result does not depend on which other slots are active in the call.
+ * Requires a plan on the fused pipeline (N <= 32), else BZ_ERR_UNSUPPORTED.  The plan must
+ * outlive the batch.  Not re-entrant across streams.
+ * --------------------------------------------------------------------------------------- */
+typedef struct bz_batch bz_batch;
+
+/* terms_per_item <= 0 autotunes the number of terms per work item (timed on the device at
+ * creation).  Synchronous. */
+bz_status bz_batch_create(bz_batch **out, const bz_plan *plan, int capacity, int terms_per_item);
+void bz_batch_destroy(bz_batch *batch);
+bz_status bz_batch_info(const bz_batch *batch, int *capacity, int *terms_per_item, size_t *workspace_bytes);
+/* gamma of one slot (default: the plan's gamma).  Synchronous. */
+bz_status bz_batch_set_gamma(bz_batch *batch, int slot, double gamma);
+/* Qhat[slot] = Q(fhat[slot]) for each active slot (eq. realQ).  fhat != Qhat. */
+bz_status bz_batch_collide(bz_batch *batch, int count, const int *slots, const void *fhat, void *Qhat,
+                           int dtype, void *stream);
+/* nsteps classical RK4 steps (Sec. 5.2) of size dt on each active slot of fhat, in place.  Each
+ * step replays a CUDA graph captured on the first call with this dt (one fused launch and one
+ * stage update per RK stage). */
+bz_status bz_batch_step_rk(bz_batch *batch, int count, const int *slots, void *fhat, int dtype, double dt,
+                           int nsteps, void *stream);
+/* Kernel launches (graph nodes included) of the last batch call. */
+int bz_batch_last_launches(const bz_batch *batch);
+
 /* Kernel kinds reported by bz_plan_timing. */
 enum { BZ_K_PLANE_INV = 0, BZ_K_PENCIL = 1, BZ_K_PLANE_FWD = 2, BZ_K_REDUCE = 3, BZ_K_OTHER = 4,
        BZ_K_FUSED = 5 };

@@ -21,6 +21,8 @@ __all__ = [
     "bz_collide", "bz_collide_terms", "bz_step_rk", "bz_moments", "bz_ftable_entries",
     "bz_plan_alpha", "bz_plan_last_launches", "bz_status_str", "library_path", "lib",
     "bz_plan_set_timing", "bz_plan_timing", "bz_collide_noalloc",
+    "bz_batch_create", "bz_batch_destroy", "bz_batch_set_gamma", "bz_batch_collide", "bz_batch_step_rk",
+    "bz_batch_last_launches",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -71,6 +73,11 @@ def _load():
         "bz_ftable_entries": [vp, c_int, vp, vp, vp],
         "bz_plan_alpha": [vp, c_int, c_int, vp, vp],
         "bz_collide_noalloc": [vp, vp, vp, c_int, vp],
+        "bz_batch_create": [ctypes.POINTER(vp), vp, c_int, c_int],
+        "bz_batch_info": [vp, ip, ip, ctypes.POINTER(c_size)],
+        "bz_batch_set_gamma": [vp, c_int, c_double],
+        "bz_batch_collide": [vp, c_int, ip, vp, vp, c_int, vp],
+        "bz_batch_step_rk": [vp, c_int, ip, vp, c_int, c_double, c_int, vp],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -80,6 +87,10 @@ def _load():
     L.bz_plan_set_timing.restype = c_int
     L.bz_plan_timing.argtypes = [vp, c_int, ctypes.POINTER(ctypes.c_long), dp]
     L.bz_plan_timing.restype = c_int
+    L.bz_batch_destroy.argtypes = [vp]
+    L.bz_batch_destroy.restype = None
+    L.bz_batch_last_launches.argtypes = [vp]
+    L.bz_batch_last_launches.restype = c_int
     L.bz_plan_destroy.argtypes = [vp]
     L.bz_plan_destroy.restype = None
     L.bz_plan_last_launches.argtypes = [vp]
@@ -271,6 +282,74 @@ def bz_plan_timing(plan: Plan, kind: int):
     ms = ctypes.c_double()
     _check(lib.bz_plan_timing(plan.handle, kind, ctypes.byref(n), ctypes.byref(ms)), "bz_plan_timing")
     return n.value, ms.value
+
+
+class Batch:
+    """Owning handle of a bz_batch (keeps its plan alive)."""
+
+    def __init__(self, handle, plan: Plan):
+        self.handle = handle
+        self.plan = plan
+        cap, tb = ctypes.c_int(), ctypes.c_int()
+        wb = ctypes.c_size_t()
+        _check(lib.bz_batch_info(handle, ctypes.byref(cap), ctypes.byref(tb), ctypes.byref(wb)), "bz_batch_info")
+        self.capacity, self.terms_per_item, self.workspace_bytes = cap.value, tb.value, wb.value
+
+    def close(self):
+        if self.handle:
+            lib.bz_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _slots(slots):
+    arr = (ctypes.c_int * len(slots))(*[int(x) for x in slots])
+    return len(slots), arr
+
+
+def bz_batch_create(plan: Plan, capacity: int, terms_per_item: int = 0) -> Batch:
+    h = ctypes.c_void_p()
+    _check(lib.bz_batch_create(ctypes.byref(h), plan.handle, capacity, terms_per_item), "bz_batch_create")
+    return Batch(h, plan)
+
+
+def bz_batch_destroy(batch: Batch):
+    batch.close()
+
+
+def bz_batch_set_gamma(batch: Batch, slot: int, gamma: float):
+    _check(lib.bz_batch_set_gamma(batch.handle, slot, gamma), "bz_batch_set_gamma")
+
+
+def _dev_batch(t, batch: Batch):
+    n = batch.capacity * batch.plan.n3
+    if not t.is_cuda or not t.is_contiguous() or t.numel() != n:
+        raise ValueError("expected a contiguous CUDA tensor of capacity * N^3 complex values")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def bz_batch_collide(batch: Batch, slots, fhat, Qhat, stream=None):
+    n, arr = _slots(slots)
+    dt = _dtype(fhat)
+    if _dtype(Qhat) != dt:
+        raise TypeError("fhat and Qhat must have the same dtype")
+    _check(lib.bz_batch_collide(batch.handle, n, arr, _dev_batch(fhat, batch), _dev_batch(Qhat, batch), dt,
+                                _stream(stream)), "bz_batch_collide")
+
+
+def bz_batch_step_rk(batch: Batch, slots, fhat, dt: float, nsteps: int, stream=None):
+    n, arr = _slots(slots)
+    _check(lib.bz_batch_step_rk(batch.handle, n, arr, _dev_batch(fhat, batch), _dtype(fhat), dt, nsteps,
+                                _stream(stream)), "bz_batch_step_rk")
+
+
+def bz_batch_last_launches(batch: Batch) -> int:
+    return lib.bz_batch_last_launches(batch.handle)
 
 
 def bz_status_str(code: int) -> str:

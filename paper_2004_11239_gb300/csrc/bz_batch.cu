@@ -1,0 +1,366 @@
+// Batched collides and RK4 over many independent instances of one plan geometry.
+//
+// Instances stand in for the spatial cells of an inhomogeneous solver: same N, L, R,
+// kernel, N_rho, M (one F table), a gamma of their own.  gamma enters only through
+// c_p = w_i w_j r_i^(gamma + 2), so instance b scales the plan's alpha_p by
+// r_i^(gamma_b - gamma_plan), a per-radial-node factor applied in the accumulation.
+//
+// State lives in slots [0, capacity); each call names the active slots, so instances can
+// join and leave between steps (continuous batching).  The fused item kernel processes
+// (instance, block of TB terms) items; an instance's result is the fixed-order FP64 sum of
+// its block partials, independent of the other instances in the call.  One RK4 step
+// (4 x [fused items, stage update]) is captured once per dt into a CUDA graph and replayed;
+// the active count and slot list are read from device memory at run time.
+#include <cmath>
+#include <map>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "bz_internal.h"
+
+struct bz_plan;
+
+namespace bz {
+const Plan *plan_internal(const bz_plan *plan);
+}
+
+struct bz_batch {
+    bz::Plan *pl = nullptr;
+    int capacity = 0, TB = 0, nblk = 0;
+    std::vector<double> gamma;
+    float *gsc = nullptr;           // [capacity][N_rho]
+    float2 *fin = nullptr;          // [capacity][N^3]
+    float2 *part = nullptr;         // [capacity][nblk][N^3]
+    double2 *f0 = nullptr, *fsum = nullptr;   // [capacity][N^3]
+    int *slots_dev = nullptr;       // [capacity]
+    int *count_dev = nullptr;       // [1]
+    int *host_stage = nullptr;      // pinned [capacity + 1]
+    cudaStream_t cap_stream = nullptr;
+    std::map<double, cudaGraphExec_t> graphs;
+    int last_launches = 0;
+};
+
+namespace bz {
+namespace {
+
+__global__ void k_batch_load(const void *fhat, int dtype, const int *slots, const int *count_dev, int n3,
+                             float2 *fin) {
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int b = (int)(e / n3), k = (int)(e % n3);
+    if (b >= *count_dev) return;
+    const size_t idx = (size_t)slots[b] * n3 + k;
+    if (dtype == BZ_C128) {
+        double2 v = ((const double2 *)fhat)[idx];
+        fin[idx] = make_float2((float)v.x, (float)v.y);
+    } else {
+        fin[idx] = ((const float2 *)fhat)[idx];
+    }
+}
+
+__device__ __forceinline__ double2 sum_blocks(const float2 *part, int slot, int nblk, int n3, int k) {
+    double sr = 0.0, si = 0.0;
+    const float2 *p = part + (size_t)slot * nblk * n3 + k;
+    for (int blk = 0; blk < nblk; ++blk) {
+        float2 v = p[(size_t)blk * n3];
+        sr += v.x;
+        si += v.y;
+    }
+    return make_double2(sr, si);
+}
+
+__global__ void k_batch_out(const float2 *part, int nblk, const int *slots, const int *count_dev, int n3,
+                            void *Qhat, int dtype) {
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int b = (int)(e / n3), k = (int)(e % n3);
+    if (b >= *count_dev) return;
+    const int slot = slots[b];
+    double2 q = sum_blocks(part, slot, nblk, n3, k);
+    const size_t idx = (size_t)slot * n3 + k;
+    if (dtype == BZ_C128) ((double2 *)Qhat)[idx] = q;
+    else ((float2 *)Qhat)[idx] = make_float2((float)q.x, (float)q.y);
+}
+
+__global__ void k_batch_rk_init(const void *fhat, int dtype, const int *slots, const int *count_dev, int n3,
+                                double2 *f0, float2 *fin) {
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int b = (int)(e / n3), k = (int)(e % n3);
+    if (b >= *count_dev) return;
+    const size_t idx = (size_t)slots[b] * n3 + k;
+    double2 v;
+    if (dtype == BZ_C128) v = ((const double2 *)fhat)[idx];
+    else {
+        float2 w = ((const float2 *)fhat)[idx];
+        v = make_double2(w.x, w.y);
+    }
+    f0[idx] = v;
+    fin[idx] = make_float2((float)v.x, (float)v.y);
+}
+
+// Stage s of RK4 (the same combination as the single-instance path), k_s from the partials.
+__global__ void k_batch_rk_stage(const float2 *part, int nblk, const int *slots, const int *count_dev, int n3,
+                                 double2 *f0, double2 *fsum, float2 *fin, int stage, double dt) {
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int b = (int)(e / n3), k = (int)(e % n3);
+    if (b >= *count_dev) return;
+    const int slot = slots[b];
+    const size_t idx = (size_t)slot * n3 + k;
+    const double2 kv = sum_blocks(part, slot, nblk, n3, k);
+    const double2 a = f0[idx];
+    double2 y;
+    if (stage == 1) {
+        fsum[idx] = make_double2(a.x + dt / 6.0 * kv.x, a.y + dt / 6.0 * kv.y);
+        y = make_double2(a.x + 0.5 * dt * kv.x, a.y + 0.5 * dt * kv.y);
+    } else if (stage == 2 || stage == 3) {
+        double2 s = fsum[idx];
+        fsum[idx] = make_double2(s.x + dt / 3.0 * kv.x, s.y + dt / 3.0 * kv.y);
+        const double c = stage == 2 ? 0.5 * dt : dt;
+        y = make_double2(a.x + c * kv.x, a.y + c * kv.y);
+    } else {
+        double2 s = fsum[idx];
+        y = make_double2(s.x + dt / 6.0 * kv.x, s.y + dt / 6.0 * kv.y);
+        f0[idx] = y;
+    }
+    fin[idx] = make_float2((float)y.x, (float)y.y);
+}
+
+__global__ void k_batch_rk_out(const double2 *f0, const int *slots, const int *count_dev, int n3, void *fhat,
+                               int dtype) {
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int b = (int)(e / n3), k = (int)(e % n3);
+    if (b >= *count_dev) return;
+    const size_t idx = (size_t)slots[b] * n3 + k;
+    if (dtype == BZ_C128) ((double2 *)fhat)[idx] = f0[idx];
+    else ((float2 *)fhat)[idx] = make_float2((float)f0[idx].x, (float)f0[idx].y);
+}
+
+ItemArgs item_args(const bz_batch &B) {
+    const Plan &pl = *B.pl;
+    ItemArgs a;
+    a.fin = B.fin; a.tw = pl.tw; a.alpha = pl.alpha; a.gsc = B.gsc; a.part = B.part;
+    a.slots = B.slots_dev; a.count_dev = B.count_dev; a.count = 0;
+    a.p0 = 0; a.p1 = pl.P; a.TB = B.TB; a.nblk = B.nblk; a.M = pl.M; a.N_rho = pl.N_rho;
+    return a;
+}
+
+unsigned grid_for(const bz_batch &B) {
+    const size_t n = (size_t)B.capacity * B.pl->N * B.pl->N * B.pl->N;
+    return (unsigned)((n + 255) / 256);
+}
+
+bz_status stage_slots(bz_batch &B, int count, const int *slots, cudaStream_t st) {
+    if (count < 0 || count > B.capacity || (count > 0 && !slots)) return BZ_ERR_ARG;
+    std::vector<char> seen(B.capacity, 0);
+    for (int b = 0; b < count; ++b) {
+        if (slots[b] < 0 || slots[b] >= B.capacity || seen[slots[b]]) return BZ_ERR_ARG;
+        seen[slots[b]] = 1;
+    }
+    // the pinned staging buffer may still feed an earlier copy on this stream
+    if (cudaStreamSynchronize(st) != cudaSuccess) return BZ_ERR_CUDA;
+    B.host_stage[0] = count;
+    for (int b = 0; b < count; ++b) B.host_stage[1 + b] = slots[b];
+    BZ_CUDA_TRY(cudaMemcpyAsync(B.count_dev, B.host_stage, sizeof(int), cudaMemcpyHostToDevice, st));
+    if (count > 0)
+        BZ_CUDA_TRY(cudaMemcpyAsync(B.slots_dev, B.host_stage + 1, count * sizeof(int), cudaMemcpyHostToDevice, st));
+    return BZ_OK;
+}
+
+void free_batch(bz_batch *B) {
+    for (auto &g : B->graphs) cudaGraphExecDestroy(g.second);
+    B->graphs.clear();
+    cudaFree(B->gsc); cudaFree(B->fin); cudaFree(B->part); cudaFree(B->f0); cudaFree(B->fsum);
+    cudaFree(B->slots_dev); cudaFree(B->count_dev);
+    if (B->host_stage) cudaFreeHost(B->host_stage);
+    if (B->cap_stream) cudaStreamDestroy(B->cap_stream);
+}
+
+bz_status upload_gsc(bz_batch &B) {
+    const Plan &pl = *B.pl;
+    std::vector<float> g((size_t)B.capacity * pl.N_rho);
+    for (int b = 0; b < B.capacity; ++b)
+        for (int i = 0; i < pl.N_rho; ++i)
+            g[(size_t)b * pl.N_rho + i] = (float)std::pow(pl.terms.r[(size_t)i * pl.M], B.gamma[b] - pl.gamma);
+    BZ_CUDA_TRY(cudaMemcpy(B.gsc, g.data(), g.size() * sizeof(float), cudaMemcpyHostToDevice));
+    return BZ_OK;
+}
+
+// Picks the terms per item: times one full batched collide of `trial` zero instances for each
+// candidate and keeps the fastest.  part must hold trial * ceil(P / min candidate) fields.
+int autotune_tb(bz_batch &B, int trial, cudaStream_t st) {
+    const Plan &pl = *B.pl;
+    const int cands[] = {16, 32, 64, 128, 256, 512};
+    int best = -1;
+    float best_ms = 1e30f;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    std::vector<int> slots(trial);
+    for (int b = 0; b < trial; ++b) slots[b] = b;
+    stage_slots(B, trial, slots.data(), st);
+    for (int tb : cands) {
+        if (tb > pl.P && best > 0) break;
+        B.TB = tb < pl.P ? tb : pl.P;
+        B.nblk = (pl.P + B.TB - 1) / B.TB;
+        ItemArgs a = item_args(B);
+        launch_fused(pl, a, st);                      // warm-up
+        cudaEventRecord(e0, st);
+        launch_fused(pl, a, st);
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) { best_ms = ms; best = B.TB; }
+        if (B.TB == pl.P) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaGetLastError();
+    return best;
+}
+
+}  // namespace
+}  // namespace bz
+
+using namespace bz;
+
+extern "C" {
+
+bz_status bz_batch_create(bz_batch **out, const bz_plan *plan, int capacity, int terms_per_item) {
+    if (!out || !plan || capacity < 1) return BZ_ERR_ARG;
+    *out = nullptr;
+    Plan *pl = const_cast<Plan *>(plan_internal(plan));
+    if (!pl->use_fused) return BZ_ERR_UNSUPPORTED;       // batches run on the fused kernel (N <= 32)
+    bz_batch *B = new (std::nothrow) bz_batch();
+    if (!B) return BZ_ERR_OOM;
+    B->pl = pl;
+    B->capacity = capacity;
+    B->gamma.assign(capacity, pl->gamma);
+    const size_t n3 = (size_t)pl->N * pl->N * pl->N;
+    const size_t field = n3 * sizeof(float2);
+    auto fail = [&](bz_status s) { free_batch(B); delete B; return s; };
+    if (cudaMalloc(&B->gsc, (size_t)capacity * pl->N_rho * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&B->fin, (size_t)capacity * field) != cudaSuccess ||
+        cudaMalloc(&B->f0, (size_t)capacity * n3 * sizeof(double2)) != cudaSuccess ||
+        cudaMalloc(&B->fsum, (size_t)capacity * n3 * sizeof(double2)) != cudaSuccess ||
+        cudaMalloc(&B->slots_dev, (size_t)capacity * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&B->count_dev, sizeof(int)) != cudaSuccess ||
+        cudaMallocHost(&B->host_stage, (size_t)(capacity + 1) * sizeof(int)) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&B->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(BZ_ERR_OOM);
+    }
+    if (upload_gsc(*B) != BZ_OK) return fail(BZ_ERR_CUDA);
+    int tb = terms_per_item;
+    if (tb <= 0) {
+        // autotune on a trial of up to 4 instances per resident cluster
+        int trial = capacity < 4 * pl->fused_G ? capacity : 4 * pl->fused_G;
+        int nblk_max = (pl->P + 15) / 16;
+        if (cudaMalloc(&B->part, (size_t)trial * nblk_max * field) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(BZ_ERR_OOM);
+        }
+        if (cudaMemset(B->fin, 0, (size_t)trial * field) != cudaSuccess) return fail(BZ_ERR_CUDA);
+        tb = autotune_tb(*B, trial, B->cap_stream);
+        cudaStreamSynchronize(B->cap_stream);
+        cudaFree(B->part);
+        B->part = nullptr;
+        if (tb <= 0) return fail(BZ_ERR_CUDA);
+    }
+    B->TB = tb < pl->P ? tb : pl->P;
+    B->nblk = (pl->P + B->TB - 1) / B->TB;
+    if (cudaMalloc(&B->part, (size_t)capacity * B->nblk * field) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(BZ_ERR_OOM);
+    }
+    *out = B;
+    return BZ_OK;
+}
+
+bz_status bz_batch_set_gamma(bz_batch *batch, int slot, double gamma) {
+    if (!batch || slot < 0 || slot >= batch->capacity || !std::isfinite(gamma)) return BZ_ERR_ARG;
+    batch->gamma[slot] = gamma;
+    const Plan &pl = *batch->pl;
+    std::vector<float> g(pl.N_rho);
+    for (int i = 0; i < pl.N_rho; ++i) g[i] = (float)std::pow(pl.terms.r[(size_t)i * pl.M], gamma - pl.gamma);
+    BZ_CUDA_TRY(cudaMemcpy(batch->gsc + (size_t)slot * pl.N_rho, g.data(), g.size() * sizeof(float),
+                           cudaMemcpyHostToDevice));
+    return BZ_OK;
+}
+
+bz_status bz_batch_info(const bz_batch *batch, int *capacity, int *terms_per_item, size_t *workspace_bytes) {
+    if (!batch) return BZ_ERR_ARG;
+    const size_t n3 = (size_t)batch->pl->N * batch->pl->N * batch->pl->N;
+    if (capacity) *capacity = batch->capacity;
+    if (terms_per_item) *terms_per_item = batch->TB;
+    if (workspace_bytes)
+        *workspace_bytes = (size_t)batch->capacity * n3 * (sizeof(float2) * (1 + batch->nblk) + 2 * sizeof(double2));
+    return BZ_OK;
+}
+
+bz_status bz_batch_collide(bz_batch *batch, int count, const int *slots, const void *fhat, void *Qhat, int dtype,
+                           void *stream) {
+    if (!batch || !fhat || !Qhat || fhat == Qhat) return BZ_ERR_ARG;
+    if (dtype != BZ_C64 && dtype != BZ_C128) return BZ_ERR_ARG;
+    bz_batch &B = *batch;
+    cudaStream_t st = (cudaStream_t)stream;
+    bz_status s = stage_slots(B, count, slots, st);
+    if (s != BZ_OK) return s;
+    const int n3 = B.pl->N * B.pl->N * B.pl->N;
+    k_batch_load<<<grid_for(B), 256, 0, st>>>(fhat, dtype, B.slots_dev, B.count_dev, n3, B.fin);
+    s = launch_fused(*B.pl, item_args(B), st);
+    if (s != BZ_OK) return s;
+    k_batch_out<<<grid_for(B), 256, 0, st>>>(B.part, B.nblk, B.slots_dev, B.count_dev, n3, Qhat, dtype);
+    BZ_CUDA_TRY(cudaGetLastError());
+    B.last_launches = 3;
+    return BZ_OK;
+}
+
+bz_status bz_batch_step_rk(bz_batch *batch, int count, const int *slots, void *fhat, int dtype, double dt,
+                           int nsteps, void *stream) {
+    if (!batch || !fhat || nsteps < 0 || !std::isfinite(dt)) return BZ_ERR_ARG;
+    if (dtype != BZ_C64 && dtype != BZ_C128) return BZ_ERR_ARG;
+    bz_batch &B = *batch;
+    cudaStream_t st = (cudaStream_t)stream;
+    bz_status s = stage_slots(B, count, slots, st);
+    if (s != BZ_OK) return s;
+    const int n3 = B.pl->N * B.pl->N * B.pl->N;
+    auto it = B.graphs.find(dt);
+    if (it == B.graphs.end()) {
+        // capture one RK4 step: 4 x (fused items, stage update)
+        cudaGraph_t g = nullptr;
+        BZ_CUDA_TRY(cudaStreamBeginCapture(B.cap_stream, cudaStreamCaptureModeThreadLocal));
+        bz_status cs = BZ_OK;
+        for (int stage = 1; stage <= 4 && cs == BZ_OK; ++stage) {
+            cs = launch_fused(*B.pl, item_args(B), B.cap_stream);
+            k_batch_rk_stage<<<grid_for(B), 256, 0, B.cap_stream>>>(B.part, B.nblk, B.slots_dev, B.count_dev, n3,
+                                                                   B.f0, B.fsum, B.fin, stage, dt);
+        }
+        cudaError_t ce = cudaStreamEndCapture(B.cap_stream, &g);
+        if (cs != BZ_OK || ce != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            return cs != BZ_OK ? cs : BZ_ERR_CUDA;
+        }
+        cudaGraphExec_t ex = nullptr;
+        ce = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        if (ce != cudaSuccess) return BZ_ERR_CUDA;
+        it = B.graphs.emplace(dt, ex).first;
+    }
+    k_batch_rk_init<<<grid_for(B), 256, 0, st>>>(fhat, dtype, B.slots_dev, B.count_dev, n3, B.f0, B.fin);
+    for (int step = 0; step < nsteps; ++step) BZ_CUDA_TRY(cudaGraphLaunch(it->second, st));
+    k_batch_rk_out<<<grid_for(B), 256, 0, st>>>(B.f0, B.slots_dev, B.count_dev, n3, fhat, dtype);
+    BZ_CUDA_TRY(cudaGetLastError());
+    B.last_launches = 2 + 8 * nsteps;
+    return BZ_OK;
+}
+
+int bz_batch_last_launches(const bz_batch *batch) { return batch ? batch->last_launches : 0; }
+
+void bz_batch_destroy(bz_batch *batch) {
+    if (!batch) return;
+    free_batch(batch);
+    delete batch;
+}
+
+}  // extern "C"

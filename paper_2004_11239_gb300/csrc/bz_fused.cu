@@ -100,10 +100,13 @@ __device__ __forceinline__ void phase_a(const float2 *__restrict__ fin, const fl
     for (int j = 0; j < N; ++j) my[lane * LD + j] = x[j];
 }
 
-template <int N>
+// Work item w: instance b = w / nblk (array slot slots[b]), term block blk = w % nblk covering
+// terms [p0 + blk TB, min(p1, p0 + (blk + 1) TB)).  The item's FP32 sum over its terms goes to
+// part[slot * nblk + blk]; it depends only on the instance and the block bounds, so a result
+// does not depend on which other instances share the launch.
+template <int N, bool SCALED>
 __global__ void __launch_bounds__(FK<N>::THREADS, FK<N>::MIN_BLOCKS)
-k_fused(const float2 *__restrict__ fin, const float2 *__restrict__ tw, const float2 *__restrict__ alpha,
-        float2 *__restrict__ part, int p0, int p1) {
+k_fused(ItemArgs a) {
     using K = FK<N>;
     constexpr int C = K::C, PPC = K::PPC, LD = K::LD, T = K::THREADS;
     extern __shared__ __align__(16) float2 smem[];
@@ -119,84 +122,101 @@ k_fused(const float2 *__restrict__ fin, const float2 *__restrict__ tw, const flo
     const int k1 = rank * PPC + pid;                         // plane phases
     const int j2p = rank * PPC + pid;                        // pencil phase: (j2p, lane)
     float2 *my = planes + (size_t)pid * N * LD;
-    // shared::cluster address of element (plane lp, row j2p, column lane) in each CTA
-    uint32_t pen[C];
+    constexpr size_t N3 = (size_t)N * N * N;
+    uint32_t pen[C];                                         // element (j2p, lane) of plane 0 in each CTA
     #pragma unroll
     for (int r = 0; r < C; ++r) pen[r] = dsmem_addr(planes + (size_t)j2p * LD + lane, (uint32_t)r);
     constexpr uint32_t PLANE_BYTES = (uint32_t)(N * LD * sizeof(float2));
 
+    const int count = a.count_dev ? *a.count_dev : a.count;
+    const int nitems = count * a.nblk;
     auto fetch_tw = [&](int p, int buf) {                    // one term's 3N twiddles, 16 B per copy
-        if (p < p1 && tid < (int)(K::TW / 16))
-            cp_async16((char *)(stw + buf * 3 * N) + 16 * tid, (const char *)(tw + (size_t)p * 3 * N) + 16 * tid);
+        if (p >= 0 && tid < (int)(K::TW / 16))
+            cp_async16((char *)(stw + buf * 3 * N) + 16 * tid, (const char *)(a.tw + (size_t)p * 3 * N) + 16 * tid);
         cp_async_commit();
     };
 
-    // prologue: h = IFFT(fhat) for the pencils this CTA owns, straight into the h slice
-    fetch_tw(p0 + cid, 0);
-    phase_a<N>(fin, nullptr, my, k1, lane);
-    cluster_barrier<C>();
-    {
-        float2 x[N];
-        #pragma unroll
-        for (int k = 0; k < N; ++k) x[k] = ld_dsmem(pen[k / PPC] + (uint32_t)(k % PPC) * PLANE_BYTES);
-        fft_inplace<N, +1>(x);                                // k1 -> j1
-        #pragma unroll
-        for (int j = 0; j < N; ++j) shs[((size_t)pid * N + j) * N + lane] = x[j];
-    }
-    cluster_barrier<C>();                                     // planes free again in every CTA
-
-    float2 acc[N];
-    #pragma unroll
-    for (int i = 0; i < N; ++i) acc[i] = make_float2(0.f, 0.f);
-
-    int it = 0;
-    for (int p = p0 + cid; p < p1; p += ncl, ++it) {
-        const int buf = it & 1;
-        cp_async_wait_all();                                  // this term's twiddles have landed
-        __syncthreads();                                      // ... for every thread; last term done
+    for (int w = cid; w < nitems; w += ncl) {
+        const int b = w / a.nblk, blk = w % a.nblk;
+        const int slot = a.slots ? a.slots[b] : b;
+        const int t0 = a.p0 + blk * a.TB;
+        const int t1 = min(a.p1, t0 + a.TB);
+        const float2 *fin = a.fin + (size_t)slot * N3;
+        // prologue: h = IFFT(fhat_b) for the pencils this CTA owns, into the h slice
+        __syncthreads();                                      // the previous item is done with smem
+        fetch_tw(t0, 0);
+        phase_a<N>(fin, nullptr, my, k1, lane);
+        cluster_barrier<C>();
         {
-            const char *ga = (const char *)(alpha + ((size_t)p * N + (size_t)rank * PPC) * N * N);
-            char *sa = (char *)sal;
-            for (int c = tid; c < (int)(K::TILE / 16); c += T) cp_async16(sa + 16 * c, ga + 16 * c);
-            cp_async_commit();
+            float2 x[N];
+            #pragma unroll
+            for (int k = 0; k < N; ++k) x[k] = ld_dsmem(pen[k / PPC] + (uint32_t)(k % PPC) * PLANE_BYTES);
+            fft_inplace<N, +1>(x);                            // k1 -> j1
+            #pragma unroll
+            for (int j = 0; j < N; ++j) shs[((size_t)pid * N + j) * N + lane] = x[j];
         }
-        fetch_tw(p + ncl, buf ^ 1);
-        // A
-        phase_a<N>(fin, stw + buf * 3 * N, my, k1, lane);
-        cluster_barrier<C>();
-        // B: pencil (j2p, lane) over k1, gathered from the cluster
-        float2 x[N];
+        cluster_barrier<C>();                                 // planes free again in every CTA
+
+        float2 acc[N];
         #pragma unroll
-        for (int k = 0; k < N; ++k) x[k] = ld_dsmem(pen[k / PPC] + (uint32_t)(k % PPC) * PLANE_BYTES);
-        fft_inplace<N, +1>(x);                                // k1 -> j1
-        #pragma unroll
-        for (int j = 0; j < N; ++j) x[j] = cmul(x[j], shs[((size_t)pid * N + j) * N + lane]);
-        fft_inplace<N, -1>(x);                                // j1 -> k1
-        #pragma unroll
-        for (int k = 0; k < N; ++k) st_dsmem(pen[k / PPC] + (uint32_t)(k % PPC) * PLANE_BYTES, x[k]);
-        cluster_barrier<C>();
-        // C: rows over j3, then column k3 = lane over j2, times alpha, accumulate
-        #pragma unroll
-        for (int j = 0; j < N; ++j) x[j] = my[lane * LD + j];
-        fft_inplace<N, -1>(x);                                // j3 -> k3 (row j2 = lane)
-        #pragma unroll
-        for (int j = 0; j < N; ++j) my[lane * LD + j] = x[j];
-        cp_async_wait_1();                                    // alpha tile (the next twiddles may pend)
-        __syncthreads();
-        #pragma unroll
-        for (int i = 0; i < N; ++i) x[i] = my[i * LD + lane];
-        fft_inplace<N, -1>(x);                                // j2 -> k2
-        #pragma unroll
-        for (int i = 0; i < N; ++i) {
-            float2 a = sal[((size_t)pid * N + i) * N + lane];
-            acc[i].x = fmaf(x[i].x, a.x, fmaf(-x[i].y, a.y, acc[i].x));
-            acc[i].y = fmaf(x[i].x, a.y, fmaf(x[i].y, a.x, acc[i].y));
+        for (int i = 0; i < N; ++i) acc[i] = make_float2(0.f, 0.f);
+        int it = 0;
+        for (int p = t0; p < t1; ++p, ++it) {
+            const int buf = it & 1;
+            cp_async_wait_all();                              // this term's twiddles have landed
+            __syncthreads();                                  // ... for every thread; last term done
+            {
+                const char *ga = (const char *)(a.alpha + ((size_t)p * N + (size_t)rank * PPC) * N * N);
+                char *sa = (char *)sal;
+                for (int c = tid; c < (int)(K::TILE / 16); c += T) cp_async16(sa + 16 * c, ga + 16 * c);
+                cp_async_commit();
+            }
+            fetch_tw(p + 1 < t1 ? p + 1 : -1, buf ^ 1);
+            float sc = 1.f;
+            if constexpr (SCALED) sc = a.gsc[(size_t)slot * a.N_rho + p / a.M];
+            // A
+            phase_a<N>(fin, stw + buf * 3 * N, my, k1, lane);
+            cluster_barrier<C>();
+            // B: pencil (j2p, lane) over k1, gathered from the cluster
+            float2 x[N];
+            #pragma unroll
+            for (int k = 0; k < N; ++k) x[k] = ld_dsmem(pen[k / PPC] + (uint32_t)(k % PPC) * PLANE_BYTES);
+            fft_inplace<N, +1>(x);                            // k1 -> j1
+            #pragma unroll
+            for (int j = 0; j < N; ++j) x[j] = cmul(x[j], shs[((size_t)pid * N + j) * N + lane]);
+            fft_inplace<N, -1>(x);                            // j1 -> k1
+            #pragma unroll
+            for (int k = 0; k < N; ++k) st_dsmem(pen[k / PPC] + (uint32_t)(k % PPC) * PLANE_BYTES, x[k]);
+            cluster_barrier<C>();
+            // C: rows over j3, then column k3 = lane over j2, times alpha, accumulate
+            #pragma unroll
+            for (int j = 0; j < N; ++j) x[j] = my[lane * LD + j];
+            fft_inplace<N, -1>(x);                            // j3 -> k3 (row j2 = lane)
+            #pragma unroll
+            for (int j = 0; j < N; ++j) my[lane * LD + j] = x[j];
+            cp_async_wait_1();                                // alpha tile (the next twiddles may pend)
+            __syncthreads();
+            #pragma unroll
+            for (int i = 0; i < N; ++i) x[i] = my[i * LD + lane];
+            fft_inplace<N, -1>(x);                            // j2 -> k2
+            #pragma unroll
+            for (int i = 0; i < N; ++i) {
+                float2 al = sal[((size_t)pid * N + i) * N + lane];
+                if constexpr (SCALED) {
+                    float2 t = cmul(x[i], al);
+                    acc[i].x = fmaf(sc, t.x, acc[i].x);
+                    acc[i].y = fmaf(sc, t.y, acc[i].y);
+                } else {
+                    acc[i].x = fmaf(x[i].x, al.x, fmaf(-x[i].y, al.y, acc[i].x));
+                    acc[i].y = fmaf(x[i].x, al.y, fmaf(x[i].y, al.x, acc[i].y));
+                }
+            }
         }
+        cp_async_wait_all();
+        float2 *out = a.part + ((size_t)slot * a.nblk + blk) * N3 + (size_t)k1 * N * N;
+        #pragma unroll
+        for (int i = 0; i < N; ++i) out[i * N + lane] = acc[i];
     }
-    cp_async_wait_all();
-    float2 *out = part + (size_t)cid * N * N * N + (size_t)k1 * N * N;
-    #pragma unroll
-    for (int i = 0; i < N; ++i) out[i * N + lane] = acc[i];
 }
 
 // acc[k] = sum over g of part[g][k] in FP64 with a fixed shape: thread (kk, s) of a 32 x 8
@@ -225,13 +245,18 @@ __global__ void __launch_bounds__(256) k_reduce_parts(const float2 *__restrict__
     }
 }
 
+template <int N, bool SC> static cudaError_t set_smem() {
+    return cudaFuncSetAttribute(k_fused<N, SC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FK<N>::SMEM);
+}
+
 template <int N> static cudaError_t fused_setup_n(int *G) {
     using K = FK<N>;
-    cudaError_t e = cudaFuncSetAttribute(k_fused<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K::SMEM);
+    cudaError_t e = set_smem<N, false>();
+    if (e == cudaSuccess) e = set_smem<N, true>();
     if (e != cudaSuccess) return e;
     if (K::C == 1) {
         int per_sm = 0, dev = 0, sms = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused<N>, K::THREADS, K::SMEM);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused<N, true>, K::THREADS, K::SMEM);
         if (e != cudaSuccess) return e;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -248,7 +273,7 @@ template <int N> static cudaError_t fused_setup_n(int *G) {
         cfg.dynamicSmemBytes = K::SMEM;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        e = cudaOccupancyMaxActiveClusters(G, k_fused<N>, &cfg);
+        e = cudaOccupancyMaxActiveClusters(G, k_fused<N, true>, &cfg);
         if (e != cudaSuccess) return e;
     }
     return *G > 0 ? cudaSuccess : cudaErrorInvalidConfiguration;
@@ -266,14 +291,11 @@ cudaError_t fused_setup(int N, int *G) {
     return cudaErrorInvalidValue;
 }
 
-template <int N>
-static bz_status run_fused_n(Plan &pl, int p0, int p1, cudaStream_t st, int *launches) {
+template <int N, bool SC> static bz_status launch_n(const Plan &pl, const ItemArgs &a, cudaStream_t st) {
     using K = FK<N>;
-    const int n3 = N * N * N;
     const int G = pl.fused_G;
-    tm_begin(pl, st);
     if (K::C == 1) {
-        k_fused<N><<<G, K::THREADS, K::SMEM, st>>>(pl.fin, pl.tw, pl.alpha, pl.part, p0, p1);
+        k_fused<N, SC><<<G, K::THREADS, K::SMEM, st>>>(a);
     } else {
         cudaLaunchConfig_t cfg = {};
         cudaLaunchAttribute attr[1];
@@ -287,26 +309,43 @@ static bz_status run_fused_n(Plan &pl, int p0, int p1, cudaStream_t st, int *lau
         cfg.stream = st;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        BZ_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_fused<N>, (const float2 *)pl.fin, (const float2 *)pl.tw,
-                                       (const float2 *)pl.alpha, pl.part, p0, p1));
+        BZ_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_fused<N, SC>, a));
     }
+    BZ_CUDA_TRY(cudaGetLastError());
+    return BZ_OK;
+}
+
+bz_status launch_fused(const Plan &pl, const ItemArgs &a, cudaStream_t st) {
+    const bool sc = a.gsc != nullptr;
+    switch (pl.N) {
+        case 8: return sc ? launch_n<8, true>(pl, a, st) : launch_n<8, false>(pl, a, st);
+        case 16: return sc ? launch_n<16, true>(pl, a, st) : launch_n<16, false>(pl, a, st);
+        case 24: return sc ? launch_n<24, true>(pl, a, st) : launch_n<24, false>(pl, a, st);
+        case 32: return sc ? launch_n<32, true>(pl, a, st) : launch_n<32, false>(pl, a, st);
+    }
+    return BZ_ERR_UNSUPPORTED;
+}
+
+// One instance (pl.fin), terms [p0, p1): one block of terms per resident cluster, then the
+// fixed-order FP64 sum of the blocks into pl.acc.
+bz_status collide_fused(Plan &pl, int p0, int p1, cudaStream_t st, int *launches) {
+    const int n3 = pl.N * pl.N * pl.N;
+    ItemArgs a;
+    a.fin = pl.fin; a.tw = pl.tw; a.alpha = pl.alpha; a.part = pl.part;
+    a.count = 1; a.p0 = p0; a.p1 = p1; a.M = pl.M; a.N_rho = pl.N_rho;
+    const int nt = p1 - p0;
+    a.TB = nt > 0 ? (nt + pl.fused_G - 1) / pl.fused_G : 1;
+    a.nblk = nt > 0 ? (nt + a.TB - 1) / a.TB : 0;
+    tm_begin(pl, st);
+    bz_status s = launch_fused(pl, a, st);
+    if (s != BZ_OK) return s;
     tm_end(pl, st, TK_FUSED);
     tm_begin(pl, st);
-    k_reduce_parts<<<(n3 + 31) / 32, 256, 0, st>>>(pl.part, G, n3, pl.acc);
+    k_reduce_parts<<<(n3 + 31) / 32, 256, 0, st>>>(pl.part, a.nblk, n3, pl.acc);
     tm_end(pl, st, TK_REDUCE);
     BZ_CUDA_TRY(cudaGetLastError());
     if (launches) *launches += 2;
     return BZ_OK;
-}
-
-bz_status collide_fused(Plan &pl, int p0, int p1, cudaStream_t st, int *launches) {
-    switch (pl.N) {
-        case 8: return run_fused_n<8>(pl, p0, p1, st, launches);
-        case 16: return run_fused_n<16>(pl, p0, p1, st, launches);
-        case 24: return run_fused_n<24>(pl, p0, p1, st, launches);
-        case 32: return run_fused_n<32>(pl, p0, p1, st, launches);
-    }
-    return BZ_ERR_UNSUPPORTED;
 }
 
 }  // namespace bz

@@ -94,7 +94,20 @@ bz_status load_input(Plan &pl, const void *fhat, int dtype, cudaStream_t st, int
 bz_status collide_core(Plan &pl, int p0, int p1, cudaStream_t st, int *launches);
 
 // bz_fused.cu
+// Arguments of the fused item kernel (see k_fused): item w = (instance w / nblk, term block
+// w % nblk); instance b lives in array slot slots[b] (identity when slots is null).
+struct ItemArgs {
+    const float2 *fin = nullptr;     // [slots][N^3] FP32 inputs
+    const float2 *tw = nullptr;      // [P][3][N]
+    const float2 *alpha = nullptr;   // [P][N^3]
+    const float *gsc = nullptr;      // [slots][N_rho] radial scale r_i^(gamma_b - gamma_plan), or null
+    float2 *part = nullptr;          // [slots][nblk][N^3] per-item partial sums
+    const int *slots = nullptr;      // device [count] or null
+    const int *count_dev = nullptr;  // device instance count, or null (use count)
+    int count = 1, p0 = 0, p1 = 0, TB = 1, nblk = 0, M = 1, N_rho = 1;
+};
 cudaError_t fused_setup(int N, int *G);
+bz_status launch_fused(const Plan &pl, const ItemArgs &a, cudaStream_t st);
 bz_status collide_fused(Plan &pl, int p0, int p1, cudaStream_t st, int *launches);
 cudaError_t collide_set_attributes(int N);
 int supported_N(int N);
