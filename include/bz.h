@@ -190,6 +190,46 @@ bz_status bz_batch_step_rk(bz_batch *batch, int count, const int *slots, void *f
 /* Kernel launches (graph nodes included) of the last batch call. */
 int bz_batch_last_launches(const bz_batch *batch);
 
+/* ---------------------------------------------------------------------------------------
+ * Serving: a worker thread runs homogeneous relaxation solves (RK4 on d fhat/dt = Q) for
+ * submitted requests with continuous batching.  Each iteration admits queued requests in
+ * arrival order while the HBM budget and group slots allow, advances every active request
+ * by one RK4 step (requests with equal geometry and dt share one batched call, N <= 32;
+ * larger N step through their own plan; each group on its own stream), and retires the
+ * finished ones.  State stays on the device from admission to completion.  A request's
+ * result does not depend on the other requests in flight.
+ * --------------------------------------------------------------------------------------- */
+typedef struct bz_server bz_server;
+
+typedef struct {
+    int N; double L, R, gamma, s; int N_rho, M, kernel;   /* operator, as in bz_plan_desc   */
+    const void *fhat0; int dtype;   /* host array of N^3 initial coefficients; copied by bz_submit */
+    double t0, t_end, dt;           /* round((t_end - t0) / dt) RK4 steps of size dt              */
+    double max_queue_s;             /* > 0: fail with BZ_ERR_TIMEOUT if not admitted in time      */
+} bz_request;
+
+typedef struct {
+    int status;          /* BZ_OK, or the error that ended the request                       */
+    int steps;           /* RK4 steps taken                                                   */
+    double t;            /* t0 + steps * dt                                                   */
+    double latency_s;    /* submit to completion                                              */
+    double queue_s;      /* submit to admission                                               */
+} bz_result;
+
+/* hbm_budget_bytes bounds the device memory of plans, batches and request state; max_batch
+ * is the slot capacity of each batched group; terms_per_item <= 0 autotunes per group. */
+bz_status bz_server_create(bz_server **out, size_t hbm_budget_bytes, int max_batch, int terms_per_item);
+/* Queues a request (never blocks on the device).  *ticket identifies it for bz_poll. */
+bz_status bz_submit(bz_server *server, const bz_request *req, uint64_t *ticket);
+/* Non-blocking.  BZ_ERR_BUSY while queued or running; otherwise fills *out, copies the
+ * final coefficients to fhat_out (host, dtype; may be NULL) when out->status == BZ_OK,
+ * forgets the ticket and returns BZ_OK.  BZ_ERR_ARG for an unknown ticket. */
+bz_status bz_poll(bz_server *server, uint64_t ticket, bz_result *out, void *fhat_out, int dtype);
+bz_status bz_server_stats(bz_server *server, long *completed, long *steps, size_t *hbm_used, int *queued,
+                          int *active);
+/* Stops the worker after its current iteration and frees everything. */
+void bz_server_destroy(bz_server *server);
+
 /* Kernel kinds reported by bz_plan_timing. */
 enum { BZ_K_PLANE_INV = 0, BZ_K_PENCIL = 1, BZ_K_PLANE_FWD = 2, BZ_K_REDUCE = 3, BZ_K_OTHER = 4,
        BZ_K_FUSED = 5 };

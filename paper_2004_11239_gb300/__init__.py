@@ -22,7 +22,7 @@ __all__ = [
     "bz_plan_alpha", "bz_plan_last_launches", "bz_status_str", "library_path", "lib",
     "bz_plan_set_timing", "bz_plan_timing", "bz_collide_noalloc",
     "bz_batch_create", "bz_batch_destroy", "bz_batch_set_gamma", "bz_batch_collide", "bz_batch_step_rk",
-    "bz_batch_last_launches",
+    "bz_batch_last_launches", "bz_server_create", "bz_submit", "bz_poll", "bz_server_stats",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -34,6 +34,19 @@ BZ_PREC_FP32 = 0
 BZ_PIPE_AUTO, BZ_PIPE_FUSED, BZ_PIPE_CHUNKED = 0, 1, 2
 _STATUS = {0: "BZ_OK", 1: "BZ_ERR_ARG", 2: "BZ_ERR_OOM", 3: "BZ_ERR_CUDA", 4: "BZ_ERR_TIMEOUT",
            5: "BZ_ERR_NONFINITE", 6: "BZ_ERR_BUSY", 7: "BZ_ERR_UNSUPPORTED"}
+
+
+class bz_request(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("L", ctypes.c_double), ("R", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("s", ctypes.c_double), ("N_rho", ctypes.c_int),
+                ("M", ctypes.c_int), ("kernel", ctypes.c_int), ("fhat0", ctypes.c_void_p),
+                ("dtype", ctypes.c_int), ("t0", ctypes.c_double), ("t_end", ctypes.c_double),
+                ("dt", ctypes.c_double), ("max_queue_s", ctypes.c_double)]
+
+
+class bz_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("steps", ctypes.c_int), ("t", ctypes.c_double),
+                ("latency_s", ctypes.c_double), ("queue_s", ctypes.c_double)]
 
 
 class BzError(RuntimeError):
@@ -78,6 +91,11 @@ def _load():
         "bz_batch_set_gamma": [vp, c_int, c_double],
         "bz_batch_collide": [vp, c_int, ip, vp, vp, c_int, vp],
         "bz_batch_step_rk": [vp, c_int, ip, vp, c_int, c_double, c_int, vp],
+        "bz_server_create": [ctypes.POINTER(vp), c_size, c_int, c_int],
+        "bz_submit": [vp, ctypes.POINTER(bz_request), ctypes.POINTER(ctypes.c_uint64)],
+        "bz_poll": [vp, ctypes.c_uint64, ctypes.POINTER(bz_result), vp, c_int],
+        "bz_server_stats": [vp, ctypes.POINTER(ctypes.c_long), ctypes.POINTER(ctypes.c_long),
+                            ctypes.POINTER(c_size), ip, ip],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -87,6 +105,8 @@ def _load():
     L.bz_plan_set_timing.restype = c_int
     L.bz_plan_timing.argtypes = [vp, c_int, ctypes.POINTER(ctypes.c_long), dp]
     L.bz_plan_timing.restype = c_int
+    L.bz_server_destroy.argtypes = [vp]
+    L.bz_server_destroy.restype = None
     L.bz_batch_destroy.argtypes = [vp]
     L.bz_batch_destroy.restype = None
     L.bz_batch_last_launches.argtypes = [vp]
@@ -350,6 +370,65 @@ def bz_batch_step_rk(batch: Batch, slots, fhat, dt: float, nsteps: int, stream=N
 
 def bz_batch_last_launches(batch: Batch) -> int:
     return lib.bz_batch_last_launches(batch.handle)
+
+
+class Server:
+    """Owning handle of a bz_server."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    def close(self):
+        if self.handle:
+            lib.bz_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def bz_server_create(hbm_budget_bytes: int, max_batch: int = 64, terms_per_item: int = 0) -> Server:
+    h = ctypes.c_void_p()
+    _check(lib.bz_server_create(ctypes.byref(h), hbm_budget_bytes, max_batch, terms_per_item), "bz_server_create")
+    return Server(h)
+
+
+def bz_submit(server: Server, fhat0, N: int, L: float, R: float, gamma: float, s: float, N_rho: int, M: int,
+              t0: float, t_end: float, dt: float, kernel: int = BZ_KERNEL_FAMILY, max_queue_s: float = 0.0) -> int:
+    """fhat0: host numpy array of N^3 complex128 (or complex64) coefficients; returns the ticket."""
+    import numpy as np
+    a = np.ascontiguousarray(fhat0)
+    dt_code = BZ_C128 if a.dtype == np.complex128 else BZ_C64
+    if a.dtype not in (np.complex128, np.complex64) or a.size != N ** 3:
+        raise ValueError("fhat0 must hold N^3 complex64/complex128 values")
+    r = bz_request(N, L, R, gamma, s, N_rho, M, kernel, a.ctypes.data, dt_code, t0, t_end, dt, max_queue_s)
+    t = ctypes.c_uint64()
+    _check(lib.bz_submit(server.handle, ctypes.byref(r), ctypes.byref(t)), "bz_submit")
+    return t.value
+
+
+def bz_poll(server: Server, ticket: int, N: int):
+    """None while pending; else (bz_result, numpy complex128 coefficients or None)."""
+    import numpy as np
+    res = bz_result()
+    out = np.empty((N, N, N), dtype=np.complex128)
+    code = lib.bz_poll(server.handle, ticket, ctypes.byref(res), ctypes.c_void_p(out.ctypes.data), BZ_C128)
+    if code == 6:
+        return None
+    _check(code, "bz_poll")
+    return res, (out if res.status == 0 else None)
+
+
+def bz_server_stats(server: Server):
+    c, st = ctypes.c_long(), ctypes.c_long()
+    u = ctypes.c_size_t()
+    q, a = ctypes.c_int(), ctypes.c_int()
+    _check(lib.bz_server_stats(server.handle, ctypes.byref(c), ctypes.byref(st), ctypes.byref(u), ctypes.byref(q),
+                               ctypes.byref(a)), "bz_server_stats")
+    return {"completed": c.value, "steps": st.value, "hbm_used": u.value, "queued": q.value, "active": a.value}
 
 
 def bz_status_str(code: int) -> str:

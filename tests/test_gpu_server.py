@@ -1,0 +1,96 @@
+"""Serving loop (bz_server_*): results alone and in a concurrent mix, against the oracle (GPU)."""
+import time
+
+import numpy as np
+import pytest
+
+import bz_inputs as bi
+from oracle import kernels, spectral
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def bz():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__._libbuild().build()
+    import paper_2004_11239_gb300 as m
+    return m
+
+
+def _wait(bz, server, tickets, Ns, timeout=600.0):
+    out = {}
+    t0 = time.time()
+    while len(out) < len(tickets):
+        for t, N in zip(tickets, Ns):
+            if t in out:
+                continue
+            r = bz.bz_poll(server, t, N)
+            if r is not None:
+                out[t] = r
+        assert time.time() - t0 < timeout, "requests did not finish"
+        time.sleep(0.005)
+    return [out[t] for t in tickets]
+
+
+R = 6.0
+L = bi.L_from_R(R)
+
+
+def _req(N, gamma, s, N_rho, M, f, t_end=6.6, dt=0.025):
+    return dict(fhat0=f, N=N, L=L, R=R, gamma=gamma, s=s, N_rho=N_rho, M=M, t0=6.5, t_end=t_end, dt=dt)
+
+
+def test_result_alone_equals_result_in_the_mix_and_matches_oracle(bz):
+    fA = bi.bkw_fhat(16, L, bi.bkw_K(6.5))
+    server = bz.bz_server_create(16 << 30, max_batch=8, terms_per_item=8)
+    ta = bz.bz_submit(server, **_req(16, 0.0, 0.5, 4, 12, fA))
+    (resA, outA), = _wait(bz, server, [ta], [16])
+    assert resA.status == 0 and resA.steps == 4 and abs(resA.t - 6.6) < 1e-12
+    # the same request among others of the same and of other groups, submitted together
+    mix = [
+        _req(16, 0.0, 0.5, 4, 12, fA),                                        # A again
+        _req(16, -1.0, 0.5, 4, 12, bi.random_mixture(16, L, seed=2, box=1.0)),  # same group
+        _req(24, 0.0, 0.25, 3, 12, bi.random_mixture(24, L, seed=3, box=1.0)),  # another group
+        _req(16, 0.0, 0.5, 4, 12, bi.random_mixture(16, L, seed=4, box=1.0), t_end=6.55),
+        _req(48, -1.0, 0.5, 1, 12, bi.random_mixture(48, L, seed=5, box=1.0), t_end=6.55),
+        _req(16, -2.0, 0.5, 4, 12, bi.random_mixture(16, L, seed=6, box=1.0), dt=0.0125, t_end=6.55),
+    ]
+    tickets = [bz.bz_submit(server, **r) for r in mix]
+    res = _wait(bz, server, tickets, [r["N"] for r in mix])
+    for (rr, out), r in zip(res, mix):
+        assert rr.status == 0, rr.status
+        assert rr.steps == round((r["t_end"] - 6.5) / r["dt"])
+    outA2 = res[0][1]
+    assert np.array_equal(outA2, outA)                 # identical bits alone and in the mix
+    # A against the oracle's RK4
+    op = spectral.OraclePlan(16, L, R, 0.0, kernels.Kernel("family", 0.5), 4, 12)
+    ref = spectral.rk4(op, fA, 0.025, 4)
+    err = float(np.max(np.abs((outA - fA) - (ref - fA))) / np.max(np.abs(ref - fA)))
+    print(f"served RK4: rel_Linf of the change={err:.2e}")
+    assert err <= TOL
+    # the N = 48 request (own plan, chunked pipeline) equals a direct bz_step_rk
+    r48 = mix[4]
+    plan = bz.bz_plan_create(48, L, R, -1.0, 0.5, 1, 12)
+    f48 = torch.from_numpy(r48["fhat0"]).cuda()
+    bz.bz_step_rk(plan, f48, 6.5, 0.025, 2)
+    torch.cuda.synchronize()
+    assert np.array_equal(res[4][1], f48.cpu().numpy())
+    st = bz.bz_server_stats(server)
+    assert st["completed"] == 7 and st["queued"] == 0 and st["active"] == 0
+    plan.close()
+    server.close()
+
+
+def test_request_larger_than_the_budget_fails_cleanly(bz):
+    server = bz.bz_server_create(1 << 20, max_batch=4)            # 1 MiB: no plan fits
+    t = bz.bz_submit(server, **_req(16, 0.0, 0.5, 4, 12, bi.bkw_fhat(16, L, bi.bkw_K(6.5))))
+    (res, out), = _wait(bz, server, [t], [16], timeout=60)
+    assert res.status == 2 and out is None                        # BZ_ERR_OOM
+    with pytest.raises(bz.BzError):
+        bz.bz_poll(server, t, 16)                                 # ticket forgotten after the poll
+    server.close()
