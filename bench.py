@@ -209,7 +209,9 @@ def run_ours(args, w):
 
     L, R = _geometry(w)
     N = w["N"]
-    plan = bz.bz_plan_create(N, L, R, w["gamma"], w["s"], w["N_rho"], w["M"])
+    plan = bz.bz_plan_create_ex(N, L, R, w["gamma"], w["s"], w["N_rho"], w["M"], h_precision=args.h_precision)
+    pipe = bz.bz_plan_pipeline(plan)
+    pipe["h_precision"] = {0: "fp64", 1: "fp64", 2: "fp32"}[args.h_precision]
     f_host = _fhat(w, L)
     f = torch.from_numpy(f_host).to("cuda")
     q = torch.empty_like(f)
@@ -309,6 +311,7 @@ def run_ours(args, w):
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload, "desc": w["desc"], "P": w["N_rho"] * w["M"],
+                       "pipeline": pipe,
                        "collides_per_step": evals_per_step,
                        "l2": "inputs larger than L2: the alpha table of %d MB streams every collide"
                              % (plan.alpha_bytes >> 20)},
@@ -394,6 +397,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="rk4_n32", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--h-precision", type=int, default=0, choices=[0, 1, 2],
+                    help="h = IFFT(fhat) precision on the fused path: 0 auto (FP64), 1 FP64, 2 FP32")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if args.workload == "batch_4096":

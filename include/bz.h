@@ -64,6 +64,13 @@ enum { BZ_PREC_FP32 = 0 };
  * FUSED where it applies. */
 enum { BZ_PIPE_AUTO = 0, BZ_PIPE_FUSED = 1, BZ_PIPE_CHUNKED = 2 };
 
+/* Precision of h = IFFT(fhat) on the fused pipeline.  FP32 transforms leave a noise floor of
+ * about eps max|h| over the grid, which the product h g_p turns into error where g_p is large
+ * and h small; forming h in FP64 (from the caller's FP64 coefficients) removes that half of
+ * the rounding error, at the cost of three short FP64 passes per collide.  FP32 forms h
+ * inside the fused kernel.  AUTO = FP64. */
+enum { BZ_H_AUTO = 0, BZ_H_FP64 = 1, BZ_H_FP32 = 2 };
+
 typedef struct bz_plan bz_plan;
 
 typedef struct {
@@ -81,6 +88,9 @@ typedef struct {
     const double *sphere_w;    /* optional host array [M] of weights (sum 4 pi)         */
     int chunk_terms;  /* terms per pipeline chunk; <= 0 selects automatically          */
     int pipeline;     /* BZ_PIPE_*; BZ_ERR_UNSUPPORTED if FUSED cannot run for this N     */
+    int cluster;      /* FUSED: CTAs per cluster (N=16: 1|2, 24: 2|3, 32: 4|8); <= 0 times the
+                         compiled sizes at creation and keeps the fastest                   */
+    int h_precision;  /* BZ_H_*                                                            */
 } bz_plan_desc;
 
 /* Creates a plan: quadrature terms, the FP64 F table (computed on the device, stored
@@ -95,6 +105,11 @@ void bz_plan_destroy(bz_plan *plan);
 
 /* Number of quadrature terms P = N_rho * M; bytes of the alpha table. */
 bz_status bz_plan_info(const bz_plan *plan, int *P, size_t *alpha_bytes, size_t *workspace_bytes);
+
+/* The collide pipeline the plan runs: *pipeline = BZ_PIPE_FUSED or BZ_PIPE_CHUNKED;
+ * for FUSED, *cluster = CTAs per cluster, *clusters = resident clusters (persistent grid),
+ * *tuned_ms = the timed collide that selected the cluster size.  Any pointer may be NULL. */
+bz_status bz_plan_pipeline(const bz_plan *plan, int *pipeline, int *cluster, int *clusters, float *tuned_ms);
 
 /* Copies the term list to host arrays of length P (any may be NULL):
  * r[p], w_r[p], qhat[3p..3p+2], w_q[p], c[p] = w_r w_q r^(gamma+2).  Synchronous. */

@@ -20,7 +20,7 @@ __all__ = [
     "bz_plan_create", "bz_plan_create_ex", "bz_plan_destroy", "bz_plan_info", "bz_plan_terms",
     "bz_collide", "bz_collide_terms", "bz_step_rk", "bz_moments", "bz_ftable_entries",
     "bz_plan_alpha", "bz_plan_last_launches", "bz_status_str", "library_path", "lib",
-    "bz_plan_set_timing", "bz_plan_timing", "bz_collide_noalloc",
+    "bz_plan_set_timing", "bz_plan_timing", "bz_collide_noalloc", "bz_plan_pipeline",
     "bz_batch_create", "bz_batch_destroy", "bz_batch_set_gamma", "bz_batch_collide", "bz_batch_step_rk",
     "bz_batch_last_launches", "bz_server_create", "bz_submit", "bz_poll", "bz_server_stats",
 ]
@@ -32,6 +32,7 @@ BZ_C64, BZ_C128 = 0, 1
 BZ_KERNEL_FAMILY, BZ_KERNEL_B5, BZ_KERNEL_B8 = 0, 1, 2
 BZ_PREC_FP32 = 0
 BZ_PIPE_AUTO, BZ_PIPE_FUSED, BZ_PIPE_CHUNKED = 0, 1, 2
+BZ_H_AUTO, BZ_H_FP64, BZ_H_FP32 = 0, 1, 2
 _STATUS = {0: "BZ_OK", 1: "BZ_ERR_ARG", 2: "BZ_ERR_OOM", 3: "BZ_ERR_CUDA", 4: "BZ_ERR_TIMEOUT",
            5: "BZ_ERR_NONFINITE", 6: "BZ_ERR_BUSY", 7: "BZ_ERR_UNSUPPORTED"}
 
@@ -61,7 +62,7 @@ class bz_plan_desc(ctypes.Structure):
                 ("M", ctypes.c_int), ("kernel", ctypes.c_int), ("precision", ctypes.c_int),
                 ("eps", ctypes.c_double), ("sphere_xyz", ctypes.POINTER(ctypes.c_double)),
                 ("sphere_w", ctypes.POINTER(ctypes.c_double)), ("chunk_terms", ctypes.c_int),
-                ("pipeline", ctypes.c_int)]
+                ("pipeline", ctypes.c_int), ("cluster", ctypes.c_int), ("h_precision", ctypes.c_int)]
 
 
 def library_path() -> str:
@@ -79,6 +80,7 @@ def _load():
         "bz_plan_create_ex": [ctypes.POINTER(vp), ctypes.POINTER(bz_plan_desc)],
         "bz_plan_info": [vp, ip, ctypes.POINTER(c_size), ctypes.POINTER(c_size)],
         "bz_plan_terms": [vp, dp, dp, dp, dp, dp],
+        "bz_plan_pipeline": [vp, ip, ip, ip, ctypes.POINTER(ctypes.c_float)],
         "bz_collide": [vp, vp, vp, c_int, vp],
         "bz_collide_terms": [vp, c_int, c_int, vp, vp, c_int, vp],
         "bz_step_rk": [vp, vp, c_int, dp, c_double, c_int, vp, vp],
@@ -189,11 +191,14 @@ def bz_plan_create(N: int, L: float, R: float, gamma: float, s: float, N_rho: in
 
 def bz_plan_create_ex(N: int, L: float, R: float, gamma: float, s: float, N_rho: int, M: int,
                       kernel: int = BZ_KERNEL_FAMILY, eps: float = 0.0, sphere=None,
-                      chunk_terms: int = 0, pipeline: int = BZ_PIPE_AUTO) -> Plan:
+                      chunk_terms: int = 0, pipeline: int = BZ_PIPE_AUTO, cluster: int = 0,
+                      h_precision: int = BZ_H_AUTO) -> Plan:
     d = bz_plan_desc()
     d.N, d.L, d.R, d.gamma, d.s, d.N_rho, d.M = N, L, R, gamma, s, N_rho, M
     d.kernel, d.precision, d.eps, d.chunk_terms = kernel, BZ_PREC_FP32, eps, chunk_terms
     d.pipeline = pipeline
+    d.cluster = cluster
+    d.h_precision = h_precision
     keep = []
     if sphere is not None:
         import numpy as np
@@ -213,6 +218,16 @@ def bz_plan_destroy(plan: Plan):
 
 def bz_plan_info(plan: Plan):
     return plan.P, plan.alpha_bytes, plan.workspace_bytes
+
+
+def bz_plan_pipeline(plan: Plan):
+    """{'pipeline': 'fused'|'chunked', 'cluster': C, 'clusters': G, 'tuned_ms': t}."""
+    p, c, g = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    t = ctypes.c_float()
+    _check(lib.bz_plan_pipeline(plan.handle, ctypes.byref(p), ctypes.byref(c), ctypes.byref(g), ctypes.byref(t)),
+           "bz_plan_pipeline")
+    return {"pipeline": "fused" if p.value == BZ_PIPE_FUSED else "chunked", "cluster": c.value,
+            "clusters": g.value, "tuned_ms": t.value}
 
 
 def bz_plan_terms(plan: Plan):

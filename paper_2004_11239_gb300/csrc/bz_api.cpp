@@ -2,6 +2,7 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <utility>
 #include <vector>
 
 #include "bz_internal.h"
@@ -28,8 +29,8 @@ void free_plan(bz::Plan &p) {
     free_timing(p);
     cudaFree(p.alpha); cudaFree(p.tw); cudaFree(p.rule_buf); cudaFree(p.rule_off);
     cudaFree(p.term_dev); cudaFree(p.S); cudaFree(p.h); cudaFree(p.fin); cudaFree(p.acc);
-    cudaFree(p.rk); cudaFree(p.mom); cudaFree(p.part);
-    p.part = nullptr;
+    cudaFree(p.rk); cudaFree(p.mom); cudaFree(p.part); cudaFree(p.fin64); cudaFree(p.scr64);
+    p.part = nullptr; p.fin64 = nullptr; p.scr64 = nullptr; p.src = nullptr;
     p.alpha = nullptr; p.tw = nullptr; p.rule_buf = nullptr; p.rule_off = nullptr;
     p.term_dev = nullptr; p.S = nullptr; p.h = nullptr; p.fin = nullptr; p.acc = nullptr;
     p.rk = nullptr; p.mom = nullptr;
@@ -58,6 +59,48 @@ std::vector<float2> make_twiddles(const bz::Plan &pl) {
     return tw;
 }
 
+// Times one full collide of a zero field for each compiled cluster size (or only `forced`)
+// and keeps the fastest; allocates the partial-sum buffer for it.
+bz_status select_fused(bz::Plan &pl, int forced) {
+    int cs[4];
+    int nc = bz::fused_candidates(pl.N, cs);
+    const size_t field = (size_t)pl.N * pl.N * pl.N * sizeof(float2);
+    int bestC = 0, bestG = 0;
+    float best = 1e30f;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return BZ_ERR_CUDA;
+    if (cudaMemset(pl.fin, 0, field) != cudaSuccess) return BZ_ERR_CUDA;
+    for (int c = 0; c < nc; ++c) {
+        if (forced > 0 && cs[c] != forced) continue;
+        int G = 0;
+        if (bz::fused_setup(pl.N, cs[c], &G) != cudaSuccess || G <= 0) { cudaGetLastError(); continue; }
+        float2 *part = nullptr;
+        if (cudaMalloc(&part, (size_t)G * field) != cudaSuccess) { cudaGetLastError(); continue; }
+        std::swap(part, pl.part);
+        pl.use_fused = 1; pl.fused_C = cs[c]; pl.fused_G = G;
+        float ms = 1e30f;
+        if (bz::collide_fused(pl, 0, pl.P, nullptr, nullptr) == BZ_OK) {      // warm-up
+            cudaEventRecord(e0);
+            bz::collide_fused(pl, 0, pl.P, nullptr, nullptr);
+            cudaEventRecord(e1);
+            if (cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+        }
+        cudaGetLastError();
+        std::swap(part, pl.part);
+        cudaFree(part);
+        if (ms < best) { best = ms; bestC = cs[c]; bestG = G; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    pl.use_fused = 0;
+    if (bestC == 0) return BZ_ERR_UNSUPPORTED;
+    if (dmalloc(&pl.part, (size_t)bestG * field) != BZ_OK) return BZ_ERR_OOM;
+    pl.use_fused = 1; pl.fused_C = bestC; pl.fused_G = bestG;
+    pl.fused_ms = best;
+    pl.ws_bytes += (size_t)bestG * field;
+    return BZ_OK;
+}
+
 bz_status create(bz_plan **out, const bz_plan_desc *d) {
     if (!out || !d) return BZ_ERR_ARG;
     *out = nullptr;
@@ -72,6 +115,8 @@ bz_status create(bz_plan **out, const bz_plan_desc *d) {
     pl.N = d->N; pl.L = d->L; pl.R = d->R; pl.gamma = d->gamma; pl.s = d->s;
     pl.N_rho = d->N_rho; pl.M = d->M; pl.kernel = d->kernel; pl.precision = d->precision;
     pl.eps = d->eps > 0 ? d->eps : M_PI / 1000.0;
+    if (d->h_precision < BZ_H_AUTO || d->h_precision > BZ_H_FP32) { delete h; return BZ_ERR_ARG; }
+    pl.h_fp64 = d->h_precision != BZ_H_FP32;
     cudaGetDevice(&pl.device);
     bz_status s = bz::build_terms(pl, d->sphere_xyz, d->sphere_w);
     if (s == BZ_OK) s = bz::build_kernel_constants(pl);
@@ -111,28 +156,24 @@ bz_status create(bz_plan **out, const bz_plan_desc *d) {
         delete h;
         return BZ_ERR_CUDA;
     }
-    // pipeline: the fused cluster kernel where it applies, else the chunked kernels
+    s = bz::ftable_build(pl);
+    if (s != BZ_OK) {
+        free_plan(pl);
+        delete h;
+        return s;
+    }
+    // pipeline: the fused cluster kernel where it applies (cluster size timed on this
+    // device, fastest kept), else the chunked kernels
     if (d->pipeline != BZ_PIPE_CHUNKED && N <= 32) {
-        int G = 0;
-        if (bz::fused_setup(N, &G) == cudaSuccess && G > 0 &&
-            dmalloc(&pl.part, (size_t)G * field) == BZ_OK) {
-            pl.use_fused = 1;
-            pl.fused_G = G;
-            pl.ws_bytes += (size_t)G * field;
-        } else {
-            cudaGetLastError();
+        if (dmalloc(&pl.fin64, n3 * sizeof(double2)) == BZ_OK && dmalloc(&pl.scr64, n3 * sizeof(double2)) == BZ_OK) {
+            pl.ws_bytes += 2 * n3 * sizeof(double2);
+            if (select_fused(pl, d->cluster) != BZ_OK) cudaGetLastError();
         }
     }
     if (d->pipeline == BZ_PIPE_FUSED && !pl.use_fused) {
         free_plan(pl);
         delete h;
         return BZ_ERR_UNSUPPORTED;
-    }
-    s = bz::ftable_build(pl);
-    if (s != BZ_OK) {
-        free_plan(pl);
-        delete h;
-        return s;
     }
     *out = h;
     return BZ_OK;
@@ -166,6 +207,16 @@ bz_status bz_plan_info(const bz_plan *plan, int *P, size_t *alpha_bytes, size_t 
     if (P) *P = p.P;
     if (alpha_bytes) *alpha_bytes = (size_t)p.P * n3 * sizeof(float2);
     if (workspace_bytes) *workspace_bytes = p.ws_bytes;
+    return BZ_OK;
+}
+
+bz_status bz_plan_pipeline(const bz_plan *plan, int *pipeline, int *cluster, int *clusters, float *tuned_ms) {
+    if (!plan) return BZ_ERR_ARG;
+    const bz::Plan &p = plan->p;
+    if (pipeline) *pipeline = p.use_fused ? BZ_PIPE_FUSED : BZ_PIPE_CHUNKED;
+    if (cluster) *cluster = p.use_fused ? p.fused_C : 0;
+    if (clusters) *clusters = p.use_fused ? p.fused_G : 0;
+    if (tuned_ms) *tuned_ms = p.use_fused ? p.fused_ms : 0.f;
     return BZ_OK;
 }
 

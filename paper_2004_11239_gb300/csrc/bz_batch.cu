@@ -33,6 +33,8 @@ struct bz_batch {
     float2 *fin = nullptr;          // [capacity][N^3]
     float2 *part = nullptr;         // [capacity][nblk][N^3]
     double2 *f0 = nullptr, *fsum = nullptr;   // [capacity][N^3]
+    double2 *fin64 = nullptr, *scr64 = nullptr;   // [capacity][N^3] FP64 stage input and h scratch
+    float2 *h = nullptr;            // [capacity][N^3] h per instance
     int *slots_dev = nullptr;       // [capacity]
     int *count_dev = nullptr;       // [1]
     int *host_stage = nullptr;      // pinned [capacity + 1]
@@ -82,7 +84,7 @@ __global__ void k_batch_out(const float2 *part, int nblk, const int *slots, cons
 }
 
 __global__ void k_batch_rk_init(const void *fhat, int dtype, const int *slots, const int *count_dev, int n3,
-                                double2 *f0, float2 *fin) {
+                                double2 *f0, float2 *fin, double2 *fin64) {
     const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int b = (int)(e / n3), k = (int)(e % n3);
     if (b >= *count_dev) return;
@@ -95,11 +97,12 @@ __global__ void k_batch_rk_init(const void *fhat, int dtype, const int *slots, c
     }
     f0[idx] = v;
     fin[idx] = make_float2((float)v.x, (float)v.y);
+    fin64[idx] = v;
 }
 
 // Stage s of RK4 (the same combination as the single-instance path), k_s from the partials.
 __global__ void k_batch_rk_stage(const float2 *part, int nblk, const int *slots, const int *count_dev, int n3,
-                                 double2 *f0, double2 *fsum, float2 *fin, int stage, double dt) {
+                                 double2 *f0, double2 *fsum, float2 *fin, double2 *fin64, int stage, double dt) {
     const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int b = (int)(e / n3), k = (int)(e % n3);
     if (b >= *count_dev) return;
@@ -122,6 +125,7 @@ __global__ void k_batch_rk_stage(const float2 *part, int nblk, const int *slots,
         f0[idx] = y;
     }
     fin[idx] = make_float2((float)y.x, (float)y.y);
+    fin64[idx] = y;
 }
 
 __global__ void k_batch_rk_out(const double2 *f0, const int *slots, const int *count_dev, int n3, void *fhat,
@@ -138,6 +142,7 @@ ItemArgs item_args(const bz_batch &B) {
     const Plan &pl = *B.pl;
     ItemArgs a;
     a.fin = B.fin; a.tw = pl.tw; a.alpha = pl.alpha; a.gsc = B.gsc; a.part = B.part;
+    a.hg = pl.h_fp64 ? B.h : nullptr;
     a.slots = B.slots_dev; a.count_dev = B.count_dev; a.count = 0;
     a.p0 = 0; a.p1 = pl.P; a.TB = B.TB; a.nblk = B.nblk; a.M = pl.M; a.N_rho = pl.N_rho;
     return a;
@@ -169,6 +174,7 @@ void free_batch(bz_batch *B) {
     for (auto &g : B->graphs) cudaGraphExecDestroy(g.second);
     B->graphs.clear();
     cudaFree(B->gsc); cudaFree(B->fin); cudaFree(B->part); cudaFree(B->f0); cudaFree(B->fsum);
+    cudaFree(B->fin64); cudaFree(B->scr64); cudaFree(B->h);
     cudaFree(B->slots_dev); cudaFree(B->count_dev);
     if (B->host_stage) cudaFreeHost(B->host_stage);
     if (B->cap_stream) cudaStreamDestroy(B->cap_stream);
@@ -242,6 +248,9 @@ bz_status bz_batch_create(bz_batch **out, const bz_plan *plan, int capacity, int
         cudaMalloc(&B->fin, (size_t)capacity * field) != cudaSuccess ||
         cudaMalloc(&B->f0, (size_t)capacity * n3 * sizeof(double2)) != cudaSuccess ||
         cudaMalloc(&B->fsum, (size_t)capacity * n3 * sizeof(double2)) != cudaSuccess ||
+        cudaMalloc(&B->fin64, (size_t)capacity * n3 * sizeof(double2)) != cudaSuccess ||
+        cudaMalloc(&B->scr64, (size_t)capacity * n3 * sizeof(double2)) != cudaSuccess ||
+        cudaMalloc(&B->h, (size_t)capacity * field) != cudaSuccess ||
         cudaMalloc(&B->slots_dev, (size_t)capacity * sizeof(int)) != cudaSuccess ||
         cudaMalloc(&B->count_dev, sizeof(int)) != cudaSuccess ||
         cudaMallocHost(&B->host_stage, (size_t)(capacity + 1) * sizeof(int)) != cudaSuccess ||
@@ -259,7 +268,8 @@ bz_status bz_batch_create(bz_batch **out, const bz_plan *plan, int capacity, int
             cudaGetLastError();
             return fail(BZ_ERR_OOM);
         }
-        if (cudaMemset(B->fin, 0, (size_t)trial * field) != cudaSuccess) return fail(BZ_ERR_CUDA);
+        if (cudaMemset(B->fin, 0, (size_t)trial * field) != cudaSuccess ||
+            cudaMemset(B->h, 0, (size_t)trial * field) != cudaSuccess) return fail(BZ_ERR_CUDA);
         tb = autotune_tb(*B, trial, B->cap_stream);
         cudaStreamSynchronize(B->cap_stream);
         cudaFree(B->part);
@@ -307,11 +317,15 @@ bz_status bz_batch_collide(bz_batch *batch, int count, const int *slots, const v
     if (s != BZ_OK) return s;
     const int n3 = B.pl->N * B.pl->N * B.pl->N;
     k_batch_load<<<grid_for(B), 256, 0, st>>>(fhat, dtype, B.slots_dev, B.count_dev, n3, B.fin);
+    if (B.pl->h_fp64) {
+        s = h64_launch(B.pl->N, fhat, dtype, B.slots_dev, B.count_dev, B.capacity, B.scr64, B.h, st);
+        if (s != BZ_OK) return s;
+    }
     s = launch_fused(*B.pl, item_args(B), st);
     if (s != BZ_OK) return s;
     k_batch_out<<<grid_for(B), 256, 0, st>>>(B.part, B.nblk, B.slots_dev, B.count_dev, n3, Qhat, dtype);
     BZ_CUDA_TRY(cudaGetLastError());
-    B.last_launches = 3;
+    B.last_launches = 6;
     return BZ_OK;
 }
 
@@ -331,9 +345,12 @@ bz_status bz_batch_step_rk(bz_batch *batch, int count, const int *slots, void *f
         BZ_CUDA_TRY(cudaStreamBeginCapture(B.cap_stream, cudaStreamCaptureModeThreadLocal));
         bz_status cs = BZ_OK;
         for (int stage = 1; stage <= 4 && cs == BZ_OK; ++stage) {
-            cs = launch_fused(*B.pl, item_args(B), B.cap_stream);
+            if (B.pl->h_fp64)
+                cs = h64_launch(B.pl->N, B.fin64, BZ_C128, B.slots_dev, B.count_dev, B.capacity, B.scr64, B.h,
+                                B.cap_stream);
+            if (cs == BZ_OK) cs = launch_fused(*B.pl, item_args(B), B.cap_stream);
             k_batch_rk_stage<<<grid_for(B), 256, 0, B.cap_stream>>>(B.part, B.nblk, B.slots_dev, B.count_dev, n3,
-                                                                   B.f0, B.fsum, B.fin, stage, dt);
+                                                                   B.f0, B.fsum, B.fin, B.fin64, stage, dt);
         }
         cudaError_t ce = cudaStreamEndCapture(B.cap_stream, &g);
         if (cs != BZ_OK || ce != cudaSuccess) {
@@ -347,11 +364,11 @@ bz_status bz_batch_step_rk(bz_batch *batch, int count, const int *slots, void *f
         if (ce != cudaSuccess) return BZ_ERR_CUDA;
         it = B.graphs.emplace(dt, ex).first;
     }
-    k_batch_rk_init<<<grid_for(B), 256, 0, st>>>(fhat, dtype, B.slots_dev, B.count_dev, n3, B.f0, B.fin);
+    k_batch_rk_init<<<grid_for(B), 256, 0, st>>>(fhat, dtype, B.slots_dev, B.count_dev, n3, B.f0, B.fin, B.fin64);
     for (int step = 0; step < nsteps; ++step) BZ_CUDA_TRY(cudaGraphLaunch(it->second, st));
     k_batch_rk_out<<<grid_for(B), 256, 0, st>>>(B.f0, B.slots_dev, B.count_dev, n3, fhat, dtype);
     BZ_CUDA_TRY(cudaGetLastError());
-    B.last_launches = 2 + 8 * nsteps;
+    B.last_launches = 2 + 20 * nsteps;
     return BZ_OK;
 }
 

@@ -218,6 +218,8 @@ static bz_status run_chunks(Plan &pl, int p0, int p1, cudaStream_t st, int *laun
 
 bz_status load_input(Plan &pl, const void *fhat, int dtype, cudaStream_t st, int *launches) {
     const int n3 = pl.N * pl.N * pl.N;
+    pl.src = fhat;                 // the fused path forms h from the caller's array in FP64
+    pl.src_dtype = dtype;
     if (dtype == BZ_C64) {
         BZ_CUDA_TRY(cudaMemcpyAsync(pl.fin, fhat, (size_t)n3 * sizeof(float2), cudaMemcpyDeviceToDevice, st));
     } else if (dtype == BZ_C128) {

@@ -1,4 +1,5 @@
-// Register-resident mixed-radix (4, 2, 3) FFTs of compile-time length N in FP32.
+// Register-resident mixed-radix (4, 2, 3) FFTs of compile-time length N in FP32 (float2)
+// or FP64 (double2).
 //
 // One thread transforms one length-N line held in registers: a decimation-in-frequency
 // recursion N = R * (N / R) with radix-4, -2 or -3 butterflies; every index is a
@@ -69,6 +70,22 @@ template <int N> __host__ __device__ constexpr int tw_off() {
 constexpr int kTwTotal = 220;
 
 struct TwTable { float2 v[kTwTotal]; };
+struct TwTableD { double2 v[kTwTotal]; };
+
+constexpr TwTableD make_tw_table_d() {
+    TwTableD t{};
+    const int lens[12] = {8, 16, 24, 32, 48, 64, 12, 6, 4, 3, 2, 1};
+    const int offs[12] = {0, 8, 24, 48, 80, 128, 192, 204, 210, 214, 217, 219};
+    for (int a = 0; a < 12; ++a) {
+        int N = lens[a];
+        for (int j = 0; j < N; ++j) {
+            TwCS cs = unit_root(j * (192 / N), 192);
+            t.v[offs[a] + j].x = cs.c;
+            t.v[offs[a] + j].y = cs.s;
+        }
+    }
+    return t;
+}
 
 constexpr TwTable make_tw_table() {
     TwTable t{};
@@ -86,48 +103,139 @@ constexpr TwTable make_tw_table() {
     return t;
 }
 
+// Double-float numbers: an unevaluated sum hi + lo of two floats with |lo| <= ulp(hi)/2
+// (Dekker 1971; Knuth's TwoSum, FMA-based TwoProduct).  About 48 significant bits on the
+// FP32 pipes.  _rn intrinsics keep the compiler from contracting the error-free steps.
+struct ff { float hi, lo; };
+struct cff { ff x, y; };
+
+struct TwTableFF { cff v[kTwTotal]; };
+
+constexpr TwTableFF make_tw_table_ff() {
+    TwTableFF t{};
+    const int lens[12] = {8, 16, 24, 32, 48, 64, 12, 6, 4, 3, 2, 1};
+    const int offs[12] = {0, 8, 24, 48, 80, 128, 192, 204, 210, 214, 217, 219};
+    for (int a = 0; a < 12; ++a) {
+        int N = lens[a];
+        for (int j = 0; j < N; ++j) {
+            TwCS cs = unit_root(j * (192 / N), 192);
+            float ch = (float)cs.c, sh = (float)cs.s;
+            t.v[offs[a] + j].x.hi = ch;
+            t.v[offs[a] + j].x.lo = (float)(cs.c - (double)ch);
+            t.v[offs[a] + j].y.hi = sh;
+            t.v[offs[a] + j].y.lo = (float)(cs.s - (double)sh);
+        }
+    }
+    return t;
+}
+
 static __constant__ TwTable c_tw = make_tw_table();
+static __constant__ TwTableD c_twd = make_tw_table_d();
+static __constant__ TwTableFF c_twff = make_tw_table_ff();
+
+__device__ __forceinline__ ff ff_two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+__device__ __forceinline__ ff ff_fast_two_sum(float a, float b) {   // |a| >= |b|
+    float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+    ff s = ff_two_sum(a.hi, b.hi);
+    ff t = ff_two_sum(a.lo, b.lo);
+    s.lo = __fadd_rn(s.lo, t.hi);
+    s = ff_fast_two_sum(s.hi, s.lo);
+    s.lo = __fadd_rn(s.lo, t.lo);
+    return ff_fast_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+    float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
+    return ff_fast_two_sum(p, e);
+}
+__device__ __forceinline__ ff ff_neg(ff a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ ff ff_from(double d) {
+    float h = (float)d;
+    return {h, (float)(d - (double)h)};
+}
 
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(s * a.x, s * a.y); }
+__device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(s * a.x, s * a.y); }
+__device__ __forceinline__ float2 cneg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ double2 cneg(double2 a) { return make_double2(-a.x, -a.y); }
+__device__ __forceinline__ cff cadd(cff a, cff b) { return {ff_add(a.x, b.x), ff_add(a.y, b.y)}; }
+__device__ __forceinline__ cff csub(cff a, cff b) { return {ff_add(a.x, ff_neg(b.x)), ff_add(a.y, ff_neg(b.y))}; }
+__device__ __forceinline__ cff cmul(cff a, cff b) {
+    return {ff_add(ff_mul(a.x, b.x), ff_neg(ff_mul(a.y, b.y))), ff_add(ff_mul(a.x, b.y), ff_mul(a.y, b.x))};
+}
+__device__ __forceinline__ cff cscale(cff a, ff s) { return {ff_mul(a.x, s), ff_mul(a.y, s)}; }
+__device__ __forceinline__ cff cneg(cff a) { return {ff_neg(a.x), ff_neg(a.y)}; }
+__device__ __forceinline__ ff neg_of(ff a) { return ff_neg(a); }
+__device__ __forceinline__ float neg_of(float a) { return -a; }
+__device__ __forceinline__ double neg_of(double a) { return -a; }
 // multiply by SIGN * i
-template <int SIGN> __device__ __forceinline__ float2 mul_i(float2 a) {
-    return SIGN > 0 ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+template <int SIGN, class T> __device__ __forceinline__ T mul_i(T a) {
+    T r;
+    if (SIGN > 0) { r.x = neg_of(a.y); r.y = a.x; }
+    else { r.x = a.y; r.y = neg_of(a.x); }
+    return r;
 }
 
-template <int N, int SIGN> __device__ __forceinline__ void mul_tw(float2 &v, int j) {
+__device__ __forceinline__ float2 tw_entry(const float2 *, int i) { return c_tw.v[i]; }
+__device__ __forceinline__ double2 tw_entry(const double2 *, int i) { return c_twd.v[i]; }
+__device__ __forceinline__ cff tw_entry(const cff *, int i) { return c_twff.v[i]; }
+
+// real constants in the element precision
+__device__ __forceinline__ float real_const(const float2 *, double c) { return (float)c; }
+__device__ __forceinline__ double real_const(const double2 *, double c) { return c; }
+__device__ __forceinline__ ff real_const(const cff *, double c) { return ff_from(c); }
+
+template <int N, int SIGN, class T> __device__ __forceinline__ void mul_tw(T &v, int j) {
     // j is a compile-time constant after unrolling; trivial roots skip the multiply
     if (j == 0) return;
     if (4 * j == N) { v = mul_i<SIGN>(v); return; }
-    if (2 * j == N) { v = make_float2(-v.x, -v.y); return; }
+    if (2 * j == N) { v = cneg(v); return; }
     if (4 * j == 3 * N) { v = mul_i<-SIGN>(v); return; }
-    float2 w = c_tw.v[tw_off<N>() + j];
-    if (SIGN < 0) w.y = -w.y;
+    T w = tw_entry((const T *)nullptr, tw_off<N>() + j);
+    if (SIGN < 0) w.y = neg_of(w.y);
     v = cmul(v, w);
 }
 
-template <int SIGN> __device__ __forceinline__ void bfly2(float2 &a, float2 &b) {
-    float2 t = a;
+template <int SIGN, class T> __device__ __forceinline__ void bfly2(T &a, T &b) {
+    T t = a;
     a = cadd(t, b);
     b = csub(t, b);
 }
 
-template <int SIGN> __device__ __forceinline__ void bfly4(float2 &a, float2 &b, float2 &c, float2 &d) {
-    float2 s0 = cadd(a, c), d0 = csub(a, c), s1 = cadd(b, d), d1 = mul_i<SIGN>(csub(b, d));
+template <int SIGN, class T> __device__ __forceinline__ void bfly4(T &a, T &b, T &c, T &d) {
+    T s0 = cadd(a, c), d0 = csub(a, c), s1 = cadd(b, d), d1 = mul_i<SIGN>(csub(b, d));
     a = cadd(s0, s1);
     c = csub(s0, s1);
     b = cadd(d0, d1);
     d = csub(d0, d1);
 }
 
-template <int SIGN> __device__ __forceinline__ void bfly3(float2 &a, float2 &b, float2 &c) {
-    const float h = 0.86602540378443864676f;   // sqrt(3)/2
-    float2 t1 = cadd(b, c), t2 = csub(b, c);
-    float2 m = make_float2(a.x - 0.5f * t1.x, a.y - 0.5f * t1.y);
-    float2 r = mul_i<SIGN>(make_float2(h * t2.x, h * t2.y));
+template <int SIGN, class T> __device__ __forceinline__ void bfly3(T &a, T &b, T &c) {
+    // sqrt(3)/2 and 1/2 in the element precision
+    const auto h = real_const((const T *)nullptr, 0.86602540378443864676372317075294);
+    const auto half = real_const((const T *)nullptr, 0.5);
+    T t1 = cadd(b, c), t2 = csub(b, c);
+    T m = csub(a, cscale(t1, half));
+    T r = mul_i<SIGN>(cscale(t2, h));
     a = cadd(a, t1);
     b = cadd(m, r);
     c = csub(m, r);
@@ -138,7 +246,7 @@ template <int N> __host__ __device__ constexpr int first_radix() {
 }
 
 // In-place DIF on x[0], x[S], ..., x[(N-1) S]; output in digit-reversed slots.
-template <int N, int SIGN, int S> __device__ __forceinline__ void dif(float2 *x) {
+template <int N, int SIGN, int S, class T> __device__ __forceinline__ void dif(T *x) {
     if constexpr (N > 1) {
         constexpr int R = first_radix<N>();
         constexpr int M = N / R;
@@ -166,9 +274,9 @@ template <int N> __host__ __device__ constexpr int slot_of(int k) {
     }
 }
 
-template <int N, int SIGN> __device__ __forceinline__ void fft_inplace(float2 (&x)[N]) {
+template <int N, int SIGN, class T> __device__ __forceinline__ void fft_inplace(T (&x)[N]) {
     dif<N, SIGN, 1>(x);
-    float2 y[N];
+    T y[N];
     #pragma unroll
     for (int k = 0; k < N; ++k) y[k] = x[slot_of<N>(k)];
     #pragma unroll

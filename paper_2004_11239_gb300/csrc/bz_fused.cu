@@ -12,8 +12,8 @@
 //   -- cluster barrier --
 //   C  planes (own k1):   FFT over j3 (rows), FFT over j2 (registers), times alpha_p (tile
 //                         prefetched by cp.async during A and B), accumulate in registers
-// A prologue forms h = IFFT(fhat) for the CTA's pencils the same way (no twiddle, inverse
-// only) straight into shared memory, so no separate h pass is launched.  DSMEM is reached
+// h = IFFT(fhat) is formed beforehand in FP64 (k_h64_*) and each item's prologue loads the
+// slice of h for the CTA's pencils into shared memory.  DSMEM is reached
 // with ld/st.shared::cluster on mapa addresses.  Each CTA ends with its plane slab of the
 // cluster's partial sum (FP32 over the cluster's terms); a second kernel adds the G
 // partials in FP64 in a fixed order (blocked summation, deterministic).  Global traffic per
@@ -27,14 +27,8 @@ namespace cg = cooperative_groups;
 
 namespace bz {
 
-template <int N> struct FusedC;
-template <> struct FusedC<8> { static constexpr int C = 1; };
-template <> struct FusedC<16> { static constexpr int C = 1; };
-template <> struct FusedC<24> { static constexpr int C = 2; };
-template <> struct FusedC<32> { static constexpr int C = 4; };
-
-template <int N> struct FK {
-    static constexpr int C = FusedC<N>::C;
+template <int N, int C_> struct FK {
+    static constexpr int C = C_;
     static constexpr int PPC = N / C;                 // planes (and pencil rows) per CTA
     static constexpr int LD = N + 1;                  // padded plane row
     static constexpr int THREADS = N * PPC;
@@ -42,7 +36,8 @@ template <int N> struct FK {
     static constexpr size_t TILE = (size_t)PPC * N * N * sizeof(float2);   // alpha tile, h slice
     static constexpr size_t TW = (size_t)3 * N * sizeof(float2);           // one term's twiddles
     static constexpr size_t SMEM = PLANES + 2 * TILE + 2 * TW;
-    static constexpr int MIN_BLOCKS = N <= 16 ? 2 : 1;   // N <= 16: two CTAs per SM fit
+    // two CTAs per SM where registers and shared memory allow it
+    static constexpr int MIN_BLOCKS = (N <= 16 || N * N / C_ <= 128) ? 2 : 1;
 };
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
@@ -104,10 +99,10 @@ __device__ __forceinline__ void phase_a(const float2 *__restrict__ fin, const fl
 // terms [p0 + blk TB, min(p1, p0 + (blk + 1) TB)).  The item's FP32 sum over its terms goes to
 // part[slot * nblk + blk]; it depends only on the instance and the block bounds, so a result
 // does not depend on which other instances share the launch.
-template <int N, bool SCALED>
-__global__ void __launch_bounds__(FK<N>::THREADS, FK<N>::MIN_BLOCKS)
+template <int N, int CC, bool SCALED>
+__global__ void __launch_bounds__(FK<N, CC>::THREADS, FK<N, CC>::MIN_BLOCKS)
 k_fused(ItemArgs a) {
-    using K = FK<N>;
+    using K = FK<N, CC>;
     constexpr int C = K::C, PPC = K::PPC, LD = K::LD, T = K::THREADS;
     extern __shared__ __align__(16) float2 smem[];
     float2 *planes = smem;                                   // [PPC][N][LD]
@@ -142,20 +137,25 @@ k_fused(ItemArgs a) {
         const int t0 = a.p0 + blk * a.TB;
         const int t1 = min(a.p1, t0 + a.TB);
         const float2 *fin = a.fin + (size_t)slot * N3;
-        // prologue: h = IFFT(fhat_b) for the pencils this CTA owns, into the h slice
+        // prologue: the h slice of the pencils this CTA owns, either formed beforehand in FP64
+        // (a.hg) or here in FP32 (no twiddle, inverse only) straight into shared memory
         __syncthreads();                                      // the previous item is done with smem
         fetch_tw(t0, 0);
-        phase_a<N>(fin, nullptr, my, k1, lane);
-        cluster_barrier<C>();
-        {
+        if (a.hg) {
+            const float2 *hs = a.hg + (size_t)slot * N3;
+            #pragma unroll 4
+            for (int j = 0; j < N; ++j) shs[((size_t)pid * N + j) * N + lane] = hs[((size_t)j * N + j2p) * N + lane];
+        } else {
+            phase_a<N>(fin, nullptr, my, k1, lane);
+            cluster_barrier<C>();
             float2 x[N];
             #pragma unroll
             for (int k = 0; k < N; ++k) x[k] = ld_dsmem(pen[k / PPC] + (uint32_t)(k % PPC) * PLANE_BYTES);
             fft_inplace<N, +1>(x);                            // k1 -> j1
             #pragma unroll
             for (int j = 0; j < N; ++j) shs[((size_t)pid * N + j) * N + lane] = x[j];
+            cluster_barrier<C>();                             // planes free again in every CTA
         }
-        cluster_barrier<C>();                                 // planes free again in every CTA
 
         float2 acc[N];
         #pragma unroll
@@ -219,44 +219,127 @@ k_fused(ItemArgs a) {
     }
 }
 
-// acc[k] = sum over g of part[g][k] in FP64 with a fixed shape: thread (kk, s) of a 32 x 8
-// block sums g = s, s + 8, ... for mode k = 32 blockIdx.x + kk; the eight slices are then
-// added in order s = 0..7.
+// h = IFFT(fhat) in FP64 (stored FP32) for the fused path.  FP32 transforms leave a noise
+// floor of about eps max|h| over the whole grid, and the product h g_p turns that floor into
+// errors where g_p is large and h is small; forming h in FP64 removes that half of the
+// rounding error (the per-term g_p stay FP32).  FP64 throughput per SM is low on this GPU,
+// so the transform runs as three line passes (axis 3, 2, 1) with eight lines per CTA: the
+// N^2 lines of a pass spread over (nearly) every SM.
+constexpr int kH64Lines = 8;
+
+__device__ __forceinline__ double2 load_c(const void *f, int dtype, size_t i) {
+    if (dtype == BZ_C128) return ((const double2 *)f)[i];
+    float2 v = ((const float2 *)f)[i];
+    return make_double2(v.x, v.y);
+}
+
+// AXIS 3: line (k1, k2) contiguous, from f into scr; AXIS 2: line (k1, k3) with stride N in
+// scr; AXIS 1: line (j2, j3) with stride N^2, from scr into h (FP32).
+template <int N, int AXIS>
+__global__ void __launch_bounds__(kH64Lines)
+k_h64_pass(const void *f, int dtype, const int *slots, const int *count_dev, double2 *scr, float2 *h) {
+    constexpr int N2 = N * N;
+    const int b = blockIdx.y;
+    if (count_dev && b >= *count_dev) return;
+    const int slot = slots ? slots[b] : b;
+    const int line = blockIdx.x * kH64Lines + threadIdx.x;
+    if (line >= N2) return;
+    const size_t vol = (size_t)slot * N * N2;
+    size_t base, stride;
+    if (AXIS == 3) { base = vol + (size_t)line * N; stride = 1; }
+    else if (AXIS == 2) { base = vol + (size_t)(line / N) * N2 + (line % N); stride = N; }
+    else { base = vol + line; stride = N2; }
+    double2 x[N];
+    #pragma unroll
+    for (int k = 0; k < N; ++k)
+        x[k] = AXIS == 3 ? load_c(f, dtype, base + k * stride) : scr[base + k * stride];
+    fft_inplace<N, +1>(x);
+    if (AXIS == 1) {
+        #pragma unroll
+        for (int j = 0; j < N; ++j) h[base + j * stride] = make_float2((float)x[j].x, (float)x[j].y);
+    } else {
+        #pragma unroll
+        for (int j = 0; j < N; ++j) scr[base + j * stride] = x[j];
+    }
+}
+
+template <int N>
+static bz_status h64_n(const void *f, int dtype, const int *slots, const int *count_dev, int count, double2 *scr,
+                       float2 *h, cudaStream_t st) {
+    const dim3 grid((N * N + kH64Lines - 1) / kH64Lines, count);
+    k_h64_pass<N, 3><<<grid, kH64Lines, 0, st>>>(f, dtype, slots, count_dev, scr, h);
+    k_h64_pass<N, 2><<<grid, kH64Lines, 0, st>>>(f, dtype, slots, count_dev, scr, h);
+    k_h64_pass<N, 1><<<grid, kH64Lines, 0, st>>>(f, dtype, slots, count_dev, scr, h);
+    BZ_CUDA_TRY(cudaGetLastError());
+    return BZ_OK;
+}
+
+bz_status h64_launch(int N, const void *f, int dtype, const int *slots, const int *count_dev, int count,
+                     double2 *scr, float2 *h, cudaStream_t st) {
+    if (count <= 0) return BZ_OK;
+    switch (N) {
+        case 8: return h64_n<8>(f, dtype, slots, count_dev, count, scr, h, st);
+        case 16: return h64_n<16>(f, dtype, slots, count_dev, count, scr, h, st);
+        case 24: return h64_n<24>(f, dtype, slots, count_dev, count, scr, h, st);
+        case 32: return h64_n<32>(f, dtype, slots, count_dev, count, scr, h, st);
+    }
+    return BZ_ERR_UNSUPPORTED;
+}
+
+// acc[k] = sum over g of part[g][k] with a fixed shape: thread (kk, s) of a 32 x 8 block sums
+// g = s, s + 8, ... for mode k = 32 blockIdx.x + kk with Kahan compensation in FP32, then the
+// eight slices are added in order s = 0..7 (compensated).  FP32 pipes only.
+struct Kahan2 {
+    float sr = 0.f, si = 0.f, cr = 0.f, ci = 0.f;
+    __device__ __forceinline__ void add(float vr, float vi) {
+        float yr = vr - cr, yi = vi - ci;
+        float tr = sr + yr, ti = si + yi;
+        cr = (tr - sr) - yr;
+        ci = (ti - si) - yi;
+        sr = tr;
+        si = ti;
+    }
+};
+
 __global__ void __launch_bounds__(256) k_reduce_parts(const float2 *__restrict__ part, int G, int n3,
                                                      double2 *__restrict__ acc) {
-    __shared__ double2 red[8][32];
+    __shared__ float4 red[8][32];
     const int kk = threadIdx.x % 32, sl = threadIdx.x / 32;
     const int k = blockIdx.x * 32 + kk;
-    double sr = 0.0, si = 0.0;
+    Kahan2 s;
     if (k < n3) {
         for (int g = sl; g < G; g += 8) {
             float2 v = part[(size_t)g * n3 + k];
-            sr += v.x;
-            si += v.y;
+            s.add(v.x, v.y);
         }
     }
-    red[sl][kk] = make_double2(sr, si);
+    red[sl][kk] = make_float4(s.sr, s.si, s.cr, s.ci);
     __syncthreads();
     if (sl == 0 && k < n3) {
-        double2 t = red[0][kk];
+        Kahan2 t;
         #pragma unroll
-        for (int u = 1; u < 8; ++u) { t.x += red[u][kk].x; t.y += red[u][kk].y; }
-        acc[k] = t;
+        for (int u = 0; u < 8; ++u) {
+            float4 q = red[u][kk];
+            t.add(q.x, q.y);
+            t.add(-q.z, -q.w);
+        }
+        acc[k] = make_double2((double)t.sr - (double)t.cr, (double)t.si - (double)t.ci);
     }
 }
 
-template <int N, bool SC> static cudaError_t set_smem() {
-    return cudaFuncSetAttribute(k_fused<N, SC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FK<N>::SMEM);
+template <int N, int C, bool SC> static cudaError_t set_smem() {
+    return cudaFuncSetAttribute(k_fused<N, C, SC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)FK<N, C>::SMEM);
 }
 
-template <int N> static cudaError_t fused_setup_n(int *G) {
-    using K = FK<N>;
-    cudaError_t e = set_smem<N, false>();
-    if (e == cudaSuccess) e = set_smem<N, true>();
+template <int N, int C> static cudaError_t setup_nc(int *G) {
+    using K = FK<N, C>;
+    cudaError_t e = set_smem<N, C, false>();
+    if (e == cudaSuccess) e = set_smem<N, C, true>();
     if (e != cudaSuccess) return e;
-    if (K::C == 1) {
+    if (C == 1) {
         int per_sm = 0, dev = 0, sms = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused<N, true>, K::THREADS, K::SMEM);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused<N, C, true>, K::THREADS, K::SMEM);
         if (e != cudaSuccess) return e;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -265,64 +348,81 @@ template <int N> static cudaError_t fused_setup_n(int *G) {
         cudaLaunchConfig_t cfg = {};
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = K::C;
+        attr[0].val.clusterDim.x = C;
         attr[0].val.clusterDim.y = 1;
         attr[0].val.clusterDim.z = 1;
-        cfg.gridDim = dim3(K::C * 64);
+        cfg.gridDim = dim3(C * 64);
         cfg.blockDim = dim3(K::THREADS);
         cfg.dynamicSmemBytes = K::SMEM;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        e = cudaOccupancyMaxActiveClusters(G, k_fused<N, true>, &cfg);
+        e = cudaOccupancyMaxActiveClusters(G, k_fused<N, C, true>, &cfg);
         if (e != cudaSuccess) return e;
     }
     return *G > 0 ? cudaSuccess : cudaErrorInvalidConfiguration;
 }
 
-// Number of resident clusters for the plan's N (0 when the fused path does not apply).
-cudaError_t fused_setup(int N, int *G) {
-    *G = 0;
+// Cluster sizes compiled for each N (the plan times them and keeps the fastest).
+int fused_candidates(int N, int *cs) {
     switch (N) {
-        case 8: return fused_setup_n<8>(G);
-        case 16: return fused_setup_n<16>(G);
-        case 24: return fused_setup_n<24>(G);
-        case 32: return fused_setup_n<32>(G);
+        case 8: cs[0] = 1; return 1;
+        case 16: cs[0] = 1; cs[1] = 2; return 2;
+        case 24: cs[0] = 2; cs[1] = 3; return 2;
+        case 32: cs[0] = 4; cs[1] = 8; return 2;
     }
+    return 0;
+}
+
+// Resident clusters for (N, C) (0 when the fused path does not apply).
+cudaError_t fused_setup(int N, int C, int *G) {
+    *G = 0;
+    if (N == 8 && C == 1) return setup_nc<8, 1>(G);
+    if (N == 16 && C == 1) return setup_nc<16, 1>(G);
+    if (N == 16 && C == 2) return setup_nc<16, 2>(G);
+    if (N == 24 && C == 2) return setup_nc<24, 2>(G);
+    if (N == 24 && C == 3) return setup_nc<24, 3>(G);
+    if (N == 32 && C == 4) return setup_nc<32, 4>(G);
+    if (N == 32 && C == 8) return setup_nc<32, 8>(G);
     return cudaErrorInvalidValue;
 }
 
-template <int N, bool SC> static bz_status launch_n(const Plan &pl, const ItemArgs &a, cudaStream_t st) {
-    using K = FK<N>;
+template <int N, int C, bool SC> static bz_status launch_nc(const Plan &pl, const ItemArgs &a, cudaStream_t st) {
+    using K = FK<N, C>;
     const int G = pl.fused_G;
-    if (K::C == 1) {
-        k_fused<N, SC><<<G, K::THREADS, K::SMEM, st>>>(a);
+    if (C == 1) {
+        k_fused<N, C, SC><<<G, K::THREADS, K::SMEM, st>>>(a);
     } else {
         cudaLaunchConfig_t cfg = {};
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = K::C;
+        attr[0].val.clusterDim.x = C;
         attr[0].val.clusterDim.y = 1;
         attr[0].val.clusterDim.z = 1;
-        cfg.gridDim = dim3(G * K::C);
+        cfg.gridDim = dim3(G * C);
         cfg.blockDim = dim3(K::THREADS);
         cfg.dynamicSmemBytes = K::SMEM;
         cfg.stream = st;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        BZ_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_fused<N, SC>, a));
+        BZ_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_fused<N, C, SC>, a));
     }
     BZ_CUDA_TRY(cudaGetLastError());
     return BZ_OK;
 }
 
+template <int N, int C> static bz_status launch_sc(const Plan &pl, const ItemArgs &a, cudaStream_t st) {
+    return a.gsc ? launch_nc<N, C, true>(pl, a, st) : launch_nc<N, C, false>(pl, a, st);
+}
+
 bz_status launch_fused(const Plan &pl, const ItemArgs &a, cudaStream_t st) {
-    const bool sc = a.gsc != nullptr;
-    switch (pl.N) {
-        case 8: return sc ? launch_n<8, true>(pl, a, st) : launch_n<8, false>(pl, a, st);
-        case 16: return sc ? launch_n<16, true>(pl, a, st) : launch_n<16, false>(pl, a, st);
-        case 24: return sc ? launch_n<24, true>(pl, a, st) : launch_n<24, false>(pl, a, st);
-        case 32: return sc ? launch_n<32, true>(pl, a, st) : launch_n<32, false>(pl, a, st);
-    }
+    const int N = pl.N, C = pl.fused_C;
+    if (N == 8 && C == 1) return launch_sc<8, 1>(pl, a, st);
+    if (N == 16 && C == 1) return launch_sc<16, 1>(pl, a, st);
+    if (N == 16 && C == 2) return launch_sc<16, 2>(pl, a, st);
+    if (N == 24 && C == 2) return launch_sc<24, 2>(pl, a, st);
+    if (N == 24 && C == 3) return launch_sc<24, 3>(pl, a, st);
+    if (N == 32 && C == 4) return launch_sc<32, 4>(pl, a, st);
+    if (N == 32 && C == 8) return launch_sc<32, 8>(pl, a, st);
     return BZ_ERR_UNSUPPORTED;
 }
 
@@ -331,13 +431,24 @@ bz_status launch_fused(const Plan &pl, const ItemArgs &a, cudaStream_t st) {
 bz_status collide_fused(Plan &pl, int p0, int p1, cudaStream_t st, int *launches) {
     const int n3 = pl.N * pl.N * pl.N;
     ItemArgs a;
-    a.fin = pl.fin; a.tw = pl.tw; a.alpha = pl.alpha; a.part = pl.part;
+    a.fin = pl.fin; a.tw = pl.tw; a.alpha = pl.alpha; a.part = pl.part; a.hg = pl.h;
     a.count = 1; a.p0 = p0; a.p1 = p1; a.M = pl.M; a.N_rho = pl.N_rho;
     const int nt = p1 - p0;
     a.TB = nt > 0 ? (nt + pl.fused_G - 1) / pl.fused_G : 1;
     a.nblk = nt > 0 ? (nt + a.TB - 1) / a.TB : 0;
+    bz_status s = BZ_OK;
+    if (pl.h_fp64) {
+        tm_begin(pl, st);
+        s = h64_launch(pl.N, pl.src ? pl.src : (const void *)pl.fin, pl.src ? pl.src_dtype : BZ_C64,
+                       nullptr, nullptr, 1, pl.scr64, pl.h, st);
+        if (s != BZ_OK) return s;
+        tm_end(pl, st, TK_OTHER);
+        if (launches) *launches += 3;
+    } else {
+        a.hg = nullptr;                                   // h formed in FP32 in the item prologue
+    }
     tm_begin(pl, st);
-    bz_status s = launch_fused(pl, a, st);
+    s = launch_fused(pl, a, st);
     if (s != BZ_OK) return s;
     tm_end(pl, st, TK_FUSED);
     tm_begin(pl, st);

@@ -58,7 +58,14 @@ struct Plan {
     double *mom = nullptr;          // moments scratch
     // fused cluster pipeline (N <= 32)
     int use_fused = 0;              // 1: bz_collide runs k_fused
+    int fused_C = 0;                // CTAs per cluster
     int fused_G = 0;                // resident clusters (persistent grid)
+    float fused_ms = 0.f;           // timed collide of the selected cluster size
+    int h_fp64 = 1;                 // fused path: h formed in FP64 (1) or in FP32 in-kernel (0)
+    double2 *fin64 = nullptr;       // [N^3] FP64 stage input (RK4) for the FP64 h pass
+    double2 *scr64 = nullptr;       // [N^3] FP64 scratch of the h pass
+    const void *src = nullptr;      // FP64-capable source of h for the next fused collide
+    int src_dtype = BZ_C128;
     float2 *part = nullptr;         // [fused_G][N^3] per-cluster partial sums
     size_t ws_bytes = 0;
     int last_launches = 0;
@@ -102,12 +109,17 @@ struct ItemArgs {
     const float2 *alpha = nullptr;   // [P][N^3]
     const float *gsc = nullptr;      // [slots][N_rho] radial scale r_i^(gamma_b - gamma_plan), or null
     float2 *part = nullptr;          // [slots][nblk][N^3] per-item partial sums
+    const float2 *hg = nullptr;      // [slots][N^3] h = IFFT(fhat), formed in FP64, stored FP32
     const int *slots = nullptr;      // device [count] or null
     const int *count_dev = nullptr;  // device instance count, or null (use count)
     int count = 1, p0 = 0, p1 = 0, TB = 1, nblk = 0, M = 1, N_rho = 1;
 };
-cudaError_t fused_setup(int N, int *G);
+int fused_candidates(int N, int *cs);
+cudaError_t fused_setup(int N, int C, int *G);
 bz_status launch_fused(const Plan &pl, const ItemArgs &a, cudaStream_t st);
+// h[slot] = IFFT(f[slot]) computed in FP64 and stored FP32 for the active slots (N <= 32).
+bz_status h64_launch(int N, const void *f, int dtype, const int *slots, const int *count_dev, int count,
+                     double2 *scr, float2 *h, cudaStream_t st);
 bz_status collide_fused(Plan &pl, int p0, int p1, cudaStream_t st, int *launches);
 cudaError_t collide_set_attributes(int N);
 int supported_N(int N);

@@ -9,7 +9,7 @@ namespace bz {
 
 namespace {
 
-__global__ void k_rk_init(const void *fhat, int dtype, double2 *f0, float2 *fin, int n) {
+__global__ void k_rk_init(const void *fhat, int dtype, double2 *f0, float2 *fin, double2 *fin64, int n) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double2 v;
@@ -20,12 +20,13 @@ __global__ void k_rk_init(const void *fhat, int dtype, double2 *f0, float2 *fin,
     }
     f0[i] = v;
     fin[i] = make_float2((float)v.x, (float)v.y);
+    if (fin64) fin64[i] = v;
 }
 
 // stage s in {1, 2, 3, 4}; k = acc (FP64 derivative of stage s)
 __global__ void k_rk_stage(const double2 *__restrict__ k, double2 *__restrict__ f0,
-                           double2 *__restrict__ fsum, float2 *__restrict__ fin, int n, int stage,
-                           double dt) {
+                           double2 *__restrict__ fsum, float2 *__restrict__ fin, double2 *__restrict__ fin64,
+                           int n, int stage, double dt) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double2 kv = k[i], a = f0[i], y;
@@ -43,6 +44,7 @@ __global__ void k_rk_stage(const double2 *__restrict__ k, double2 *__restrict__ 
         f0[i] = y;
     }
     fin[i] = make_float2((float)y.x, (float)y.y);
+    if (fin64) fin64[i] = y;
 }
 
 __global__ void k_rk_out(const double2 *f0, void *fhat, int dtype, int n) {
@@ -94,13 +96,15 @@ bz_status rk4_steps(Plan &pl, void *fhat, int dtype, double dt, int nsteps, cuda
     const int n = pl.N * pl.N * pl.N;
     const int bs = 256, gs = (n + bs - 1) / bs;
     double2 *f0 = pl.rk, *fsum = pl.rk + n;
-    k_rk_init<<<gs, bs, 0, st>>>(fhat, dtype, f0, pl.fin, n);
+    k_rk_init<<<gs, bs, 0, st>>>(fhat, dtype, f0, pl.fin, pl.fin64, n);
+    pl.src = pl.fin64;             // stage inputs for the FP64 h pass (fused plans)
+    pl.src_dtype = BZ_C128;
     int nl = 1;
     for (int step = 0; step < nsteps; ++step) {
         for (int stage = 1; stage <= 4; ++stage) {
             bz_status s = collide_core(pl, 0, pl.P, st, &nl);
             if (s != BZ_OK) return s;
-            k_rk_stage<<<gs, bs, 0, st>>>(pl.acc, f0, fsum, pl.fin, n, stage, dt);
+            k_rk_stage<<<gs, bs, 0, st>>>(pl.acc, f0, fsum, pl.fin, pl.fin64, n, stage, dt);
             ++nl;
         }
     }

@@ -172,3 +172,35 @@ def test_rk4_matches_oracle_trajectory(bz, pipeline):
     # mass is conserved exactly by the scheme (Qhat_0 = 0)
     assert got[0, 0, 0] == f0[0, 0, 0]
     plan.close()
+
+
+@pytest.mark.parametrize("N,cluster", [(16, 1), (16, 2), (24, 2), (24, 3), (32, 4), (32, 8)])
+def test_every_cluster_size_matches_oracle(bz, N, cluster):
+    L = 10.0
+    R = bi.R_from_L(L)
+    fhat = bi.random_mixture(N, L, seed=31 + N)
+    plan = bz.bz_plan_create_ex(N, L, R, -1.0, 0.5, 2, 12, pipeline=bz.BZ_PIPE_FUSED, cluster=cluster)
+    info = bz.bz_plan_pipeline(plan)
+    assert info["pipeline"] == "fused" and info["cluster"] == cluster and info["clusters"] > 0
+    got = _gpu_collide(bz, plan, fhat)
+    ref = spectral.collide(spectral.OraclePlan(N, L, R, -1.0, kernels.Kernel("family", 0.5), 2, 12), fhat)
+    err = _rel(got, ref)
+    print(f"N={N} cluster={cluster} G={info['clusters']}: rel_Linf={err:.2e}")
+    assert err <= TOL
+    plan.close()
+
+
+@pytest.mark.parametrize("hp,bound", [(1, TOL), (2, 2.5e-5)])
+def test_h_precision_options(bz, hp, bound):
+    """FP64-formed h (default) meets the FP32 bar on an under-resolved N = 32 mixture; the
+    FP32-in-kernel h option trades about twice the error for speed and stays within 2.5e-5."""
+    N, L = 32, 10.0
+    R = bi.R_from_L(L)
+    fhat = bi.random_mixture(N, L, seed=63)
+    plan = bz.bz_plan_create_ex(N, L, R, -1.0, 0.5, 2, 12, h_precision=hp)
+    got = _gpu_collide(bz, plan, fhat)
+    ref = spectral.collide(spectral.OraclePlan(N, L, R, -1.0, kernels.Kernel("family", 0.5), 2, 12), fhat)
+    err = _rel(got, ref)
+    print(f"N=32 h_precision={hp}: rel_Linf={err:.2e}")
+    assert err <= bound
+    plan.close()
