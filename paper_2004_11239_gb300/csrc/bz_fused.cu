@@ -263,13 +263,70 @@ k_h64_pass(const void *f, int dtype, const int *slots, const int *count_dev, dou
     }
 }
 
+// Power-of-two N: one warp (N <= 16: a lane segment) per line, radix-2 decimation in
+// frequency across lanes with shuffles, lane l ends with frequency bitrev(l).  Each lane's
+// twiddles for the log2 N stages are read once.  32 lanes per line keep many more FP64
+// operations in flight than one thread per line.
+template <int N> __device__ __forceinline__ int bitrev_n(int l) {
+    int r = 0;
+    #pragma unroll
+    for (int b = 1; b < N; b <<= 1) r = (r << 1) | ((l & b) ? 1 : 0);
+    return r;
+}
+
+template <int N, int AXIS>
+__global__ void __launch_bounds__(256)
+k_h64_warp(const void *f, int dtype, const int *slots, const int *count_dev, double2 *scr, float2 *h) {
+    constexpr int N2 = N * N, LPW = 32 / N, LINES = 8 * LPW;     // lines per warp, per CTA
+    const int b = blockIdx.y;
+    if (count_dev && b >= *count_dev) return;
+    const int slot = slots ? slots[b] : b;
+    const int lane = threadIdx.x & 31, l = lane % N;
+    const int line = blockIdx.x * LINES + (threadIdx.x >> 5) * LPW + lane / N;
+    if (line >= N2) return;                                   // whole segments exit together
+    // twiddle of this lane at each stage (half-size hs): exp(+2 pi i (l mod hs) / (2 hs))
+    double2 tw[16];
+    int st = 0;
+    #pragma unroll
+    for (int hs = N / 2; hs >= 1; hs >>= 1, ++st) {
+        const int j = (l % hs) * (N / (2 * hs));              // index into the length-N roots
+        tw[st] = c_twd.v[tw_off<N>() + j];
+    }
+    const size_t vol = (size_t)slot * N * N2;
+    size_t base, stride;
+    if (AXIS == 3) { base = vol + (size_t)line * N; stride = 1; }
+    else if (AXIS == 2) { base = vol + (size_t)(line / N) * N2 + (line % N); stride = N; }
+    else { base = vol + line; stride = N2; }
+    double2 v = AXIS == 3 ? load_c(f, dtype, base + (size_t)l * stride) : scr[base + (size_t)l * stride];
+    st = 0;
+    #pragma unroll
+    for (int hs = N / 2; hs >= 1; hs >>= 1, ++st) {
+        double2 p;
+        p.x = __shfl_xor_sync(0xffffffffu, v.x, hs);
+        p.y = __shfl_xor_sync(0xffffffffu, v.y, hs);
+        if (l & hs) v = cmul(csub(p, v), tw[st]);
+        else v = cadd(v, p);
+    }
+    const size_t o = base + (size_t)bitrev_n<N>(l) * stride;
+    if (AXIS == 1) h[o] = make_float2((float)v.x, (float)v.y);
+    else scr[o] = v;
+}
+
 template <int N>
 static bz_status h64_n(const void *f, int dtype, const int *slots, const int *count_dev, int count, double2 *scr,
                        float2 *h, cudaStream_t st) {
-    const dim3 grid((N * N + kH64Lines - 1) / kH64Lines, count);
-    k_h64_pass<N, 3><<<grid, kH64Lines, 0, st>>>(f, dtype, slots, count_dev, scr, h);
-    k_h64_pass<N, 2><<<grid, kH64Lines, 0, st>>>(f, dtype, slots, count_dev, scr, h);
-    k_h64_pass<N, 1><<<grid, kH64Lines, 0, st>>>(f, dtype, slots, count_dev, scr, h);
+    if constexpr ((N & (N - 1)) == 0) {
+        constexpr int LINES = 8 * (32 / N);
+        const dim3 grid((N * N + LINES - 1) / LINES, count);
+        k_h64_warp<N, 3><<<grid, 256, 0, st>>>(f, dtype, slots, count_dev, scr, h);
+        k_h64_warp<N, 2><<<grid, 256, 0, st>>>(f, dtype, slots, count_dev, scr, h);
+        k_h64_warp<N, 1><<<grid, 256, 0, st>>>(f, dtype, slots, count_dev, scr, h);
+    } else {
+        const dim3 grid((N * N + kH64Lines - 1) / kH64Lines, count);
+        k_h64_pass<N, 3><<<grid, kH64Lines, 0, st>>>(f, dtype, slots, count_dev, scr, h);
+        k_h64_pass<N, 2><<<grid, kH64Lines, 0, st>>>(f, dtype, slots, count_dev, scr, h);
+        k_h64_pass<N, 1><<<grid, kH64Lines, 0, st>>>(f, dtype, slots, count_dev, scr, h);
+    }
     BZ_CUDA_TRY(cudaGetLastError());
     return BZ_OK;
 }
