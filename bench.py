@@ -34,6 +34,10 @@ WORKLOADS = {
     "single_n16": dict(N=16, N_rho=16, M=12, gamma=0.0, s=0.5, R=None, L=10.0, dt=None,
                        data="c1", desc="single collide, N=16, N_rho=16, M=12, gamma=0, s=0.5, "
                                        "L=10, two Maxwellians at +-2 e1"),
+    "serve": dict(N=None, N_rho=None, M=None, gamma=None, s=None, R=None, L=10.0, dt=0.02,
+                  data="mixtures", desc="continuous-batching server: 64 requests, Poisson arrivals at 200/s, "
+                  "N in {16,24,32}, N_rho=N, M in {12,32}, gamma in {0,-1,-2}, s in {0.25,0.5}, RK4 to "
+                  "t=0.2 (dt=0.02, 10 steps), two-Maxwellian data; plans warmed before the trace; 32 terms per work item"),
     "batch_4096": dict(N=None, N_rho=None, M=32, gamma=None, s=None, R=None, L=10.0, dt=0.01,
                        data="mixtures", desc="4096 instances (3072 at N=16, 1024 at N=32), N_rho=N, "
                        "M=32, gamma in {0,-1}, s in {0.25,0.5,0.75}, two-Maxwellian mixtures, "
@@ -411,6 +415,78 @@ def run_batch(args, w):
     return 0
 
 
+def run_serve(args, w):
+    """Seeded Poisson trace through bz_submit / bz_poll; latency percentiles and throughput."""
+    import numpy as np
+    import torch
+    import bz_inputs as bi
+    import paper_2004_11239_gb300 as bz
+    torch.cuda.set_device(0)
+    L = w["L"]
+    R = bi.R_from_L(L)
+    n_req, rate = 64, 200.0
+    u = bi.SplitMix64(77).uniform(4 * n_req)
+    arrivals = bi.poisson_arrivals(n_req, rate, seed=78)
+    Ns, Ms, gs, ss = [16, 24, 32], [12, 32], [0.0, -1.0, -2.0], [0.25, 0.5]
+    reqs = []
+    for i in range(n_req):
+        N = Ns[int(u[4 * i] * 3)]
+        reqs.append(dict(N=N, M=Ms[int(u[4 * i + 1] * 2)], gamma=gs[int(u[4 * i + 2] * 3)],
+                         s=ss[int(u[4 * i + 3] * 2)], f=bi.random_mixture(N, L, seed=1000 + i)))
+    server = bz.bz_server_create(200 << 30, max_batch=32, terms_per_item=32)
+
+    def submit(r, t_end):
+        return bz.bz_submit(server, r["f"], r["N"], L, R, r["gamma"], r["s"], r["N"], r["M"], 0.0, t_end, w["dt"])
+
+    def wait(tickets):
+        out = {}
+        while len(out) < len(tickets):
+            for t, N in tickets:
+                if t not in out:
+                    res = bz.bz_poll(server, t, N)
+                    if res is not None:
+                        out[t] = res
+            time.sleep(0.0005)
+        return out
+
+    # warm every (N, M, s) group once: plan tables, batches, graphs
+    keys = {}
+    for r in reqs:
+        keys.setdefault((r["N"], r["M"], r["s"]), r)
+    wait([(submit(r, w["dt"]), r["N"]) for r in keys.values()])
+    rates = [rate] if args.rates is None else [float(x) for x in args.rates.split(",")]
+    sweep = []
+    for rt in rates:
+        arr = bi.poisson_arrivals(n_req, rt, seed=78)
+        t0 = time.perf_counter()
+        tickets = []
+        with ClockSampler(0) as clk:
+            for r, ta in zip(reqs, arr):
+                delay = t0 + ta - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+                tickets.append((submit(r, 0.2), r["N"]))
+            res = wait(tickets)
+        wall = time.perf_counter() - t0
+        lat = np.array([res[t][0].latency_s for t, _ in tickets])
+        que = np.array([res[t][0].queue_s for t, _ in tickets])
+        sweep.append({"rate": rt, "requests_per_s": n_req / wall, "wall_s": wall,
+                      "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99)),
+                      "queue_p50_s": float(np.percentile(que, 50)), "queue_p99_s": float(np.percentile(que, 99)),
+                      "all_ok": all(res[t][0].status == 0 for t, _ in tickets), "clocks": clk.summary()})
+    server.close()
+    head = sweep[-1]
+    line = {"metric": "served requests/s", "value": head["requests_per_s"], "unit": "requests/s", "n_gpus": 1,
+            "steps": n_req, "warmup": len(keys), "ms_per_step": 1e3 * head["wall_s"] / n_req,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": w["desc"], "groups": len(keys), "rate": head["rate"]},
+            "latency_s": {"p50": head["latency_p50_s"], "p99": head["latency_p99_s"]},
+            "queue_s": {"p50": head["queue_p50_s"], "p99": head["queue_p99_s"]},
+            "q_evals_per_s": 4 * 10 * n_req / head["wall_s"], "sweep": sweep}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -419,12 +495,15 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="rk4_n32", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--rates", default=None, help="serve workload: comma-separated arrival rates (req/s)")
     ap.add_argument("--h-precision", type=int, default=0, choices=[0, 1, 2],
                     help="h = IFFT(fhat) precision on the fused path: 0 auto (FP64), 1 FP64, 2 FP32")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if args.workload == "batch_4096":
         return run_batch(args, w)
+    if args.workload == "serve":
+        return run_serve(args, w)
     if args.impl == "reference":
         return run_reference(args, w)
     return run_ours(args, w)

@@ -60,15 +60,21 @@ __global__ void k_batch_load(const void *fhat, int dtype, const int *slots, cons
     }
 }
 
+// Sum of an instance's block partials in block order, Kahan-compensated on the FP32 pipes
+// (the FP64 units of this GPU are far slower); returned in FP64.
 __device__ __forceinline__ double2 sum_blocks(const float2 *part, int slot, int nblk, int n3, int k) {
-    double sr = 0.0, si = 0.0;
+    float sr = 0.f, si = 0.f, cr = 0.f, ci = 0.f;
     const float2 *p = part + (size_t)slot * nblk * n3 + k;
     for (int blk = 0; blk < nblk; ++blk) {
         float2 v = p[(size_t)blk * n3];
-        sr += v.x;
-        si += v.y;
+        float yr = v.x - cr, yi = v.y - ci;
+        float tr = sr + yr, ti = si + yi;
+        cr = (tr - sr) - yr;
+        ci = (ti - si) - yi;
+        sr = tr;
+        si = ti;
     }
-    return make_double2(sr, si);
+    return make_double2((double)sr - (double)cr, (double)si - (double)ci);
 }
 
 __global__ void k_batch_out(const float2 *part, int nblk, const int *slots, const int *count_dev, int n3,
