@@ -169,6 +169,26 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def max_over_ranks(x: float) -> float:
+    """Maximum of a per-rank float over the default process group (identity without one)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: float, ms_local: float):
+    """Whole-job units per second: all ranks' units over the slowest rank's time (replicas)."""
+    import torch.distributed as dist
+    ws = dist.get_world_size() if dist.is_available() and dist.is_initialized() else 1
+    ms = max_over_ranks(ms_local)
+    return units_per_rank * ws / (ms / 1e3), ms
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -276,12 +296,7 @@ def run_ours(args, w):
     ms = e0.elapsed_time(e1)
     kern = {name: bz.bz_plan_timing(plan, kind) for name, kind in bz.KERNEL_KINDS.items()}
     bz.bz_plan_set_timing(plan, 0)
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = evals_per_step * args.steps * ws / (ms / 1e3)
+    value, ms = job_throughput(evals_per_step * args.steps, ms)
 
     # end to end through the public API with host buffers (pinned), copies inside the region
     h_in = torch.from_numpy(f_host).pin_memory()

@@ -116,6 +116,18 @@ bz_status bz_plan_pipeline(const bz_plan *plan, int *pipeline, int *cluster, int
 bz_status bz_plan_terms(const bz_plan *plan, double *r, double *w_r, double *qhat,
                         double *w_q, double *c);
 
+/* Host only (no GPU needed).  The quadrature terms a plan with these parameters uses, in
+ * term order p = i*M + j: radial Gauss-Legendre nodes and weights on [0, R], the sphere rule
+ * (M = 12: icosahedron; M = 2n^2 or n^2: product rule), c_p = w_r w_q r^(gamma + 2)
+ * (Sec. 4, eq. approxG).  Arrays of length N_rho * M (qhat: 3x), any may be NULL. */
+bz_status bz_quadrature(int N_rho, double R, int M, double gamma, double *r, double *w_r, double *qhat,
+                        double *w_q, double *c);
+
+/* Host only.  The angular kernel's normalisation c (g = sin(theta) b(cos theta), lambda = 1/6)
+ * and the part-I moments A = (int g (1-cos), int g (1-cos)^2, int g sin^2) over [0, eps]
+ * (Sec. 4.1; eps <= 0 selects pi/1000). */
+bz_status bz_kernel_constants(int kernel, double s, double eps, double *c, double A[3]);
+
 /* Qhat = Q(fhat, fhat) over all terms (eq. realQ).  fhat and Qhat are device arrays
  * of N^3 complex values of the given dtype; fhat != Qhat (BZ_ERR_ARG otherwise).
  * Arithmetic: FP32 FFTs and products, FP64 accumulation over terms. */

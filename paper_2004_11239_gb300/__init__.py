@@ -21,6 +21,7 @@ __all__ = [
     "bz_collide", "bz_collide_terms", "bz_step_rk", "bz_moments", "bz_ftable_entries",
     "bz_plan_alpha", "bz_plan_last_launches", "bz_status_str", "library_path", "lib",
     "bz_plan_set_timing", "bz_plan_timing", "bz_collide_noalloc", "bz_plan_pipeline",
+    "bz_quadrature", "bz_kernel_constants",
     "bz_batch_create", "bz_batch_destroy", "bz_batch_set_gamma", "bz_batch_collide", "bz_batch_step_rk",
     "bz_batch_last_launches", "bz_server_create", "bz_submit", "bz_poll", "bz_server_stats",
 ]
@@ -81,6 +82,8 @@ def _load():
         "bz_plan_info": [vp, ip, ctypes.POINTER(c_size), ctypes.POINTER(c_size)],
         "bz_plan_terms": [vp, dp, dp, dp, dp, dp],
         "bz_plan_pipeline": [vp, ip, ip, ip, ctypes.POINTER(ctypes.c_float)],
+        "bz_quadrature": [c_int, c_double, c_int, c_double, dp, dp, dp, dp, dp],
+        "bz_kernel_constants": [c_int, c_double, c_double, dp, dp],
         "bz_collide": [vp, vp, vp, c_int, vp],
         "bz_collide_terms": [vp, c_int, c_int, vp, vp, c_int, vp],
         "bz_step_rk": [vp, vp, c_int, dp, c_double, c_int, vp, vp],
@@ -228,6 +231,25 @@ def bz_plan_pipeline(plan: Plan):
            "bz_plan_pipeline")
     return {"pipeline": "fused" if p.value == BZ_PIPE_FUSED else "chunked", "cluster": c.value,
             "clusters": g.value, "tuned_ms": t.value}
+
+
+def bz_quadrature(N_rho: int, R: float, M: int, gamma: float):
+    """Host-only term list: numpy arrays r, w_r, qhat[P,3], w_q, c."""
+    import numpy as np
+    P = N_rho * M
+    r, wr, wq, c = (np.empty(P) for _ in range(4))
+    q = np.empty((P, 3))
+    f = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))  # noqa: E731
+    _check(lib.bz_quadrature(N_rho, R, M, gamma, f(r), f(wr), f(q), f(wq), f(c)), "bz_quadrature")
+    return r, wr, q, wq, c
+
+
+def bz_kernel_constants(kernel: int, s: float, eps: float = 0.0):
+    """Host-only kernel constant c and part-I moments (A1, A2, A3)."""
+    c = ctypes.c_double()
+    A = (ctypes.c_double * 3)()
+    _check(lib.bz_kernel_constants(kernel, s, eps, ctypes.byref(c), A), "bz_kernel_constants")
+    return c.value, tuple(A)
 
 
 def bz_plan_terms(plan: Plan):

@@ -291,6 +291,34 @@ bz_status bz_plan_alpha(const bz_plan *plan, int p0, int p1, void *dst, void *st
 
 int bz_plan_last_launches(const bz_plan *plan) { return plan ? plan->p.last_launches : 0; }
 
+bz_status bz_quadrature(int N_rho, double R, int M, double gamma, double *r, double *w_r, double *qhat,
+                        double *w_q, double *c) {
+    if (N_rho < 1 || M < 1 || !(R > 0) || !std::isfinite(gamma)) return BZ_ERR_ARG;
+    bz::Plan pl;
+    pl.N_rho = N_rho; pl.R = R; pl.M = M; pl.gamma = gamma;
+    bz_status s = bz::build_terms(pl, nullptr, nullptr);
+    if (s != BZ_OK) return s;
+    const bz::HostTerms &T = pl.terms;
+    for (int p = 0; p < pl.P; ++p) {
+        if (r) r[p] = T.r[p];
+        if (w_r) w_r[p] = T.wr[p];
+        if (w_q) w_q[p] = T.wq[p];
+        if (c) c[p] = T.c[p];
+        if (qhat) for (int d = 0; d < 3; ++d) qhat[3 * p + d] = T.q[3 * p + d];
+    }
+    return BZ_OK;
+}
+
+bz_status bz_kernel_constants(int kernel, double s, double eps, double *c, double A[3]) {
+    bz::Plan pl;
+    pl.kernel = kernel; pl.s = s; pl.eps = eps > 0 ? eps : M_PI / 1000.0;
+    bz_status st = bz::build_kernel_constants(pl);
+    if (st != BZ_OK) return st;
+    if (c) *c = pl.kc;
+    if (A) for (int i = 0; i < 3; ++i) A[i] = pl.A[i];
+    return BZ_OK;
+}
+
 bz_status bz_plan_set_timing(bz_plan *plan, int max_launches) {
     if (!plan || max_launches < 0) return BZ_ERR_ARG;
     bz::Plan &pl = plan->p;

@@ -75,6 +75,14 @@ __global__ void ftable_kernel(TableArgs a) {
     int k1 = i1 < N / 2 ? i1 : i1 - N;
     int k2 = i2 < N / 2 ? i2 : i2 - N;
     int k3 = i3 < N / 2 ? i3 : i3 - N;
+    // F(-k) = conj F(k) (eq. FF): the entry of the smaller index of each pair (k, -k) is computed
+    // and written to both; modes with a Nyquist component (-N/2) have no partner.
+    const bool nyq = k1 == -N / 2 || k2 == -N / 2 || k3 == -N / 2;
+    int midx = -1;
+    if (!nyq) {
+        midx = (((-k1 + N) % N) * N + ((-k2 + N) % N)) * N + ((-k3 + N) % N);
+        if (midx < idx) return;                           // written by the partner's thread
+    }
     const double *tp = a.term + 5 * (size_t)p;
     double r = tp[0];
     double kap = k1 * tp[1] + k2 * tp[2] + k3 * tp[3];
@@ -86,6 +94,7 @@ __global__ void ftable_kernel(TableArgs a) {
     double2 F = f_value(aa * kap, aa * kp, A, n, omc, sn, W);
     double sc = tp[4] * a.inv_n3;
     a.alpha[(size_t)p * n3 + idx] = make_float2((float)(sc * F.x), (float)(sc * F.y));
+    if (midx > idx) a.alpha[(size_t)p * n3 + midx] = make_float2((float)(sc * F.x), (float)(-sc * F.y));
 }
 
 struct EntryArgs {

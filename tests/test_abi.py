@@ -1,5 +1,6 @@
 """The C ABI library builds, loads and exports every function that include/*.h declares (CPU only)."""
 import ctypes
+import math
 import glob
 import os
 import re
@@ -44,3 +45,39 @@ def test_status_strings_and_argument_checks_without_gpu(libpath):
     assert bz.lib.bz_plan_create(ctypes.byref(h), 16, -1.0, 9.0, 0.0, 0.5, 4, 12) == 1   # L < 0
     assert bz.lib.bz_collide(None, None, None, 0, None) == 1
     assert h.value is None
+
+
+@pytest.mark.parametrize("N_rho,M,gamma", [(16, 12, 0.0), (32, 32, -1.0), (5, 72, -2.0), (8, 64, 0.5)])
+def test_library_quadrature_matches_oracle(libpath, N_rho, M, gamma):
+    """The library's host quadrature (Newton Gauss-Legendre, its own sphere rules) equals the oracle's."""
+    import numpy as np
+    import paper_2004_11239_gb300 as bz
+    from oracle import quadrature
+    R = 6.0
+    r, wr, q, wq, c = bz.bz_quadrature(N_rho, R, M, gamma)
+    r2, wr2, q2, wq2 = quadrature.terms(N_rho, R, M)
+    assert np.allclose(r, r2, rtol=0, atol=1e-13 * R)
+    assert np.allclose(wr, wr2, rtol=1e-12)
+    assert np.allclose(q, q2, rtol=0, atol=1e-14)
+    assert np.allclose(wq, wq2, rtol=1e-13)
+    assert np.allclose(c, wr2 * wq2 * r2 ** (gamma + 2), rtol=1e-12)
+
+
+@pytest.mark.parametrize("name,kid,s", [("family", 0, 0.0), ("family", 0, 0.25), ("family", 0, 0.5),
+                                        ("family", 0, 0.75), ("b5", 1, 0.0), ("b8", 2, 0.0)])
+def test_library_kernel_constants_match_oracle(libpath, name, kid, s):
+    import paper_2004_11239_gb300 as bz
+    from oracle import kernels
+    k = kernels.Kernel(name, s)
+    c, A = bz.bz_kernel_constants(kid, s)
+    assert abs(c - k.c) <= 1e-14 * k.c
+    for got, ref in zip(A, k.taylor_moments(math.pi / 1000)):
+        assert abs(got - ref) <= 1e-11 * abs(ref)
+
+
+def test_library_rejects_unknown_sphere_rule(libpath):
+    import paper_2004_11239_gb300 as bz
+    with pytest.raises(bz.BzError):
+        bz.bz_quadrature(4, 6.0, 13, 0.0)
+    with pytest.raises(bz.BzError):
+        bz.bz_kernel_constants(0, 1.5)
