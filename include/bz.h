@@ -56,7 +56,16 @@ enum { BZ_C64 = 0, BZ_C128 = 1 };
  *   BZ_KERNEL_B8:     b = 5 cos(theta/2) / (192 pi sin(theta) sin^(5/2)(theta/2)), eq. b8. */
 enum { BZ_KERNEL_FAMILY = 0, BZ_KERNEL_B5 = 1, BZ_KERNEL_B8 = 2 };
 
-enum { BZ_PREC_FP32 = 0 };
+/* Arithmetic of the per-term transforms (Sec. 4, eq. realQ: two 3D FFTs per term).
+ *   BZ_PREC_FP32:   FP32 register FFTs on the CUDA cores (every supported N).
+ *   BZ_PREC_BF16X3: each one-axis transform is a DFT on the tensor cores with BF16 operands
+ *                   split as x = x_hi + x_lo and the products x_hi w_hi + x_lo w_hi +
+ *                   x_hi w_lo accumulated in FP32 (about 16 significant bits per product);
+ *                   twiddles, the product with h, the alpha weighting and the sum over terms
+ *                   stay FP32, h is formed in FP64.  Fused pipeline, N = 32 only; other N
+ *                   or BZ_PIPE_CHUNKED give BZ_ERR_UNSUPPORTED.  Accuracy target: relative
+ *                   L-infinity error 1e-3 of max |Qhat|. */
+enum { BZ_PREC_FP32 = 0, BZ_PREC_BF16X3 = 1 };
 
 /* Collide pipelines.  FUSED: one thread-block cluster per term keeps the whole field in
  * (distributed) shared memory from twiddle to weighted accumulation (N <= 32).  CHUNKED:
@@ -82,7 +91,7 @@ typedef struct {
     int N_rho;        /* Gauss-Legendre points in |q| (Sec. 4)                         */
     int M;            /* sphere points: 12 = icosahedron; 2n^2 or n^2 = product rule    */
     int kernel;       /* BZ_KERNEL_*                                                   */
-    int precision;    /* BZ_PREC_FP32                                                  */
+    int precision;    /* BZ_PREC_*                                                     */
     double eps;       /* Taylor/quadrature split angle; <= 0 selects pi/1000 (Sec. 4.1) */
     const double *sphere_xyz;  /* optional host array [M][3] of unit vectors, or NULL  */
     const double *sphere_w;    /* optional host array [M] of weights (sum 4 pi)         */
@@ -274,6 +283,12 @@ bz_status bz_plan_timing(bz_plan *plan, int kind, long *launches, double *ms);
 /* Number of kernel launches issued by the last bz_collide / bz_collide_terms /
  * bz_step_rk call on this plan. */
 int bz_plan_last_launches(const bz_plan *plan);
+
+/* Device-side waits of the plan's kernels are bounded (BZ_PREC_BF16X3: the waits for
+ * tensor-core completion).  *count = 1 if one gave up since the plan was created (the
+ * results of that launch are invalid), else 0.  Waits for the device.  No counterpart in
+ * the paper. */
+bz_status bz_plan_device_errors(bz_plan *plan, int *count);
 
 #ifdef __cplusplus
 }

@@ -19,7 +19,7 @@ __all__ = [
     "BZ_C64", "BZ_C128", "BZ_KERNEL_FAMILY", "BZ_KERNEL_B5", "BZ_KERNEL_B8", "BzError",
     "bz_plan_create", "bz_plan_create_ex", "bz_plan_destroy", "bz_plan_info", "bz_plan_terms",
     "bz_collide", "bz_collide_terms", "bz_step_rk", "bz_moments", "bz_ftable_entries",
-    "bz_plan_alpha", "bz_plan_last_launches", "bz_status_str", "library_path", "lib",
+    "bz_plan_alpha", "bz_plan_last_launches", "bz_plan_device_errors", "bz_status_str", "library_path", "lib",
     "bz_plan_set_timing", "bz_plan_timing", "bz_collide_noalloc", "bz_plan_pipeline",
     "bz_quadrature", "bz_kernel_constants",
     "bz_batch_create", "bz_batch_destroy", "bz_batch_set_gamma", "bz_batch_collide", "bz_batch_step_rk",
@@ -31,7 +31,7 @@ _LIB_PATH = os.path.join(_HERE, "_lib", "libbz.so")
 
 BZ_C64, BZ_C128 = 0, 1
 BZ_KERNEL_FAMILY, BZ_KERNEL_B5, BZ_KERNEL_B8 = 0, 1, 2
-BZ_PREC_FP32 = 0
+BZ_PREC_FP32, BZ_PREC_BF16X3 = 0, 1
 BZ_PIPE_AUTO, BZ_PIPE_FUSED, BZ_PIPE_CHUNKED = 0, 1, 2
 BZ_H_AUTO, BZ_H_FP64, BZ_H_FP32 = 0, 1, 2
 _STATUS = {0: "BZ_OK", 1: "BZ_ERR_ARG", 2: "BZ_ERR_OOM", 3: "BZ_ERR_CUDA", 4: "BZ_ERR_TIMEOUT",
@@ -91,6 +91,7 @@ def _load():
         "bz_ftable_entries": [vp, c_int, vp, vp, vp],
         "bz_plan_alpha": [vp, c_int, c_int, vp, vp],
         "bz_collide_noalloc": [vp, vp, vp, c_int, vp],
+        "bz_plan_device_errors": [vp, ip],
         "bz_batch_create": [ctypes.POINTER(vp), vp, c_int, c_int],
         "bz_batch_info": [vp, ip, ip, ctypes.POINTER(c_size)],
         "bz_batch_set_gamma": [vp, c_int, c_double],
@@ -195,10 +196,10 @@ def bz_plan_create(N: int, L: float, R: float, gamma: float, s: float, N_rho: in
 def bz_plan_create_ex(N: int, L: float, R: float, gamma: float, s: float, N_rho: int, M: int,
                       kernel: int = BZ_KERNEL_FAMILY, eps: float = 0.0, sphere=None,
                       chunk_terms: int = 0, pipeline: int = BZ_PIPE_AUTO, cluster: int = 0,
-                      h_precision: int = BZ_H_AUTO) -> Plan:
+                      h_precision: int = BZ_H_AUTO, precision: int = BZ_PREC_FP32) -> Plan:
     d = bz_plan_desc()
     d.N, d.L, d.R, d.gamma, d.s, d.N_rho, d.M = N, L, R, gamma, s, N_rho, M
-    d.kernel, d.precision, d.eps, d.chunk_terms = kernel, BZ_PREC_FP32, eps, chunk_terms
+    d.kernel, d.precision, d.eps, d.chunk_terms = kernel, precision, eps, chunk_terms
     d.pipeline = pipeline
     d.cluster = cluster
     d.h_precision = h_precision
@@ -323,6 +324,13 @@ def bz_plan_alpha(plan: Plan, p0: int, p1: int, stream=None):
 
 def bz_plan_last_launches(plan: Plan) -> int:
     return lib.bz_plan_last_launches(plan.handle)
+
+
+def bz_plan_device_errors(plan: Plan) -> int:
+    """1 if a bounded device-side wait of the plan's kernels gave up (results invalid)."""
+    c = ctypes.c_int()
+    _check(lib.bz_plan_device_errors(plan.handle, ctypes.byref(c)), "bz_plan_device_errors")
+    return c.value
 
 
 BZ_K_PLANE_INV, BZ_K_PENCIL, BZ_K_PLANE_FWD, BZ_K_REDUCE, BZ_K_OTHER = range(5)

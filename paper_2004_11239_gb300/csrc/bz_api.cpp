@@ -30,6 +30,8 @@ void free_plan(bz::Plan &p) {
     cudaFree(p.alpha); cudaFree(p.tw); cudaFree(p.rule_buf); cudaFree(p.rule_off);
     cudaFree(p.term_dev); cudaFree(p.S); cudaFree(p.h); cudaFree(p.fin); cudaFree(p.acc);
     cudaFree(p.rk); cudaFree(p.mom); cudaFree(p.part); cudaFree(p.fin64); cudaFree(p.scr64);
+    cudaFree(p.wimg); cudaFree(p.dev_err);
+    p.wimg = nullptr; p.dev_err = nullptr;
     p.part = nullptr; p.fin64 = nullptr; p.scr64 = nullptr; p.src = nullptr;
     p.alpha = nullptr; p.tw = nullptr; p.rule_buf = nullptr; p.rule_off = nullptr;
     p.term_dev = nullptr; p.S = nullptr; p.h = nullptr; p.fin = nullptr; p.acc = nullptr;
@@ -63,7 +65,9 @@ std::vector<float2> make_twiddles(const bz::Plan &pl) {
 // and keeps the fastest; allocates the partial-sum buffer for it.
 bz_status select_fused(bz::Plan &pl, int forced) {
     int cs[4];
-    int nc = bz::fused_candidates(pl.N, cs);
+    const bool mixed = pl.precision == BZ_PREC_BF16X3;
+    int nc = mixed ? 1 : bz::fused_candidates(pl.N, cs);
+    if (mixed) cs[0] = 8;
     const size_t field = (size_t)pl.N * pl.N * pl.N * sizeof(float2);
     int bestC = 0, bestG = 0;
     float best = 1e30f;
@@ -73,7 +77,8 @@ bz_status select_fused(bz::Plan &pl, int forced) {
     for (int c = 0; c < nc; ++c) {
         if (forced > 0 && cs[c] != forced) continue;
         int G = 0;
-        if (bz::fused_setup(pl.N, cs[c], &G) != cudaSuccess || G <= 0) { cudaGetLastError(); continue; }
+        const cudaError_t se = mixed ? bz::mixed_setup(pl.N, &G) : bz::fused_setup(pl.N, cs[c], &G);
+        if (se != cudaSuccess || G <= 0) { cudaGetLastError(); continue; }
         float2 *part = nullptr;
         if (cudaMalloc(&part, (size_t)G * field) != cudaSuccess) { cudaGetLastError(); continue; }
         std::swap(part, pl.part);
@@ -106,7 +111,9 @@ bz_status create(bz_plan **out, const bz_plan_desc *d) {
     *out = nullptr;
     if (!bz::supported_N(d->N) || d->N_rho < 1 || d->M < 1 || !(d->L > 0) || !(d->R > 0))
         return BZ_ERR_ARG;
-    if (d->precision != BZ_PREC_FP32) return BZ_ERR_UNSUPPORTED;
+    if (d->precision != BZ_PREC_FP32 && d->precision != BZ_PREC_BF16X3) return BZ_ERR_ARG;
+    if (d->precision == BZ_PREC_BF16X3 && (d->N != 32 || d->pipeline == BZ_PIPE_CHUNKED))
+        return BZ_ERR_UNSUPPORTED;
     if (d->pipeline < BZ_PIPE_AUTO || d->pipeline > BZ_PIPE_CHUNKED) return BZ_ERR_ARG;
     if (d->kernel < BZ_KERNEL_FAMILY || d->kernel > BZ_KERNEL_B8) return BZ_ERR_ARG;
     bz_plan *h = new (std::nothrow) bz_plan();
@@ -116,7 +123,7 @@ bz_status create(bz_plan **out, const bz_plan_desc *d) {
     pl.N_rho = d->N_rho; pl.M = d->M; pl.kernel = d->kernel; pl.precision = d->precision;
     pl.eps = d->eps > 0 ? d->eps : M_PI / 1000.0;
     if (d->h_precision < BZ_H_AUTO || d->h_precision > BZ_H_FP32) { delete h; return BZ_ERR_ARG; }
-    pl.h_fp64 = d->h_precision != BZ_H_FP32;
+    pl.h_fp64 = d->h_precision != BZ_H_FP32 || d->precision == BZ_PREC_BF16X3;   // BF16X3 reads h formed in FP64
     cudaGetDevice(&pl.device);
     bz_status s = bz::build_terms(pl, d->sphere_xyz, d->sphere_w);
     if (s == BZ_OK) s = bz::build_kernel_constants(pl);
@@ -143,7 +150,8 @@ bz_status create(bz_plan **out, const bz_plan_desc *d) {
         (s = dmalloc(&pl.fin, field)) != BZ_OK ||
         (s = dmalloc(&pl.acc, n3 * sizeof(double2))) != BZ_OK ||
         (s = dmalloc(&pl.rk, 2 * n3 * sizeof(double2))) != BZ_OK ||
-        (s = dmalloc(&pl.mom, 8 * sizeof(double))) != BZ_OK) {
+        (s = dmalloc(&pl.mom, 8 * sizeof(double))) != BZ_OK ||
+        (s = dmalloc(&pl.dev_err, sizeof(int))) != BZ_OK) {
         free_plan(pl);
         delete h;
         return s;
@@ -151,6 +159,8 @@ bz_status create(bz_plan **out, const bz_plan_desc *d) {
     pl.ws_bytes = (size_t)chunk * field + 2 * field + 3 * n3 * sizeof(double2);
     std::vector<float2> tw = make_twiddles(pl);
     if (cudaMemcpy(pl.tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(pl.dev_err, 0, sizeof(int)) != cudaSuccess ||
+        (pl.precision == BZ_PREC_BF16X3 && bz::mixed_upload(&pl.wimg) != BZ_OK) ||
         bz::collide_set_attributes(N) != cudaSuccess) {
         free_plan(pl);
         delete h;
@@ -170,7 +180,7 @@ bz_status create(bz_plan **out, const bz_plan_desc *d) {
             if (select_fused(pl, d->cluster) != BZ_OK) cudaGetLastError();
         }
     }
-    if (d->pipeline == BZ_PIPE_FUSED && !pl.use_fused) {
+    if ((d->pipeline == BZ_PIPE_FUSED || pl.precision == BZ_PREC_BF16X3) && !pl.use_fused) {
         free_plan(pl);
         delete h;
         return BZ_ERR_UNSUPPORTED;
@@ -290,6 +300,14 @@ bz_status bz_plan_alpha(const bz_plan *plan, int p0, int p1, void *dst, void *st
 }
 
 int bz_plan_last_launches(const bz_plan *plan) { return plan ? plan->p.last_launches : 0; }
+
+bz_status bz_plan_device_errors(bz_plan *plan, int *count) {
+    if (!plan || !count) return BZ_ERR_ARG;
+    int v = 0;
+    if (cudaMemcpy(&v, plan->p.dev_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return BZ_ERR_CUDA;
+    *count = v != 0;
+    return BZ_OK;
+}
 
 bz_status bz_quadrature(int N_rho, double R, int M, double gamma, double *r, double *w_r, double *qhat,
                         double *w_q, double *c) {

@@ -20,6 +20,7 @@
 // term is fhat (L2-resident) and alpha_p (HBM).
 #include <cooperative_groups.h>
 
+#include "bz_cluster.cuh"
 #include "bz_fft.cuh"
 #include "bz_internal.h"
 
@@ -39,34 +40,6 @@ template <int N, int C_> struct FK {
     // two CTAs per SM where registers and shared memory allow it
     static constexpr int MIN_BLOCKS = (N <= 16 || N * N / C_ <= 128) ? 2 : 1;
 };
-
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
-    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
-
-// Distributed shared memory through the shared::cluster window (32-bit addresses).
-__device__ __forceinline__ uint32_t dsmem_addr(const void *local, uint32_t rank) {
-    uint32_t a = (uint32_t)__cvta_generic_to_shared(local), r;
-    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;\n" : "=r"(r) : "r"(a), "r"(rank));
-    return r;
-}
-__device__ __forceinline__ float2 ld_dsmem(uint32_t a) {
-    float2 v;
-    asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];\n" : "=f"(v.x), "=f"(v.y) : "r"(a) : "memory");
-    return v;
-}
-__device__ __forceinline__ void st_dsmem(uint32_t a, float2 v) {
-    asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};\n" ::"r"(a), "f"(v.x), "f"(v.y) : "memory");
-}
-
-template <int C> __device__ __forceinline__ void cluster_barrier() {
-    if constexpr (C > 1) cg::this_cluster().sync();
-    else __syncthreads();
-}
 
 // Phase A for plane k1 (column k3 = lane): x = twiddle * fhat over k2, IFFT over k2, store
 // the column, then rows over k3.  tws == nullptr: no twiddle (the h prologue).
@@ -473,6 +446,7 @@ template <int N, int C> static bz_status launch_sc(const Plan &pl, const ItemArg
 
 bz_status launch_fused(const Plan &pl, const ItemArgs &a, cudaStream_t st) {
     const int N = pl.N, C = pl.fused_C;
+    if (pl.precision == BZ_PREC_BF16X3) return launch_mixed(pl, a, st);
     if (N == 8 && C == 1) return launch_sc<8, 1>(pl, a, st);
     if (N == 16 && C == 1) return launch_sc<16, 1>(pl, a, st);
     if (N == 16 && C == 2) return launch_sc<16, 2>(pl, a, st);
@@ -494,7 +468,7 @@ bz_status collide_fused(Plan &pl, int p0, int p1, cudaStream_t st, int *launches
     a.TB = nt > 0 ? (nt + pl.fused_G - 1) / pl.fused_G : 1;
     a.nblk = nt > 0 ? (nt + a.TB - 1) / a.TB : 0;
     bz_status s = BZ_OK;
-    if (pl.h_fp64) {
+    if (pl.h_fp64 || pl.precision == BZ_PREC_BF16X3) {
         tm_begin(pl, st);
         s = h64_launch(pl.N, pl.src ? pl.src : (const void *)pl.fin, pl.src ? pl.src_dtype : BZ_C64,
                        nullptr, nullptr, 1, pl.scr64, pl.h, st);

@@ -67,6 +67,8 @@ struct Plan {
     const void *src = nullptr;      // FP64-capable source of h for the next fused collide
     int src_dtype = BZ_C128;
     float2 *part = nullptr;         // [fused_G][N^3] per-cluster partial sums
+    uint4 *wimg = nullptr;          // BZ_PREC_BF16X3: split DFT matrix (tensor-core B operand)
+    int *dev_err = nullptr;         // device flag: a bounded wait of the fused kernel gave up
     size_t ws_bytes = 0;
     int last_launches = 0;
     Timing tm;
@@ -121,6 +123,11 @@ bz_status launch_fused(const Plan &pl, const ItemArgs &a, cudaStream_t st);
 bz_status h64_launch(int N, const void *f, int dtype, const int *slots, const int *count_dev, int count,
                      double2 *scr, float2 *h, cudaStream_t st);
 bz_status collide_fused(Plan &pl, int p0, int p1, cudaStream_t st, int *launches);
+
+// bz_mixed.cu (BZ_PREC_BF16X3, N = 32)
+cudaError_t mixed_setup(int N, int *G);
+bz_status mixed_upload(uint4 **wimg);
+bz_status launch_mixed(const Plan &pl, const ItemArgs &a, cudaStream_t st);
 cudaError_t collide_set_attributes(int N);
 int supported_N(int N);
 

@@ -47,6 +47,20 @@ def test_status_strings_and_argument_checks_without_gpu(libpath):
     assert h.value is None
 
 
+def test_precision_checks_without_gpu(libpath):
+    """The split-BF16 form exists for the fused N = 32 pipeline only; the checks come before
+    any CUDA call."""
+    import paper_2004_11239_gb300 as bz
+    h = ctypes.c_void_p()
+    for N, prec, pipe, want in [(16, bz.BZ_PREC_BF16X3, 0, 7), (32, bz.BZ_PREC_BF16X3, bz.BZ_PIPE_CHUNKED, 7),
+                                (32, 5, 0, 1)]:
+        d = bz.bz_plan_desc()
+        d.N, d.L, d.R, d.gamma, d.s, d.N_rho, d.M = N, 10.0, 9.0, 0.0, 0.5, 2, 12
+        d.precision, d.pipeline = prec, pipe
+        assert bz.lib.bz_plan_create_ex(ctypes.byref(h), ctypes.byref(d)) == want
+        assert h.value is None
+
+
 @pytest.mark.parametrize("N_rho,M,gamma", [(16, 12, 0.0), (32, 32, -1.0), (5, 72, -2.0), (8, 64, 0.5)])
 def test_library_quadrature_matches_oracle(libpath, N_rho, M, gamma):
     """The library's host quadrature (Newton Gauss-Legendre, its own sphere rules) equals the oracle's."""
