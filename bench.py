@@ -103,7 +103,7 @@ def _profiled_traffic(kernel, workload):
             vals[k.strip()] = v.strip()
     src = os.path.join(ROOT, "paper_2004_11239_gb300", "csrc")
     h = hashlib.sha256()
-    for f in ("bz_fused.cu", "bz_fft.cuh"):
+    for f in ("bz_fused.cu", "bz_fft.cuh", "bz_cluster.cuh"):
         h.update(open(os.path.join(src, f), "rb").read())
     if vals.get("kernel_sources_sha256_16") != h.hexdigest()[:16]:
         return None
@@ -338,6 +338,10 @@ def run_ours(args, w):
                  "derived: 152 SMs x 128 FP32 lanes x 2 x sm_max_mhz", "launches": n_launch,
                  "avg_launch_us": avg_s * 1e6, "also": {k: other[k] for k in ("bound", "achieved", "peak", "unit", "frac")}})
 
+    mixed = None
+    if N == 32 and not args.no_mixed:
+        mixed = _measure_mixed(args, w, bz, plan, f_host, L, R, st, peaks, src, barrier)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         P = w["N_rho"] * w["M"]
@@ -359,6 +363,8 @@ def run_ours(args, w):
             "clocks": clocks, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
             "roofline": roof, "kernels_ms": {k: v[1] for k, v in kern.items()},
             "cpu_baseline": cpu}
+    if mixed is not None:
+        line["mixed"] = mixed
     if rank == 0:
         print(json.dumps(line))
     plan.close()
@@ -366,6 +372,72 @@ def run_ours(args, w):
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def _tc_flops_per_term(N):
+    """Tensor-core flops of one term in the split-BF16 form: six one-axis DFTs, each N^2 lines x
+    2N real outputs x 3 (split products) x 2N real inputs, 2 flops per multiply-add."""
+    return 6 * 2 * N ** 2 * (2 * N) * 3 * (2 * N)
+
+
+def _measure_mixed(args, w, bz, plan32, f_host, L, R, st, peaks, src, barrier):
+    """The same workload on the split-BF16 tensor-core form (BZ_PREC_BF16X3): throughput, the
+    deviation from the FP32 form on one collide of the input, and the dominant kernel's
+    tensor-pipe roofline."""
+    import numpy as np
+    import torch
+    N = w["N"]
+    pm = bz.bz_plan_create_ex(N, L, R, w["gamma"], w["s"], w["N_rho"], w["M"], precision=bz.BZ_PREC_BF16X3)
+    f = torch.from_numpy(f_host).to("cuda")
+    q32, qm = torch.empty_like(f), torch.empty_like(f)
+    bz.bz_collide(plan32, f, q32, st)
+    bz.bz_collide(pm, f, qm, st)
+    torch.cuda.synchronize()
+    a, b = qm.cpu().numpy(), q32.cpu().numpy()
+    dev = float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+    is_rk = w["dt"] is not None
+    evals_per_step = 4 if is_rk else 1
+
+    def step():
+        if is_rk:
+            bz.bz_step_rk(pm, f, 0.0, w["dt"], 1, st)
+        else:
+            bz.bz_collide(pm, f, qm, st)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    launches_per_step = bz.bz_plan_last_launches(pm)
+    bz.bz_plan_set_timing(pm, launches_per_step * args.steps + 16)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    e0.record(st)
+    for _ in range(args.steps):
+        step()
+    e1.record(st)
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    n_launch, ms_k = bz.bz_plan_timing(pm, bz.KERNEL_KINDS["fused"])
+    bz.bz_plan_set_timing(pm, 0)
+    value, ms = job_throughput(evals_per_step * args.steps, ms)
+    errors = bz.bz_plan_device_errors(pm)
+    terms_per_launch = (w["N_rho"] * w["M"]) * evals_per_step * args.steps / max(n_launch, 1)
+    avg_s = ms_k / 1e3 / max(n_launch, 1)
+    tc = _tc_flops_per_term(N) * terms_per_launch / avg_s / 1e12
+    tc_peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1900.0))
+    fft = _flops_per_term(N)["fused"] * terms_per_launch / avg_s / 1e12
+    pm.close()
+    return {"precision": "bf16x3", "value": value, "unit": "evals/s", "ms_per_step": ms / args.steps,
+            "rel_linf_vs_fp32_form": dev, "device_errors": errors,
+            "gpu_launches": launches_per_step * args.steps,
+            "roofline": {"bound": "tensor", "kernel": "k_mixed", "achieved": tc, "peak": tc_peak,
+                         "unit": "TFLOP/s", "frac": tc / tc_peak, "launches": n_launch,
+                         "avg_launch_us": avg_s * 1e6,
+                         "peak_source": f"{src} bf16 (sustained)" if "bf16_tflops_sustained" in peaks else src,
+                         "work": "split-BF16 DFT-GEMM flops: 6 x 2 N^2 x 2N x 3 x 2N per term",
+                         "fft_equivalent_tflops": fft}}
 
 
 def run_batch(args, w):
@@ -510,6 +582,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="rk4_n32", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true",
+                    help="skip the split-BF16 tensor-core form (measured beside the FP32 form at N = 32)")
     ap.add_argument("--rates", default=None, help="serve workload: comma-separated arrival rates (req/s)")
     ap.add_argument("--h-precision", type=int, default=0, choices=[0, 1, 2],
                     help="h = IFFT(fhat) precision on the fused path: 0 auto (FP64), 1 FP64, 2 FP32")

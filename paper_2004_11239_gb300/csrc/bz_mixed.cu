@@ -14,14 +14,15 @@
 //
 // Work split as in the FP32 fused kernel: a cluster of 8 CTAs per term, CTA r owns planes
 // k1 in [4r, 4r + 4) for the two plane-local axes and pencils j2 in [4r, 4r + 4) for the
-// k1 axis; the two exchanges between the layouts go through distributed shared memory in
-// FP32.  Per term and CTA (128 threads, thread (w, l) = warp w, lane l):
+// k1 axis; the two exchanges between the layouts are pushes (remote FP32 stores through
+// distributed shared memory) into a pencil buffer X and a plane buffer Y, each followed by
+// one cluster barrier.  Per term and CTA (128 threads, thread (w, l) = warp w, lane l):
 //   1  A <- twiddle * fhat    rows (k1, k2), K = k3   MN-major   (fhat column from TMEM)
 //   2  A <- D1                rows (k1, j3), K = k2   MN-major
-//   -- D2 -> FP32 planes, cluster barrier, gather the k1 pencils --
+//   -- push D2 into the pencil buffers X of the cluster, cluster barrier --
 //   3  A <- pencil            rows (j2, j3), K = k1   K-major
 //   4  A <- conj(D3 h)        rows (j2, j3), K = j1   K-major    (h column from TMEM)
-//   -- scatter D4 into the planes, cluster barrier --
+//   -- push D4 into the plane buffers Y of the cluster, cluster barrier --
 //   5  A <- plane rows        rows (k1, j2), K = j3   K-major
 //   6  A <- D5                rows (k1, k3), K = j2   MN-major
 //   acc += alpha_p * conj(D6)  (accumulator in TMEM)
@@ -44,21 +45,20 @@ constexpr int XN = 32;                   // modes per axis
 constexpr int XC = 8;                    // CTAs per cluster
 constexpr int XP = XN / XC;              // planes (pencil rows) per CTA
 constexpr int XT = XP * XN;              // threads = GEMM rows
-constexpr int XLD = XN + 1;              // padded FP32 plane row
 constexpr uint32_t A_BYTES = 32768;      // A: 16 K-groups x 16 row-groups x 128 B
 constexpr uint32_t A_KG = 2048;          // bytes between K-groups of A (LBO)
 constexpr uint32_t A_LO = 8 * A_KG;      // the lo half of the split (K-groups 8..15)
 constexpr uint32_t B_HALF = 8192;        // one split half of B: 8 K-groups x 8 row-groups x 128 B
 constexpr uint32_t B_KG = 1024;          // bytes between K-groups of B (LBO)
 constexpr uint32_t B_BYTES = 2 * B_HALF;
-constexpr uint32_t P_BYTES = XP * XN * XLD * 8;   // FP32 planes [XP][XN][XLD]
-constexpr uint32_t TW_BYTES = 2 * 3 * XN * 8;     // two terms' twiddles
-constexpr uint32_t X_SMEM = A_BYTES + B_BYTES + P_BYTES + TW_BYTES;
+constexpr uint32_t X_BYTES = XP * XN * XN * 8;    // pencils [j2 - 4 rank][k1][j3], FP32
+constexpr uint32_t Y_BYTES = XP * XN * XN * 8;    // planes [k1 - 4 rank][j2][j3 ^ (j2 & 15)], FP32
+constexpr uint32_t X_SMEM = A_BYTES + B_BYTES + X_BYTES + Y_BYTES;
 constexpr uint32_t TM_COLS = 256;        // D, acc, fhat column, h column
 constexpr uint32_t TM_D = 0, TM_ACC = 64, TM_F = 128, TM_H = 192;
 // at most two CTAs per SM may be resident, so that 2 x 256 tensor-memory columns always fit
 static_assert(3 * (X_SMEM + 1024) > 228 * 1024, "a third CTA per SM would oversubscribe TMEM");
-static_assert(2 * (X_SMEM + 2048) <= 228 * 1024, "two CTAs per SM");
+static_assert(2 * (X_SMEM + 1024 + 64) <= 228 * 1024, "two CTAs per SM");
 static_assert(XT == 128, "one GEMM row per thread, M = 128");
 
 // Instruction descriptor of tcgen05.mma kind::f16: FP32 D, BF16 A and B, M = 128, N = 64;
@@ -185,7 +185,7 @@ __device__ __forceinline__ void store_k(uint32_t sA, const float *v, int m) {
 // FP32 sum over its terms goes to part[slot * nblk + blk].
 template <bool SCALED>
 __global__ void __launch_bounds__(XT, 2) k_mixed(const ItemArgs a, const uint4 *__restrict__ wimg, int *err) {
-    extern __shared__ __align__(1024) uint8_t xsm[];
+    extern __shared__ __align__(128) uint8_t xsm[];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t s_tmem;
     const int tid = threadIdx.x, w = tid >> 5, l = tid & 31;
@@ -193,8 +193,8 @@ __global__ void __launch_bounds__(XT, 2) k_mixed(const ItemArgs a, const uint4 *
     const int cid = blockIdx.x / XC, ncl = gridDim.x / XC;
     const uint32_t sA = (uint32_t)__cvta_generic_to_shared(xsm);
     const uint32_t sB = sA + A_BYTES;
-    float2 *planes = (float2 *)(xsm + A_BYTES + B_BYTES);       // [XP][XN][XLD]
-    float2 *stw = (float2 *)(xsm + A_BYTES + B_BYTES + P_BYTES); // [2][3][XN]
+    float2 *xpen = (float2 *)(xsm + A_BYTES + B_BYTES);                // X [XP][XN][XN]
+    float2 *ypl = (float2 *)(xsm + A_BYTES + B_BYTES + X_BYTES);      // Y [XP][XN][XN]
     const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&mbar);
 
     for (int i = tid; i < (int)(B_BYTES / 16); i += XT) ((uint4 *)(xsm + A_BYTES))[i] = wimg[i];
@@ -215,10 +215,16 @@ __global__ void __launch_bounds__(XT, 2) k_mixed(const ItemArgs a, const uint4 *
     const uint32_t tl = tmem + ((uint32_t)(32 * w) << 16);      // this thread's lane, column 0
     uint32_t phase = 0;
 
-    constexpr uint32_t PLANE_BYTES = (uint32_t)(XN * XLD * sizeof(float2));
-    uint32_t pen[XC];                                            // (j2 = 4 rank + w, j3 = l), plane 0
+    constexpr uint32_t SLAB = (uint32_t)(XN * XN * sizeof(float2));    // one [XN][XN] slab of X or Y
+    // X element (j2 - 4 rr, k1 = 4 rank + w, j3 = l) and Y element (k1 - 4 rr, j2 = 4 rank + w,
+    // j3 = l) in CTA rr, slab 0; slab (j2 % 4) resp. (k1 % 4) is SLAB bytes further
+    const int jx = rank * XP + w;
+    uint32_t xr[XC], yr[XC];
     #pragma unroll
-    for (int r = 0; r < XC; ++r) pen[r] = dsmem_addr(planes + (size_t)(rank * XP + w) * XLD + l, (uint32_t)r);
+    for (int r = 0; r < XC; ++r) {
+        xr[r] = dsmem_addr(xpen + (size_t)jx * XN + l, (uint32_t)r);
+        yr[r] = dsmem_addr(ypl + (size_t)jx * XN + (l ^ (jx & 15)), (uint32_t)r);
+    }
 
     // One transform: 12 MMAs (A_hi B_hi, A_lo B_hi, A_hi B_lo over four K-slabs of 16)
     // into D, issued by one thread once every thread's operand writes are visible.
@@ -249,13 +255,9 @@ __global__ void __launch_bounds__(XT, 2) k_mixed(const ItemArgs a, const uint4 *
     constexpr size_t N3 = (size_t)XN * XN * XN;
     const int count = a.count_dev ? *a.count_dev : a.count;
     const int nitems = count * a.nblk;
+    cluster_barrier<XC>();                                       // every CTA of the cluster has started
     const int k1 = rank * XP + w;                                // plane of the plane-local passes
     const int j2 = rank * XP + w;                                // pencil row of the k1 passes
-    auto fetch_tw = [&](int p, int buf) {                        // one term's 3N twiddles
-        if (p >= 0 && tid < (int)(3 * XN * sizeof(float2) / 16))
-            cp_async16((char *)(stw + buf * 3 * XN) + 16 * tid, (const char *)(a.tw + (size_t)p * 3 * XN) + 16 * tid);
-        cp_async_commit();
-    };
 
     for (int it = cid; it < nitems; it += ncl) {
         const int b = it / a.nblk, blk = it % a.nblk;
@@ -264,8 +266,6 @@ __global__ void __launch_bounds__(XT, 2) k_mixed(const ItemArgs a, const uint4 *
         const int t1 = min(a.p1, t0 + a.TB);
         const float2 *fin = a.fin + (size_t)slot * N3;
         const float2 *hg = a.hg + (size_t)slot * N3;
-        __syncthreads();                                         // previous item done with smem
-        fetch_tw(t0, 0);
         {
             // the thread's fhat column (k1, k2 = i, k3 = l), its h column (j1 = i, j2, j3 = l)
             // and a zero accumulator, in its tensor-memory lane
@@ -289,27 +289,23 @@ __global__ void __launch_bounds__(XT, 2) k_mixed(const ItemArgs a, const uint4 *
         }
         int ti = 0;
         for (int p = t0; p < t1; ++p, ++ti) {
-            const int buf = ti & 1;
-            cp_async_wait_all();
-            __syncthreads();                                     // this term's twiddles landed
-            fetch_tw(p + 1 < t1 ? p + 1 : -1, buf ^ 1);
             const float2 *alpha_p = a.alpha + ((size_t)p * XN + (size_t)rank * XP) * XN * XN;
             if (tid == 0)
                 asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(alpha_p),
                              "r"((uint32_t)(XP * XN * XN * sizeof(float2))) : "memory");
             float sc = 1.f;
             if constexpr (SCALED) sc = a.gsc[(size_t)slot * a.N_rho + p / a.M];
-            const float2 *tws = stw + buf * 3 * XN;
+            const float2 *tws = a.tw + (size_t)p * 3 * XN;            // L1-resident twiddles
             float v[64];
 
             // 1: beta_p fhat, rows (k1, k2), K = k3 = l
             tm_ld64(tl + TM_F, v);
             tm_wait_ld();
             {
-                const float2 t13 = cmul(tws[k1], tws[2 * XN + l]);
+                const float2 t13 = cmul(__ldg(tws + k1), __ldg(tws + 2 * XN + l));
                 #pragma unroll
                 for (int i = 0; i < XN; ++i) {
-                    const float2 x = cmul(make_float2(v[2 * i], v[2 * i + 1]), cmul(t13, tws[XN + i]));
+                    const float2 x = cmul(make_float2(v[2 * i], v[2 * i + 1]), cmul(t13, __ldg(tws + XN + i)));
                     v[2 * i] = x.x; v[2 * i + 1] = x.y;
                 }
             }
@@ -322,17 +318,18 @@ __global__ void __launch_bounds__(XT, 2) k_mixed(const ItemArgs a, const uint4 *
             store_mn(sA, v, w, l);
             run_pass(1);
             wait_pass();
-            // D2 = row (k1, j3 = l) over j2 -> FP32 plane k1
+            // D2 = row (k1, j3 = l) over j2 -> X of the CTA that owns pencil row j2
             tm_ld64(tl + TM_D, v);
             tm_wait_ld();
             #pragma unroll
-            for (int j = 0; j < XN; ++j) planes[(size_t)(w * XN + j) * XLD + l] = make_float2(v[2 * j], v[2 * j + 1]);
+            for (int j = 0; j < XN; ++j)
+                st_dsmem(xr[j / XP] + (uint32_t)(j % XP) * SLAB, make_float2(v[2 * j], v[2 * j + 1]));
             tc_fence_before();
             cluster_barrier<XC>();
-            // 3: pencil (j2, j3 = l) over k1 from the cluster, rows (j2, j3) = tid, K = k1
+            // 3: pencil (j2, j3 = l) over k1 from X, rows (j2, j3) = tid, K = k1
             #pragma unroll
             for (int k = 0; k < XN; ++k) {
-                const float2 x = ld_dsmem(pen[k / XP] + (uint32_t)(k % XP) * PLANE_BYTES);
+                const float2 x = xpen[(size_t)(w * XN + k) * XN + l];
                 v[2 * k] = x.x; v[2 * k + 1] = x.y;
             }
             store_k(sA, v, tid);
@@ -353,18 +350,22 @@ __global__ void __launch_bounds__(XT, 2) k_mixed(const ItemArgs a, const uint4 *
             store_k(sA, v, tid);
             run_pass(0);
             wait_pass();
-            // D4 = pencil over k1 -> back into the planes of the cluster
+            // D4 = pencil over k1 -> Y of the CTA that owns plane k1
             tm_ld64(tl + TM_D, v);
             tm_wait_ld();
             #pragma unroll
             for (int k = 0; k < XN; ++k)
-                st_dsmem(pen[k / XP] + (uint32_t)(k % XP) * PLANE_BYTES, make_float2(v[2 * k], v[2 * k + 1]));
+                st_dsmem(yr[k / XP] + (uint32_t)(k % XP) * SLAB, make_float2(v[2 * k], v[2 * k + 1]));
+            // this term's alpha_p(k1, k2 = i, k3 = l), loaded while the cluster catches up
+            float2 al[XN];
+            #pragma unroll
+            for (int i = 0; i < XN; ++i) al[i] = alpha_p[(size_t)(w * XN + i) * XN + l];
             tc_fence_before();
             cluster_barrier<XC>();
-            // 5: plane row (k1, j2 = l) over j3, rows (k1, j2) = tid, K = j3
+            // 5: plane row (k1, j2 = l) over j3 from Y, rows (k1, j2) = tid, K = j3
             #pragma unroll
             for (int j = 0; j < XN; ++j) {
-                const float2 x = planes[(size_t)(w * XN + l) * XLD + j];
+                const float2 x = ypl[(size_t)(w * XN + l) * XN + (j ^ (l & 15))];
                 v[2 * j] = x.x; v[2 * j + 1] = x.y;
             }
             store_k(sA, v, tid);
@@ -375,9 +376,6 @@ __global__ void __launch_bounds__(XT, 2) k_mixed(const ItemArgs a, const uint4 *
             tm_wait_ld();
             store_mn(sA, v, w, l);
             run_pass(1);
-            float2 al[XN];                                       // alpha_p(k1, k2 = i, k3 = l)
-            #pragma unroll
-            for (int i = 0; i < XN; ++i) al[i] = alpha_p[(size_t)(w * XN + i) * XN + l];
             wait_pass();
             // acc += alpha_p conj(D6): row (k1, k3 = l) over k2
             #pragma unroll
@@ -402,7 +400,6 @@ __global__ void __launch_bounds__(XT, 2) k_mixed(const ItemArgs a, const uint4 *
             }
             tm_wait_st();
         }
-        cp_async_wait_all();
         {
             float s[64];
             tm_ld64(tl + TM_ACC, s);
