@@ -88,12 +88,28 @@ def _bytes_per_term(N):
             "fused": 8 * n}              # alpha_p from HBM; fhat and h are L2/SMEM-resident, the field stays on chip
 
 
+_PROFILES = {
+    # kernel kind: (summary under profiles/, kernel sources the summary was taken from)
+    "fused": ("fused_rk4_n32.md", ("bz_fused.cu", "bz_fft.cuh", "bz_cluster.cuh")),
+    "mixed": ("mixed_rk4_n32.md", ("bz_mixed.cu", "bz_fft.cuh", "bz_cluster.cuh")),
+}
+
+
+def _sources_hash(files):
+    import hashlib
+    src = os.path.join(ROOT, "paper_2004_11239_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in files:
+        h.update(open(os.path.join(src, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def _profiled_traffic(kernel, workload):
     """DRAM bytes per launch from the committed ncu summary, if the kernel sources still match."""
-    import hashlib
-    if kernel != "fused" or workload != "rk4_n32":
+    if kernel not in _PROFILES or workload != "rk4_n32":
         return None
-    prof = os.path.join(ROOT, "profiles", "fused_rk4_n32.md")
+    name, files = _PROFILES[kernel]
+    prof = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(prof):
         return None
     vals = {}
@@ -101,11 +117,7 @@ def _profiled_traffic(kernel, workload):
         if ":" in line and line.startswith("    "):
             k, v = line.strip().split(":", 1)
             vals[k.strip()] = v.strip()
-    src = os.path.join(ROOT, "paper_2004_11239_gb300", "csrc")
-    h = hashlib.sha256()
-    for f in ("bz_fused.cu", "bz_fft.cuh", "bz_cluster.cuh"):
-        h.update(open(os.path.join(src, f), "rb").read())
-    if vals.get("kernel_sources_sha256_16") != h.hexdigest()[:16]:
+    if vals.get("kernel_sources_sha256_16") != _sources_hash(files):
         return None
     return float(vals["traffic_bytes_per_launch"])
 
@@ -433,7 +445,8 @@ def _measure_mixed(args, w, bz, plan32, f_host, L, R, st, peaks, src, barrier):
             "rel_linf_vs_fp32_form": dev, "device_errors": errors,
             "gpu_launches": launches_per_step * args.steps,
             "roofline": {"bound": "tensor", "kernel": "k_mixed", "achieved": tc, "peak": tc_peak,
-                         "unit": "TFLOP/s", "frac": tc / tc_peak, "launches": n_launch,
+                         "unit": "TFLOP/s", "frac": tc / tc_peak,
+                         "traffic": _profiled_traffic("mixed", args.workload), "launches": n_launch,
                          "avg_launch_us": avg_s * 1e6,
                          "peak_source": f"{src} bf16 (sustained)" if "bf16_tflops_sustained" in peaks else src,
                          "work": "split-BF16 DFT-GEMM flops: 6 x 2 N^2 x 2N x 3 x 2N per term",
