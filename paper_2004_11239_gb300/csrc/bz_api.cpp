@@ -135,9 +135,9 @@ bz_status create(bz_plan **out, const bz_plan_desc *d) {
     const size_t field = n3 * sizeof(float2);
     int chunk = d->chunk_terms;
     if (chunk <= 0) {
-        size_t target = (size_t)32 << 20;          // chunk scratch sized to stay in L2
-        chunk = (int)(target / field);
-        if (chunk < 1) chunk = 1;
+        // one wave of plane CTAs, within an L2-sized scratch
+        if (bz::collide_set_attributes(N) != cudaSuccess) { delete h; return BZ_ERR_CUDA; }
+        chunk = bz::chunk_terms_for(N);
     }
     if (chunk > pl.P) chunk = pl.P;
     if (chunk > 65535) chunk = 65535;

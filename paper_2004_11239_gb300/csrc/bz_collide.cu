@@ -18,7 +18,8 @@
 namespace bz {
 
 template <int N> struct Cfg {
-    static constexpr int PPC = N <= 8 ? 8 : (N <= 16 ? 16 : (N <= 32 ? 8 : 4));   // planes per CTA
+    // planes per CTA; N = 64 takes two so that three CTAs (12 warps) share an SM
+    static constexpr int PPC = N <= 8 ? 8 : (N <= 16 ? 16 : (N <= 32 ? 8 : (N <= 48 ? 4 : 2)));
     static constexpr int LD = N + 1;                                              // padded row
     static constexpr int THREADS = PPC * N;
     static constexpr size_t SMEM = (size_t)PPC * N * LD * sizeof(float2);
@@ -69,7 +70,7 @@ k_plane_inv(const float2 *__restrict__ fin, const float2 *__restrict__ tw, float
 //   MODE 1: S = FFT_1( h . IFFT_1(S) )              (in place)
 // ---------------------------------------------------------------------------------------
 template <int N, int MODE>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, 3)
 k_pencil(float2 *__restrict__ S, const float2 *__restrict__ h, float2 *__restrict__ out) {
     constexpr int N2 = N * N;
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
@@ -169,6 +170,35 @@ template <int N> static cudaError_t set_attrs() {
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_plane_fwd<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)Cfg<N>::SMEM);
+}
+
+// Terms per chunk: as many as one wave of plane CTAs holds (resident CTAs / CTAs per term),
+// capped by an L2-sized scratch of 32 MB.
+template <int N> static int chunk_for() {
+    int per_sm = 0, dev = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_plane_inv<N>, Cfg<N>::THREADS, Cfg<N>::SMEM) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int wave = per_sm * sms / (N / Cfg<N>::PPC);
+    const int l2 = (int)(((size_t)32 << 20) / ((size_t)N * N * N * sizeof(float2)));
+    const int c = wave < l2 ? wave : l2;
+    return c > 0 ? c : 1;
+}
+
+int chunk_terms_for(int N) {
+    switch (N) {
+        case 8: return chunk_for<8>();
+        case 16: return chunk_for<16>();
+        case 24: return chunk_for<24>();
+        case 32: return chunk_for<32>();
+        case 48: return chunk_for<48>();
+        case 64: return chunk_for<64>();
+    }
+    return 1;
 }
 
 cudaError_t collide_set_attributes(int N) {

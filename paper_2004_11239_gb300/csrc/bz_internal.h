@@ -129,6 +129,7 @@ cudaError_t mixed_setup(int N, int *G);
 bz_status mixed_upload(uint4 **wimg);
 bz_status launch_mixed(const Plan &pl, const ItemArgs &a, cudaStream_t st);
 cudaError_t collide_set_attributes(int N);
+int chunk_terms_for(int N);          // after collide_set_attributes(N)
 int supported_N(int N);
 
 // bz_rk.cu
