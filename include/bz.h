@@ -67,6 +67,18 @@ enum { BZ_KERNEL_FAMILY = 0, BZ_KERNEL_B5 = 1, BZ_KERNEL_B8 = 2 };
  *                   L-infinity error 1e-3 of max |Qhat|. */
 enum { BZ_PREC_FP32 = 0, BZ_PREC_BF16X3 = 1 };
 
+/* Form of the inner sum over l + m = k (Sec. 2, eq. sum; Sec. 4, eq. realQ).
+ *   BZ_CONV_CIRCULAR: l + m = k modulo N, the N-point FFT convolution the fast method
+ *                     computes (eq. realQ).
+ *   BZ_CONV_PADDED:   l + m = k without wrap-around, the literal Galerkin sum of eq. sum: the
+ *                     plan runs the circular pipeline on a 2N grid (N = 8, 16 fused; 24, 32
+ *                     chunked), the input embedded with the modes outside -N/2..N/2-1 zero,
+ *                     alpha zero outside that range, and returns the N-range.  FP32 form;
+ *                     bz_collide, bz_collide_terms, bz_moments and bz_ftable_entries take and
+ *                     return N^3 arrays as for a circular plan; bz_step_rk, bz_plan_alpha,
+ *                     bz_collide_noalloc and batches return BZ_ERR_UNSUPPORTED. */
+enum { BZ_CONV_CIRCULAR = 0, BZ_CONV_PADDED = 1 };
+
 /* Collide pipelines.  FUSED: one thread-block cluster per term keeps the whole field in
  * (distributed) shared memory from twiddle to weighted accumulation (N <= 32).  CHUNKED:
  * four kernels per chunk of terms over an L2-sized scratch buffer (every N).  AUTO picks
@@ -100,6 +112,7 @@ typedef struct {
     int cluster;      /* FUSED: CTAs per cluster (N=16: 1|2, 24: 2|3, 32: 4|8); <= 0 times the
                          compiled sizes at creation and keeps the fastest                   */
     int h_precision;  /* BZ_H_*                                                            */
+    int conv;         /* BZ_CONV_*                                                         */
 } bz_plan_desc;
 
 /* Creates a plan: quadrature terms, the FP64 F table (computed on the device, stored

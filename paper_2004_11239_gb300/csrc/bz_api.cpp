@@ -112,6 +112,9 @@ bz_status create(bz_plan **out, const bz_plan_desc *d) {
     if (!bz::supported_N(d->N) || d->N_rho < 1 || d->M < 1 || !(d->L > 0) || !(d->R > 0))
         return BZ_ERR_ARG;
     if (d->precision != BZ_PREC_FP32 && d->precision != BZ_PREC_BF16X3) return BZ_ERR_ARG;
+    if (d->conv != BZ_CONV_CIRCULAR && d->conv != BZ_CONV_PADDED) return BZ_ERR_ARG;
+    const bool padded = d->conv == BZ_CONV_PADDED;
+    if (padded && (d->N > 32 || d->precision != BZ_PREC_FP32)) return BZ_ERR_UNSUPPORTED;
     if (d->precision == BZ_PREC_BF16X3 && (d->N != 32 || d->pipeline == BZ_PIPE_CHUNKED))
         return BZ_ERR_UNSUPPORTED;
     if (d->pipeline < BZ_PIPE_AUTO || d->pipeline > BZ_PIPE_CHUNKED) return BZ_ERR_ARG;
@@ -119,7 +122,7 @@ bz_status create(bz_plan **out, const bz_plan_desc *d) {
     bz_plan *h = new (std::nothrow) bz_plan();
     if (!h) return BZ_ERR_OOM;
     bz::Plan &pl = h->p;
-    pl.N = d->N; pl.L = d->L; pl.R = d->R; pl.gamma = d->gamma; pl.s = d->s;
+    pl.N = padded ? 2 * d->N : d->N; pl.Nin = padded ? d->N : 0; pl.L = d->L; pl.R = d->R; pl.gamma = d->gamma; pl.s = d->s;
     pl.N_rho = d->N_rho; pl.M = d->M; pl.kernel = d->kernel; pl.precision = d->precision;
     pl.eps = d->eps > 0 ? d->eps : M_PI / 1000.0;
     if (d->h_precision < BZ_H_AUTO || d->h_precision > BZ_H_FP32) { delete h; return BZ_ERR_ARG; }
@@ -269,6 +272,7 @@ bz_status bz_step_rk(bz_plan *plan, void *fhat, int dtype, double *t, double dt,
     (void)workspace;
     if (!plan || !fhat || nsteps < 0 || !std::isfinite(dt)) return BZ_ERR_ARG;
     if (dtype != BZ_C64 && dtype != BZ_C128) return BZ_ERR_ARG;
+    if (plan->p.Nin) return BZ_ERR_UNSUPPORTED;               // padded plans: bz_collide
     int nl = 0;
     bz_status s = bz::rk4_steps(plan->p, fhat, dtype, dt, nsteps, (cudaStream_t)stream, &nl);
     plan->p.last_launches = nl;
@@ -292,6 +296,7 @@ bz_status bz_plan_alpha(const bz_plan *plan, int p0, int p1, void *dst, void *st
     if (!plan || !dst) return BZ_ERR_ARG;
     const bz::Plan &pl = plan->p;
     if (p0 < 0 || p1 < p0 || p1 > pl.P) return BZ_ERR_ARG;
+    if (pl.Nin) return BZ_ERR_UNSUPPORTED;                    // the padded table lives on the 2N grid
     size_t n3 = (size_t)pl.N * pl.N * pl.N;
     if (cudaMemcpyAsync(dst, pl.alpha + (size_t)p0 * n3, (size_t)(p1 - p0) * n3 * sizeof(float2),
                         cudaMemcpyDeviceToDevice, (cudaStream_t)stream) != cudaSuccess)

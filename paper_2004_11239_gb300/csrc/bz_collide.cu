@@ -157,6 +157,47 @@ __global__ void k_acc_to_c64(const double2 *__restrict__ in, float2 *__restrict_
     if (i < n) out[i] = make_float2((float)in[i].x, (float)in[i].y);
 }
 
+// Padded plans (BZ_CONV_PADDED): the caller's Nin-grid lives inside the N = 2 Nin grid at the
+// same signed modes.  Embed: one thread per N-grid mode, zero outside the caller's range.
+__global__ void k_embed(const void *__restrict__ f, int dtype, int Nin, int N, float2 *__restrict__ out,
+                        double2 *__restrict__ out64) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N * N * N) return;
+    const int h = Nin / 2;
+    int s[3] = {i / (N * N), (i / N) % N, i % N};
+    bool in = true;
+    size_t src = 0;
+    #pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const int k = s[d] < N / 2 ? s[d] : s[d] - N;
+        in = in && k >= -h && k < h;
+        src = src * Nin + (size_t)((k + Nin) % Nin);
+    }
+    double2 v = make_double2(0.0, 0.0);
+    if (in) {
+        if (dtype == BZ_C128) v = ((const double2 *)f)[src];
+        else { const float2 w = ((const float2 *)f)[src]; v = make_double2(w.x, w.y); }
+    }
+    out[i] = make_float2((float)v.x, (float)v.y);
+    if (out64) out64[i] = v;
+}
+
+// Extract: one thread per caller mode, from the FP64 accumulator of the N grid.
+__global__ void k_extract(const double2 *__restrict__ acc, int Nin, int N, void *__restrict__ Q, int dtype) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Nin * Nin * Nin) return;
+    int s[3] = {i / (Nin * Nin), (i / Nin) % Nin, i % Nin};
+    size_t src = 0;
+    #pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const int k = s[d] < Nin / 2 ? s[d] : s[d] - Nin;
+        src = src * N + (size_t)((k + N) % N);
+    }
+    const double2 v = acc[src];
+    if (dtype == BZ_C128) ((double2 *)Q)[i] = v;
+    else ((float2 *)Q)[i] = make_float2((float)v.x, (float)v.y);
+}
+
 // ---------------------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------------------
@@ -248,6 +289,16 @@ static bz_status run_chunks(Plan &pl, int p0, int p1, cudaStream_t st, int *laun
 
 bz_status load_input(Plan &pl, const void *fhat, int dtype, cudaStream_t st, int *launches) {
     const int n3 = pl.N * pl.N * pl.N;
+    if (dtype != BZ_C64 && dtype != BZ_C128) return BZ_ERR_ARG;
+    if (pl.Nin) {
+        // padded: embed into the 2N grid, in FP32 and (where the FP64 h pass reads it) FP64
+        k_embed<<<(n3 + 255) / 256, 256, 0, st>>>(fhat, dtype, pl.Nin, pl.N, pl.fin, pl.fin64);
+        BZ_CUDA_TRY(cudaGetLastError());
+        pl.src = pl.fin64;
+        pl.src_dtype = BZ_C128;
+        if (launches) *launches += 1;
+        return BZ_OK;
+    }
     pl.src = fhat;                 // the fused path forms h from the caller's array in FP64
     pl.src_dtype = dtype;
     if (dtype == BZ_C64) {
@@ -285,6 +336,14 @@ bz_status collide_range(Plan &pl, int p0, int p1, const void *fhat, int in_dtype
 
 bz_status write_output(Plan &pl, void *Qhat, int dtype, cudaStream_t st, int *launches) {
     const int n3 = pl.N * pl.N * pl.N;
+    if (pl.Nin) {
+        if (dtype != BZ_C64 && dtype != BZ_C128) return BZ_ERR_ARG;
+        const int m3 = pl.Nin * pl.Nin * pl.Nin;
+        k_extract<<<(m3 + 255) / 256, 256, 0, st>>>(pl.acc, pl.Nin, pl.N, Qhat, dtype);
+        BZ_CUDA_TRY(cudaGetLastError());
+        if (launches) *launches += 1;
+        return BZ_OK;
+    }
     if (dtype == BZ_C128) {
         BZ_CUDA_TRY(cudaMemcpyAsync(Qhat, pl.acc, (size_t)n3 * sizeof(double2), cudaMemcpyDeviceToDevice, st));
     } else if (dtype == BZ_C64) {
@@ -385,6 +444,7 @@ extern "C" bz_status bz_collide_noalloc(const bz_plan *plan, const void *fhat, v
     if (!plan || !fhat || !Qhat || fhat == Qhat) return BZ_ERR_ARG;
     if (dtype != BZ_C64 && dtype != BZ_C128) return BZ_ERR_ARG;
     const Plan &pl = *plan_internal(plan);
+    if (pl.Nin) return BZ_ERR_UNSUPPORTED;                   // padded plans: bz_collide
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return BZ_ERR_CUDA;
     if (dev != pl.device) return BZ_ERR_ARG;

@@ -48,6 +48,7 @@ __device__ __forceinline__ double2 f_value(double x, double y, const double *A, 
 
 struct TableArgs {
     int N, M, P, p0;
+    int nin;                 // > 0: alpha is zero outside the signed range [-nin/2, nin/2) per axis
     double L, inv_n3;
     double A0, A1, A2;
     const double *term;      // [P][5]: r, q0, q1, q2, c
@@ -83,6 +84,16 @@ __global__ void ftable_kernel(TableArgs a) {
         midx = (((-k1 + N) % N) * N + ((-k2 + N) % N)) * N + ((-k3 + N) % N);
         if (midx < idx) return;                           // written by the partner's thread
     }
+    // padded plans: only the modes of the caller's grid carry a weight (both members of the pair
+    // are tested: -k leaves the range when a component of k is -nin/2)
+    const int h = a.nin / 2;
+    const bool in_k = a.nin == 0 || (k1 >= -h && k1 < h && k2 >= -h && k2 < h && k3 >= -h && k3 < h);
+    const bool in_m = midx >= 0 && (a.nin == 0 || (-k1 >= -h && -k1 < h && -k2 >= -h && -k2 < h && -k3 >= -h && -k3 < h));
+    if (!in_k && !in_m) {
+        a.alpha[(size_t)p * n3 + idx] = make_float2(0.f, 0.f);
+        if (midx > idx) a.alpha[(size_t)p * n3 + midx] = make_float2(0.f, 0.f);
+        return;
+    }
     const double *tp = a.term + 5 * (size_t)p;
     double r = tp[0];
     double kap = k1 * tp[1] + k2 * tp[2] + k3 * tp[3];
@@ -93,8 +104,9 @@ __global__ void ftable_kernel(TableArgs a) {
     double A[3] = {a.A0, a.A1, a.A2};
     double2 F = f_value(aa * kap, aa * kp, A, n, omc, sn, W);
     double sc = tp[4] * a.inv_n3;
-    a.alpha[(size_t)p * n3 + idx] = make_float2((float)(sc * F.x), (float)(sc * F.y));
-    if (midx > idx) a.alpha[(size_t)p * n3 + midx] = make_float2((float)(sc * F.x), (float)(-sc * F.y));
+    a.alpha[(size_t)p * n3 + idx] = in_k ? make_float2((float)(sc * F.x), (float)(sc * F.y)) : make_float2(0.f, 0.f);
+    if (midx > idx)
+        a.alpha[(size_t)p * n3 + midx] = in_m ? make_float2((float)(sc * F.x), (float)(-sc * F.y)) : make_float2(0.f, 0.f);
 }
 
 struct EntryArgs {
@@ -175,7 +187,7 @@ bz_status ftable_build(Plan &pl) {
     if (smem > 48 * 1024)
         BZ_CUDA_TRY(cudaFuncSetAttribute(ftable_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     TableArgs a;
-    a.N = N; a.M = pl.M; a.P = P; a.L = pl.L;
+    a.N = N; a.M = pl.M; a.P = P; a.L = pl.L; a.nin = pl.Nin;
     a.inv_n3 = 1.0 / ((double)N * N * N);
     a.A0 = pl.A[0]; a.A1 = pl.A[1]; a.A2 = pl.A[2];
     a.term = pl.term_dev; a.rule = pl.rule_buf; a.rule_off = pl.rule_off; a.alpha = pl.alpha;
@@ -194,7 +206,8 @@ bz_status ftable_build(Plan &pl) {
 bz_status ftable_entries(Plan &pl, int count, const int *k_idx, const int *term, double *out) {
     if (count <= 0) return count == 0 ? BZ_OK : BZ_ERR_ARG;
     EntryArgs a;
-    a.N = pl.N; a.M = pl.M; a.P = pl.P; a.count = count; a.L = pl.L;
+    a.N = pl.Nin ? pl.Nin : pl.N;      // indices address the caller's grid
+    a.M = pl.M; a.P = pl.P; a.count = count; a.L = pl.L;
     a.A0 = pl.A[0]; a.A1 = pl.A[1]; a.A2 = pl.A[2];
     a.term = pl.term_dev; a.rule = pl.rule_buf; a.rule_off = pl.rule_off;
     a.k_idx = k_idx; a.tsel = term; a.out = out;

@@ -36,6 +36,7 @@ struct Timing {
 struct Plan {
     // parameters
     int N = 0, N_rho = 0, M = 0, P = 0, kernel = 0, precision = 0, device = 0;
+    int Nin = 0;                    // BZ_CONV_PADDED: the caller's modes per axis (N = 2 Nin); 0 = circular
     double L = 0, R = 0, gamma = 0, s = 0, eps = 0;
     double A[3] = {0, 0, 0};        // part I kernel moments
     double kc = 0;                  // kernel constant (c_s, 1/(4 pi), 5/(192 pi))

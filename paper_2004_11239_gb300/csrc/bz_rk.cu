@@ -116,7 +116,7 @@ bz_status rk4_steps(Plan &pl, void *fhat, int dtype, double dt, int nsteps, cuda
 }
 
 bz_status moments(Plan &pl, const void *fhat, int dtype, double out[5], cudaStream_t st) {
-    k_moments<<<1, 32, 0, st>>>(fhat, dtype, pl.N, pl.L, pl.mom);
+    k_moments<<<1, 32, 0, st>>>(fhat, dtype, pl.Nin ? pl.Nin : pl.N, pl.L, pl.mom);   // the caller's grid
     BZ_CUDA_TRY(cudaGetLastError());
     BZ_CUDA_TRY(cudaMemcpyAsync(out, pl.mom, 5 * sizeof(double), cudaMemcpyDeviceToHost, st));
     BZ_CUDA_TRY(cudaStreamSynchronize(st));

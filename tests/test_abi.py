@@ -48,15 +48,17 @@ def test_status_strings_and_argument_checks_without_gpu(libpath):
 
 
 def test_precision_checks_without_gpu(libpath):
-    """The split-BF16 form exists for the fused N = 32 pipeline only; the checks come before
-    any CUDA call."""
+    """The split-BF16 form exists for the fused N = 32 pipeline only, the padded form for
+    N <= 32 in FP32; the checks come before any CUDA call."""
     import paper_2004_11239_gb300 as bz
     h = ctypes.c_void_p()
-    for N, prec, pipe, want in [(16, bz.BZ_PREC_BF16X3, 0, 7), (32, bz.BZ_PREC_BF16X3, bz.BZ_PIPE_CHUNKED, 7),
-                                (32, 5, 0, 1)]:
+    P, C = bz.BZ_CONV_PADDED, bz.BZ_CONV_CIRCULAR
+    for N, prec, pipe, conv, want in [(16, bz.BZ_PREC_BF16X3, 0, C, 7), (32, bz.BZ_PREC_BF16X3, bz.BZ_PIPE_CHUNKED, C, 7),
+                                      (32, 5, 0, C, 1), (64, 0, 0, P, 7), (16, bz.BZ_PREC_BF16X3, 0, P, 7),
+                                      (16, 0, 0, 5, 1)]:
         d = bz.bz_plan_desc()
         d.N, d.L, d.R, d.gamma, d.s, d.N_rho, d.M = N, 10.0, 9.0, 0.0, 0.5, 2, 12
-        d.precision, d.pipeline = prec, pipe
+        d.precision, d.pipeline, d.conv = prec, pipe, conv
         assert bz.lib.bz_plan_create_ex(ctypes.byref(h), ctypes.byref(d)) == want
         assert h.value is None
 
