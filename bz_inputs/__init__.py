@@ -91,6 +91,40 @@ def bkw_fhat(N: int, L: float, K: float) -> np.ndarray:
     return val.astype(np.complex128) / (2.0 * L) ** 3
 
 
+def bkw2d_K(t: float, lam: float = 0.125, C: float = 0.5) -> float:
+    """K(t) = 1 - C exp(-lambda t) with the 2D benchmark values C = 1/2, lambda = 1/8 (Sec. 5.1)."""
+    return 1.0 - C * math.exp(-lam * t)
+
+
+def grid2d_cells(N: int, L: float) -> np.ndarray:
+    """Cell-centred 2D velocity nodes v_j = -L + 2L (j + 1/2) / N (the grid of Table 1)."""
+    return -L + 2.0 * L * (np.arange(N) + 0.5) / N
+
+
+def bkw2d_fhat_samples(N: int, L: float, K: float) -> np.ndarray:
+    """[N, N] coefficients whose trigonometric interpolant takes the 2D BKW values (Sec. 5.1,
+    eq. BKW, d = 2) at the cell-centred nodes: fhat_k = N^-2 sum_j f(v_j) exp(-i pi k.v_j / L)."""
+    v = grid2d_cells(N, L)
+    V1, V2 = np.meshgrid(v, v, indexing="ij")
+    v2 = V1 ** 2 + V2 ** 2
+    f = np.exp(-v2 / (2 * K)) / (2 * math.pi * K) * ((4 * K - 2) / (2 * K) + (1 - K) / (2 * K * K) * v2)
+    E = np.exp(-1j * math.pi * np.outer(signed_modes(N), v) / L)
+    return E @ f @ E.T / N ** 2
+
+
+def random_mixture2d(N: int, L: float, seed: int, box: float = 2.0) -> np.ndarray:
+    """Two 2D Maxwellians of mass 1/2, centres uniform in [-box, box]^2, T in [0.5, 2]."""
+    u = SplitMix64(seed).uniform(6)
+    w = math.pi * signed_modes(N).astype(np.float64) / L
+    W1, W2 = np.meshgrid(w, w, indexing="ij")
+    out = np.zeros((N, N), dtype=np.complex128)
+    for g in range(2):
+        c1, c2 = box * (2 * u[3 * g] - 1), box * (2 * u[3 * g + 1] - 1)
+        T = 0.5 + 1.5 * u[3 * g + 2]
+        out += 0.5 * np.exp(-1j * (W1 * c1 + W2 * c2) - 0.5 * T * (W1 ** 2 + W2 ** 2))
+    return out / (2.0 * L) ** 2
+
+
 def grid_samples_to_fhat(fv: np.ndarray, L: float) -> np.ndarray:
     """fhat_k = N^-3 sum_j f(v_j) exp(-i pi k.v_j/L) with v_j = -L + 2L j/N (library FFT)."""
     N = fv.shape[0]

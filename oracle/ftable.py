@@ -33,14 +33,14 @@ NPTS_DEFAULT = 20                # Gauss-Legendre points per panel of part II
 
 
 def build(force: bool = False) -> str:
-    """Compile ftable.c into _build/liboracle.so with gcc (FP64, OpenMP)."""
-    src = os.path.join(_HERE, "ftable.c")
-    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= os.path.getmtime(src):
+    """Compile ftable.c and ftable2d.c into _build/liboracle.so with gcc (FP64, OpenMP)."""
+    srcs = [os.path.join(_HERE, "ftable.c"), os.path.join(_HERE, "ftable2d.c")]
+    if not force and os.path.exists(_SO) and all(os.path.getmtime(_SO) >= os.path.getmtime(x) for x in srcs):
         return _SO
     os.makedirs(_BUILD, exist_ok=True)
     tmp = _SO + f".tmp{os.getpid()}"
     subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-fno-fast-math",
-                           "-o", tmp, src, "-lm"])
+                           "-o", tmp] + srcs + ["-lm"])
     os.replace(tmp, _SO)
     return _SO
 
@@ -60,6 +60,10 @@ def _load():
                                         ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                         ctypes.c_double, dp, ctypes.c_int, dp, dp, dp]
         lib.oracle_fentries.restype = ctypes.c_int
+        lib.oracle_ftable2d.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int, dp, dp,
+                                        ctypes.c_int, ctypes.c_double, ctypes.c_double, dp,
+                                        ctypes.c_int, dp, dp, dp]
+        lib.oracle_ftable2d.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -104,6 +108,26 @@ def fentries(N: int, L: float, k, r, qhat, kernel: Kernel, eps: float = EPS_DEFA
                              _dp(gx), _dp(gw), _dp(out.view(np.float64)))
     if rc != 0:
         raise MemoryError("oracle_fentries failed")
+    return out
+
+
+def ftable2d(N: int, L: float, r, qhat, kernel, eps: float = EPS_DEFAULT,
+             npts: int = NPTS_DEFAULT) -> np.ndarray:
+    """2D F (eq. FF2D1, three-part split of Sec. 4.1) for every mode of the N^2 grid and term
+    (r[p], qhat[p] in R^2); [P, N, N] c128.  kernel is a kernels.Kernel2D."""
+    lib = _load()
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    qhat = np.ascontiguousarray(qhat, dtype=np.float64).reshape(-1, 2)
+    P = len(r)
+    A = np.array(kernel.taylor_moments(eps), dtype=np.float64)
+    gx, gw = gauss_legendre(npts)
+    gx = np.ascontiguousarray(gx)
+    gw = np.ascontiguousarray(gw)
+    out = np.empty((P, N, N), dtype=np.complex128)
+    rc = lib.oracle_ftable2d(N, L, P, _dp(r), _dp(qhat), kernel.kid, kernel.c, eps, _dp(A), npts,
+                             _dp(gx), _dp(gw), _dp(out.view(np.float64)))
+    if rc != 0:
+        raise MemoryError("oracle_ftable2d failed")
     return out
 
 

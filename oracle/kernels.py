@@ -95,3 +95,73 @@ class Kernel:
 
 def kernel_from(name: str, s: float = 0.0) -> Kernel:
     return Kernel(name, float(s))
+
+
+# ---------------------------------------------------------------------------
+# 2D kernels (Sec. 5.2, eqs. b1-b4): b(cos theta) on theta in [0, 2 pi], the measure on S^1
+# being d theta; all four give lambda = 1/8 (eq. KK2).  On (0, pi], b = c sin^beta(theta/2)
+# (times |cos(theta/2)| for b4).
+# ---------------------------------------------------------------------------
+
+_B2D = {  # name: (kid, c, beta, has_cos)
+    "b1": (3, 1.0 / (2.0 * math.pi), 0.0, False),
+    "b2": (4, 3.0 / 32.0, -1.0, False),
+    "b3": (5, 1.0 / (8.0 * math.pi), -2.0, False),
+    "b4": (6, 5.0 / 256.0, -2.5, True),
+}
+
+
+def _int_sin_pow(alpha: float, W: float) -> float:
+    """int_0^eps sin^alpha(theta/2) d theta, W = sin(eps/2), by the power series of arcsin."""
+    tot, coef, n = 0.0, 1.0, 0
+    while True:
+        term = coef * W ** (alpha + 2 * n + 1) / (alpha + 2 * n + 1)
+        tot += term
+        if abs(term) < 1e-30 * abs(tot) or n > 60:
+            break
+        n += 1
+        coef *= (2 * n - 1) / (2 * n)
+    return 2.0 * tot
+
+
+@dataclass(frozen=True)
+class Kernel2D:
+    name: str          # "b1", "b2", "b3", "b4"
+
+    @property
+    def kid(self) -> int:
+        return _B2D[self.name][0]
+
+    @property
+    def c(self) -> float:
+        return _B2D[self.name][1]
+
+    def b(self, theta):
+        """b(cos theta) for theta in (0, 2 pi)."""
+        import numpy as np
+        th = np.asarray(theta, dtype=np.float64)
+        _, c, beta, has_cos = _B2D[self.name]
+        v = c * np.sin(0.5 * th) ** beta
+        return v * np.abs(np.cos(0.5 * th)) if has_cos else v
+
+    def taylor_moments(self, eps: float):
+        """(A1, A2, A3) = int_0^eps b (1-cos, (1-cos)^2, sin^2) d theta (parts I and III)."""
+        _, c, beta, has_cos = _B2D[self.name]
+        W = math.sin(0.5 * eps)
+        if has_cos:
+            # int_0^eps sin^a(t/2) cos(t/2) dt = 2 W^(a+1) / (a+1)
+            A1 = 2.0 * c * 2.0 * W ** (beta + 3.0) / (beta + 3.0)
+            A2 = 4.0 * c * 2.0 * W ** (beta + 5.0) / (beta + 5.0)
+        else:
+            A1 = 2.0 * c * _int_sin_pow(beta + 2.0, W)     # 1 - cos = 2 sin^2(t/2)
+            A2 = 4.0 * c * _int_sin_pow(beta + 4.0, W)
+        A3 = 2.0 * A1 - A2                                  # sin^2 = 2 (1 - cos) - (1 - cos)^2
+        return A1, A2, A3
+
+    def lam(self) -> float:
+        """lambda = (1/4) int_0^{2 pi} sin^2(theta) b d theta (Sec. 5.1) in closed form: with
+        sin^2 = 4 sin^2(t/2) cos^2(t/2) and u = sin(t/2) each kernel is a Beta integral,
+        2 c B((beta + 3)/2, (3 + [cos factor])/2)."""
+        _, c, beta, has_cos = _B2D[self.name]
+        e = 1.0 if has_cos else 0.0
+        return 2.0 * c * beta_fn((beta + 3.0) / 2.0, (3.0 + e) / 2.0)
