@@ -96,6 +96,21 @@ def bkw2d_K(t: float, lam: float = 0.125, C: float = 0.5) -> float:
     return 1.0 - C * math.exp(-lam * t)
 
 
+def bkw2d_fhat(N: int, L: float, K: float) -> np.ndarray:
+    """Fourier coefficients [N, N] of the 2D BKW profile (Sec. 5.1, eq. BKW with d = 2).
+
+    f(v) = (2 pi K)^-1 exp(-|v|^2/(2K)) (A + B |v|^2), A = (2K-1)/K, B = (1-K)/(2K^2); its
+    transform is (A + B (2K - K^2 |w|^2)) exp(-K |w|^2 / 2), sampled at w = pi k / L.
+    """
+    w = math.pi * signed_modes(N).astype(np.float64) / L
+    W1, W2 = np.meshgrid(w, w, indexing="ij")
+    w2sum = W1 ** 2 + W2 ** 2
+    A = (2.0 * K - 1.0) / K
+    B = (1.0 - K) / (2.0 * K * K)
+    val = (A + B * (2.0 * K - K * K * w2sum)) * np.exp(-0.5 * K * w2sum)
+    return val.astype(np.complex128) / (2.0 * L) ** 2
+
+
 def grid2d_cells(N: int, L: float) -> np.ndarray:
     """Cell-centred 2D velocity nodes v_j = -L + 2L (j + 1/2) / N (the grid of Table 1)."""
     return -L + 2.0 * L * (np.arange(N) + 0.5) / N

@@ -56,6 +56,12 @@ enum { BZ_C64 = 0, BZ_C128 = 1 };
  *   BZ_KERNEL_B8:     b = 5 cos(theta/2) / (192 pi sin(theta) sin^(5/2)(theta/2)), eq. b8. */
 enum { BZ_KERNEL_FAMILY = 0, BZ_KERNEL_B5 = 1, BZ_KERNEL_B8 = 2 };
 
+/* 2D angular kernels (dim = 2; Sec. 5.2, eqs. b1-b4), b(cos theta) on theta in [0, 2 pi] with
+ * the measure d theta on the circle, all with lambda = 1/8 (eq. KK2):
+ *   BZ_KERNEL_B1: 1 / (2 pi) (cutoff);          BZ_KERNEL_B2: 3 / (32 sin(theta/2));
+ *   BZ_KERNEL_B3: 1 / (8 pi sin^2(theta/2));     BZ_KERNEL_B4: 5 |cos(theta/2)| / (256 sin^(5/2)(theta/2)). */
+enum { BZ_KERNEL_B1 = 3, BZ_KERNEL_B2 = 4, BZ_KERNEL_B3 = 5, BZ_KERNEL_B4 = 6 };
+
 /* Arithmetic of the per-term transforms (Sec. 4, eq. realQ: two 3D FFTs per term).
  *   BZ_PREC_FP32:   FP32 register FFTs on the CUDA cores (every supported N).
  *   BZ_PREC_BF16X3: each one-axis transform is a DFT on the tensor cores with BF16 operands
@@ -113,6 +119,12 @@ typedef struct {
                          compiled sizes at creation and keeps the fastest                   */
     int h_precision;  /* BZ_H_*                                                            */
     int conv;         /* BZ_CONV_*                                                         */
+    int dim;          /* 3 (or 0): the 3D operator; 2: the 2D operator of Sec. 4.1 (i) and Sec. 5.2 on
+                         an N x N grid (N = 8, 16, 32 or 64; arrays [k1][k2]; kernels BZ_KERNEL_B1..B4;
+                         M midpoint points phi_j = 2 pi (j + 1/2) / M on the circle, c_p = w_i w_j
+                         r_i^gamma r_i; FP32, circular).  A 2D plan runs bz_collide, bz_collide_terms,
+                         bz_step_rk, bz_ftable_entries (k_idx's third index ignored) and the
+                         inspection calls; the others return BZ_ERR_UNSUPPORTED.                */
 } bz_plan_desc;
 
 /* Creates a plan: quadrature terms, the FP64 F table (computed on the device, stored

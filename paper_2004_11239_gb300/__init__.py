@@ -31,6 +31,7 @@ _LIB_PATH = os.path.join(_HERE, "_lib", "libbz.so")
 
 BZ_C64, BZ_C128 = 0, 1
 BZ_KERNEL_FAMILY, BZ_KERNEL_B5, BZ_KERNEL_B8 = 0, 1, 2
+BZ_KERNEL_B1, BZ_KERNEL_B2, BZ_KERNEL_B3, BZ_KERNEL_B4 = 3, 4, 5, 6   # 2D kernels (dim = 2)
 BZ_PREC_FP32, BZ_PREC_BF16X3 = 0, 1
 BZ_PIPE_AUTO, BZ_PIPE_FUSED, BZ_PIPE_CHUNKED = 0, 1, 2
 BZ_H_AUTO, BZ_H_FP64, BZ_H_FP32 = 0, 1, 2
@@ -65,7 +66,7 @@ class bz_plan_desc(ctypes.Structure):
                 ("eps", ctypes.c_double), ("sphere_xyz", ctypes.POINTER(ctypes.c_double)),
                 ("sphere_w", ctypes.POINTER(ctypes.c_double)), ("chunk_terms", ctypes.c_int),
                 ("pipeline", ctypes.c_int), ("cluster", ctypes.c_int), ("h_precision", ctypes.c_int),
-                ("conv", ctypes.c_int)]
+                ("conv", ctypes.c_int), ("dim", ctypes.c_int)]
 
 
 def library_path() -> str:
@@ -156,17 +157,18 @@ def _dtype(t) -> int:
 
 def _dev(t, n3: int):
     if not t.is_cuda or not t.is_contiguous() or t.numel() != n3:
-        raise ValueError("expected a contiguous CUDA tensor of N^3 complex values")
+        raise ValueError(f"expected a contiguous CUDA tensor of {n3} complex values (N^d)")
     return ctypes.c_void_p(t.data_ptr())
 
 
 class Plan:
     """Owning handle of a bz_plan (destroyed with the object or by close())."""
 
-    def __init__(self, handle: ctypes.c_void_p, N: int, L: float):
+    def __init__(self, handle: ctypes.c_void_p, N: int, L: float, dim: int = 3):
         self.handle = handle
         self.N = N
         self.L = L
+        self.dim = dim
         P = ctypes.c_int()
         ab = ctypes.c_size_t()
         wb = ctypes.c_size_t()
@@ -175,7 +177,8 @@ class Plan:
 
     @property
     def n3(self) -> int:
-        return self.N ** 3
+        """Modes of one field: N^3, or N^2 for a 2D plan."""
+        return self.N ** self.dim
 
     def close(self):
         if self.handle:
@@ -199,7 +202,7 @@ def bz_plan_create_ex(N: int, L: float, R: float, gamma: float, s: float, N_rho:
                       kernel: int = BZ_KERNEL_FAMILY, eps: float = 0.0, sphere=None,
                       chunk_terms: int = 0, pipeline: int = BZ_PIPE_AUTO, cluster: int = 0,
                       h_precision: int = BZ_H_AUTO, precision: int = BZ_PREC_FP32,
-                      conv: int = BZ_CONV_CIRCULAR) -> Plan:
+                      conv: int = BZ_CONV_CIRCULAR, dim: int = 3) -> Plan:
     d = bz_plan_desc()
     d.N, d.L, d.R, d.gamma, d.s, d.N_rho, d.M = N, L, R, gamma, s, N_rho, M
     d.kernel, d.precision, d.eps, d.chunk_terms = kernel, precision, eps, chunk_terms
@@ -207,6 +210,7 @@ def bz_plan_create_ex(N: int, L: float, R: float, gamma: float, s: float, N_rho:
     d.cluster = cluster
     d.h_precision = h_precision
     d.conv = conv
+    d.dim = dim
     keep = []
     if sphere is not None:
         import numpy as np
@@ -217,7 +221,7 @@ def bz_plan_create_ex(N: int, L: float, R: float, gamma: float, s: float, N_rho:
         d.sphere_w = w.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     h = ctypes.c_void_p()
     _check(lib.bz_plan_create_ex(ctypes.byref(h), ctypes.byref(d)), "bz_plan_create_ex")
-    return Plan(h, N, L)
+    return Plan(h, N, L, dim)
 
 
 def bz_plan_destroy(plan: Plan):

@@ -111,6 +111,14 @@ bz_status create(bz_plan **out, const bz_plan_desc *d) {
     *out = nullptr;
     if (!bz::supported_N(d->N) || d->N_rho < 1 || d->M < 1 || !(d->L > 0) || !(d->R > 0))
         return BZ_ERR_ARG;
+    const int dim = d->dim == 0 ? 3 : d->dim;
+    if (dim != 2 && dim != 3) return BZ_ERR_ARG;
+    if (dim == 2) {
+        if (d->N != 8 && d->N != 16 && d->N != 32 && d->N != 64) return BZ_ERR_ARG;
+        if (d->kernel < BZ_KERNEL_B1 || d->kernel > BZ_KERNEL_B4) return BZ_ERR_ARG;
+        if (d->precision != BZ_PREC_FP32 || d->conv != BZ_CONV_CIRCULAR || d->pipeline == BZ_PIPE_CHUNKED)
+            return BZ_ERR_UNSUPPORTED;
+    }
     if (d->precision != BZ_PREC_FP32 && d->precision != BZ_PREC_BF16X3) return BZ_ERR_ARG;
     if (d->conv != BZ_CONV_CIRCULAR && d->conv != BZ_CONV_PADDED) return BZ_ERR_ARG;
     const bool padded = d->conv == BZ_CONV_PADDED;
@@ -118,10 +126,11 @@ bz_status create(bz_plan **out, const bz_plan_desc *d) {
     if (d->precision == BZ_PREC_BF16X3 && (d->N != 32 || d->pipeline == BZ_PIPE_CHUNKED))
         return BZ_ERR_UNSUPPORTED;
     if (d->pipeline < BZ_PIPE_AUTO || d->pipeline > BZ_PIPE_CHUNKED) return BZ_ERR_ARG;
-    if (d->kernel < BZ_KERNEL_FAMILY || d->kernel > BZ_KERNEL_B8) return BZ_ERR_ARG;
+    if (dim == 3 && (d->kernel < BZ_KERNEL_FAMILY || d->kernel > BZ_KERNEL_B8)) return BZ_ERR_ARG;
     bz_plan *h = new (std::nothrow) bz_plan();
     if (!h) return BZ_ERR_OOM;
     bz::Plan &pl = h->p;
+    pl.dim = dim;
     pl.N = padded ? 2 * d->N : d->N; pl.Nin = padded ? d->N : 0; pl.L = d->L; pl.R = d->R; pl.gamma = d->gamma; pl.s = d->s;
     pl.N_rho = d->N_rho; pl.M = d->M; pl.kernel = d->kernel; pl.precision = d->precision;
     pl.eps = d->eps > 0 ? d->eps : M_PI / 1000.0;
@@ -134,9 +143,10 @@ bz_status create(bz_plan **out, const bz_plan_desc *d) {
     bz::build_theta_rules(pl);
 
     const int N = pl.N;
-    const size_t n3 = (size_t)N * N * N;
+    const size_t n3 = bz::modes(pl);          // N^3, or N^2 for a 2D plan
     const size_t field = n3 * sizeof(float2);
     int chunk = d->chunk_terms;
+    if (dim == 2) chunk = 1;                  // no chunked pipeline in 2D
     if (chunk <= 0) {
         // one wave of plane CTAs, within an L2-sized scratch
         if (bz::collide_set_attributes(N) != cudaSuccess) { delete h; return BZ_ERR_CUDA; }
@@ -164,7 +174,7 @@ bz_status create(bz_plan **out, const bz_plan_desc *d) {
     if (cudaMemcpy(pl.tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(pl.dev_err, 0, sizeof(int)) != cudaSuccess ||
         (pl.precision == BZ_PREC_BF16X3 && bz::mixed_upload(&pl.wimg) != BZ_OK) ||
-        bz::collide_set_attributes(N) != cudaSuccess) {
+        (dim == 3 && bz::collide_set_attributes(N) != cudaSuccess)) {
         free_plan(pl);
         delete h;
         return BZ_ERR_CUDA;
@@ -174,6 +184,20 @@ bz_status create(bz_plan **out, const bz_plan_desc *d) {
         free_plan(pl);
         delete h;
         return s;
+    }
+    if (dim == 2) {
+        // one CTA per term block over a persistent grid; FP64 stage inputs for the h pass
+        if (bz::setup_2d(pl) != cudaSuccess ||
+            (s = dmalloc(&pl.part, (size_t)pl.fused_G * field)) != BZ_OK ||
+            (s = dmalloc(&pl.fin64, n3 * sizeof(double2))) != BZ_OK) {
+            cudaGetLastError();
+            free_plan(pl);
+            delete h;
+            return s != BZ_OK ? s : BZ_ERR_CUDA;
+        }
+        pl.ws_bytes += (size_t)pl.fused_G * field + n3 * sizeof(double2);
+        *out = h;
+        return BZ_OK;
     }
     // pipeline: the fused cluster kernel where it applies (cluster size timed on this
     // device, fastest kept), else the chunked kernels
@@ -216,7 +240,7 @@ void bz_plan_destroy(bz_plan *plan) {
 bz_status bz_plan_info(const bz_plan *plan, int *P, size_t *alpha_bytes, size_t *workspace_bytes) {
     if (!plan) return BZ_ERR_ARG;
     const bz::Plan &p = plan->p;
-    size_t n3 = (size_t)p.N * p.N * p.N;
+    size_t n3 = bz::modes(p);
     if (P) *P = p.P;
     if (alpha_bytes) *alpha_bytes = (size_t)p.P * n3 * sizeof(float2);
     if (workspace_bytes) *workspace_bytes = p.ws_bytes;
@@ -226,9 +250,10 @@ bz_status bz_plan_info(const bz_plan *plan, int *P, size_t *alpha_bytes, size_t 
 bz_status bz_plan_pipeline(const bz_plan *plan, int *pipeline, int *cluster, int *clusters, float *tuned_ms) {
     if (!plan) return BZ_ERR_ARG;
     const bz::Plan &p = plan->p;
-    if (pipeline) *pipeline = p.use_fused ? BZ_PIPE_FUSED : BZ_PIPE_CHUNKED;
-    if (cluster) *cluster = p.use_fused ? p.fused_C : 0;
-    if (clusters) *clusters = p.use_fused ? p.fused_G : 0;
+    const bool fused = p.use_fused || p.dim == 2;       // the 2D kernel keeps a term's field on chip
+    if (pipeline) *pipeline = fused ? BZ_PIPE_FUSED : BZ_PIPE_CHUNKED;
+    if (cluster) *cluster = fused ? p.fused_C : 0;
+    if (clusters) *clusters = fused ? p.fused_G : 0;
     if (tuned_ms) *tuned_ms = p.use_fused ? p.fused_ms : 0.f;
     return BZ_OK;
 }
@@ -283,6 +308,7 @@ bz_status bz_step_rk(bz_plan *plan, void *fhat, int dtype, double *t, double dt,
 bz_status bz_moments(bz_plan *plan, const void *fhat, int dtype, double out[5], void *stream) {
     if (!plan || !fhat || !out) return BZ_ERR_ARG;
     if (dtype != BZ_C64 && dtype != BZ_C128) return BZ_ERR_ARG;
+    if (plan->p.dim == 2) return BZ_ERR_UNSUPPORTED;
     return bz::moments(plan->p, fhat, dtype, out, (cudaStream_t)stream);
 }
 
@@ -297,7 +323,7 @@ bz_status bz_plan_alpha(const bz_plan *plan, int p0, int p1, void *dst, void *st
     const bz::Plan &pl = plan->p;
     if (p0 < 0 || p1 < p0 || p1 > pl.P) return BZ_ERR_ARG;
     if (pl.Nin) return BZ_ERR_UNSUPPORTED;                    // the padded table lives on the 2N grid
-    size_t n3 = (size_t)pl.N * pl.N * pl.N;
+    size_t n3 = bz::modes(pl);
     if (cudaMemcpyAsync(dst, pl.alpha + (size_t)p0 * n3, (size_t)(p1 - p0) * n3 * sizeof(float2),
                         cudaMemcpyDeviceToDevice, (cudaStream_t)stream) != cudaSuccess)
         return BZ_ERR_CUDA;

@@ -288,7 +288,7 @@ static bz_status run_chunks(Plan &pl, int p0, int p1, cudaStream_t st, int *laun
 }
 
 bz_status load_input(Plan &pl, const void *fhat, int dtype, cudaStream_t st, int *launches) {
-    const int n3 = pl.N * pl.N * pl.N;
+    const int n3 = (int)modes(pl);
     if (dtype != BZ_C64 && dtype != BZ_C128) return BZ_ERR_ARG;
     if (pl.Nin) {
         // padded: embed into the 2N grid, in FP32 and (where the FP64 h pass reads it) FP64
@@ -315,6 +315,7 @@ bz_status load_input(Plan &pl, const void *fhat, int dtype, cudaStream_t st, int
 
 // Q over terms [p0, p1) of the FP32 input already in pl.fin; result in pl.acc (FP64).
 bz_status collide_core(Plan &pl, int p0, int p1, cudaStream_t st, int *launches) {
+    if (pl.dim == 2) return collide_2d(pl, p0, p1, st, launches);
     if (pl.use_fused) return collide_fused(pl, p0, p1, st, launches);
     switch (pl.N) {
         case 8: return run_chunks<8>(pl, p0, p1, st, launches);
@@ -335,7 +336,7 @@ bz_status collide_range(Plan &pl, int p0, int p1, const void *fhat, int in_dtype
 }
 
 bz_status write_output(Plan &pl, void *Qhat, int dtype, cudaStream_t st, int *launches) {
-    const int n3 = pl.N * pl.N * pl.N;
+    const int n3 = (int)modes(pl);
     if (pl.Nin) {
         if (dtype != BZ_C64 && dtype != BZ_C128) return BZ_ERR_ARG;
         const int m3 = pl.Nin * pl.Nin * pl.Nin;
@@ -444,7 +445,7 @@ extern "C" bz_status bz_collide_noalloc(const bz_plan *plan, const void *fhat, v
     if (!plan || !fhat || !Qhat || fhat == Qhat) return BZ_ERR_ARG;
     if (dtype != BZ_C64 && dtype != BZ_C128) return BZ_ERR_ARG;
     const Plan &pl = *plan_internal(plan);
-    if (pl.Nin) return BZ_ERR_UNSUPPORTED;                   // padded plans: bz_collide
+    if (pl.Nin || pl.dim == 2) return BZ_ERR_UNSUPPORTED;    // padded and 2D plans: bz_collide
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return BZ_ERR_CUDA;
     if (dev != pl.device) return BZ_ERR_ARG;

@@ -109,8 +109,52 @@ __global__ void ftable_kernel(TableArgs a) {
         a.alpha[(size_t)p * n3 + midx] = in_m ? make_float2((float)(sc * F.x), (float)(-sc * F.y)) : make_float2(0.f, 0.f);
 }
 
+// 2D (Sec. 4.1 (i)): with x = a k.qhat, y = a k.qperp the odd terms cancel between parts I and
+// III and part II folds onto [eps, pi], so
+//   F = 2 [ i x A1 - x^2 A2 / 2 - y^2 A3 / 2 ] + 2 sum_n W_n [ (exp(i x c_n) - 1) cos(y s_n) + (cos(y s_n) - 1) ]
+// with W_n = w_n b(t_n) (the circle's measure carries no sin t).
+__device__ __forceinline__ double2 f_value_2d(double x, double y, const double *A, int n,
+                                              const double *omc, const double *sn, const double *W) {
+    double sr = -0.5 * x * x * A[1] - 0.5 * y * y * A[2];
+    double si = x * A[0];
+    for (int q = 0; q < n; ++q) {
+        double sy, cy, sh, ch;
+        sincos(0.5 * y * sn[q], &sy, &cy);
+        const double cs = 1.0 - 2.0 * sy * sy;             // cos(y s), its deficit -2 sin^2(y s / 2)
+        sincos(0.5 * x * omc[q], &sh, &ch);
+        sr += W[q] * (-2.0 * sh * sh * cs - 2.0 * sy * sy);
+        si += W[q] * (2.0 * sh * ch * cs);
+    }
+    return make_double2(2.0 * sr, 2.0 * si);
+}
+
+// 2D table: one thread per (mode of the N x N grid, term); alpha = c_p F / N^2.
+__global__ void ftable2d_kernel(TableArgs a) {
+    extern __shared__ double sm[];
+    const int p = a.p0 + blockIdx.y;
+    const int i = p / a.M;
+    const int off = a.rule_off[i];
+    const int n = a.rule_off[i + 1] - off;
+    double *omc = sm, *sn = sm + n, *W = sm + 2 * n;
+    const double *src = a.rule + 3 * (size_t)off;
+    for (int t = threadIdx.x; t < 3 * n; t += blockDim.x) sm[t] = src[t];
+    __syncthreads();
+    const int N = a.N, n2 = N * N;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n2) return;
+    const int i1 = idx / N, i2 = idx % N;
+    const int k1 = i1 < N / 2 ? i1 : i1 - N;
+    const int k2 = i2 < N / 2 ? i2 : i2 - N;
+    const double *tp = a.term + 5 * (size_t)p;
+    const double aa = M_PI * tp[0] / (2.0 * a.L);
+    const double A[3] = {a.A0, a.A1, a.A2};
+    const double2 F = f_value_2d(aa * (k1 * tp[1] + k2 * tp[2]), aa * (-k1 * tp[2] + k2 * tp[1]), A, n, omc, sn, W);
+    const double sc = tp[4] * a.inv_n3;
+    a.alpha[(size_t)p * n2 + idx] = make_float2((float)(sc * F.x), (float)(sc * F.y));
+}
+
 struct EntryArgs {
-    int N, M, P, count;
+    int N, M, P, count, dim;
     double L;
     double A0, A1, A2;
     const double *term;
@@ -127,7 +171,7 @@ __global__ void fentries_kernel(EntryArgs a) {
     if (e >= a.count) return;
     const int N = a.N;
     int p = a.tsel[e];
-    int i1 = a.k_idx[3 * e], i2 = a.k_idx[3 * e + 1], i3 = a.k_idx[3 * e + 2];
+    int i1 = a.k_idx[3 * e], i2 = a.k_idx[3 * e + 1], i3 = a.dim == 2 ? 0 : a.k_idx[3 * e + 2];
     if (p < 0 || p >= a.P || i1 < 0 || i1 >= N || i2 < 0 || i2 >= N || i3 < 0 || i3 >= N) {
         a.out[2 * e] = nan("");          // out-of-range request: no table access
         a.out[2 * e + 1] = nan("");
@@ -141,13 +185,18 @@ __global__ void fentries_kernel(EntryArgs a) {
     int k2 = i2 < N / 2 ? i2 : i2 - N;
     int k3 = i3 < N / 2 ? i3 : i3 - N;
     const double *tp = a.term + 5 * (size_t)p;
-    double kap = k1 * tp[1] + k2 * tp[2] + k3 * tp[3];
-    double kk = (double)k1 * k1 + (double)k2 * k2 + (double)k3 * k3;
-    double kp2 = kk - kap * kap;
-    double kp = kp2 > 0.0 ? sqrt(kp2) : 0.0;
     double aa = M_PI * tp[0] / (2.0 * a.L);
     double A[3] = {a.A0, a.A1, a.A2};
-    double2 F = f_value(aa * kap, aa * kp, A, n, src, src + n, src + 2 * n);
+    double2 F;
+    if (a.dim == 2) {
+        F = f_value_2d(aa * (k1 * tp[1] + k2 * tp[2]), aa * (-k1 * tp[2] + k2 * tp[1]), A, n, src, src + n, src + 2 * n);
+    } else {
+        double kap = k1 * tp[1] + k2 * tp[2] + k3 * tp[3];
+        double kk = (double)k1 * k1 + (double)k2 * k2 + (double)k3 * k3;
+        double kp2 = kk - kap * kap;
+        double kp = kp2 > 0.0 ? sqrt(kp2) : 0.0;
+        F = f_value(aa * kap, aa * kp, A, n, src, src + n, src + 2 * n);
+    }
     a.out[2 * e] = F.x;
     a.out[2 * e + 1] = F.y;
 }
@@ -184,19 +233,22 @@ bz_status ftable_build(Plan &pl) {
 
     const size_t smem = 3 * (size_t)pl.rule_max * sizeof(double);
     if (smem > 200 * 1024) return BZ_ERR_UNSUPPORTED;
-    if (smem > 48 * 1024)
+    if (smem > 48 * 1024) {
         BZ_CUDA_TRY(cudaFuncSetAttribute(ftable_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        BZ_CUDA_TRY(cudaFuncSetAttribute(ftable2d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    }
     TableArgs a;
     a.N = N; a.M = pl.M; a.P = P; a.L = pl.L; a.nin = pl.Nin;
-    a.inv_n3 = 1.0 / ((double)N * N * N);
+    a.inv_n3 = 1.0 / (double)modes(pl);      // the forward transform's N^-d
     a.A0 = pl.A[0]; a.A1 = pl.A[1]; a.A2 = pl.A[2];
     a.term = pl.term_dev; a.rule = pl.rule_buf; a.rule_off = pl.rule_off; a.alpha = pl.alpha;
-    const int n3 = N * N * N, bs = 128;
+    const int n3 = (int)modes(pl), bs = 128;
     const int ychunk = 32768;   // gridDim.y limit
     for (int p0 = 0; p0 < P; p0 += ychunk) {
         a.p0 = p0;
         dim3 grid((n3 + bs - 1) / bs, (P - p0) < ychunk ? (P - p0) : ychunk);
-        ftable_kernel<<<grid, bs, smem>>>(a);
+        if (pl.dim == 2) ftable2d_kernel<<<grid, bs, smem>>>(a);
+        else ftable_kernel<<<grid, bs, smem>>>(a);
         BZ_CUDA_TRY(cudaGetLastError());
     }
     BZ_CUDA_TRY(cudaDeviceSynchronize());
@@ -207,7 +259,7 @@ bz_status ftable_entries(Plan &pl, int count, const int *k_idx, const int *term,
     if (count <= 0) return count == 0 ? BZ_OK : BZ_ERR_ARG;
     EntryArgs a;
     a.N = pl.Nin ? pl.Nin : pl.N;      // indices address the caller's grid
-    a.M = pl.M; a.P = pl.P; a.count = count; a.L = pl.L;
+    a.M = pl.M; a.P = pl.P; a.count = count; a.L = pl.L; a.dim = pl.dim;
     a.A0 = pl.A[0]; a.A1 = pl.A[1]; a.A2 = pl.A[2];
     a.term = pl.term_dev; a.rule = pl.rule_buf; a.rule_off = pl.rule_off;
     a.k_idx = k_idx; a.tsel = term; a.out = out;

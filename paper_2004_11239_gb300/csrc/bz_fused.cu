@@ -457,6 +457,11 @@ bz_status launch_fused(const Plan &pl, const ItemArgs &a, cudaStream_t st) {
     return BZ_ERR_UNSUPPORTED;
 }
 
+// acc[k] = sum over the nblk item partials of part (fixed order, compensated).
+void reduce_parts(const float2 *part, int nblk, int n, double2 *acc, cudaStream_t st) {
+    k_reduce_parts<<<(n + 31) / 32, 256, 0, st>>>(part, nblk, n, acc);
+}
+
 // One instance (pl.fin), terms [p0, p1): one block of terms per resident cluster, then the
 // fixed-order FP64 sum of the blocks into pl.acc.
 bz_status collide_fused(Plan &pl, int p0, int p1, cudaStream_t st, int *launches) {

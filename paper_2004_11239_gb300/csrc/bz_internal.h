@@ -37,6 +37,7 @@ struct Plan {
     // parameters
     int N = 0, N_rho = 0, M = 0, P = 0, kernel = 0, precision = 0, device = 0;
     int Nin = 0;                    // BZ_CONV_PADDED: the caller's modes per axis (N = 2 Nin); 0 = circular
+    int dim = 3;                    // 3: the 3D operator; 2: the 2D operator on an N x N grid
     double L = 0, R = 0, gamma = 0, s = 0, eps = 0;
     double A[3] = {0, 0, 0};        // part I kernel moments
     double kc = 0;                  // kernel constant (c_s, 1/(4 pi), 5/(192 pi))
@@ -74,6 +75,9 @@ struct Plan {
     int last_launches = 0;
     Timing tm;
 };
+
+// Fourier modes of one field: N^3 (3D) or N^2 (2D).
+inline size_t modes(const Plan &pl) { return (size_t)pl.N * pl.N * (pl.dim == 2 ? 1 : pl.N); }
 
 // Brackets one launch with events when timing is on (events are pre-created).
 inline void tm_begin(Plan &pl, cudaStream_t st) {
@@ -130,8 +134,13 @@ cudaError_t mixed_setup(int N, int *G);
 bz_status mixed_upload(uint4 **wimg);
 bz_status launch_mixed(const Plan &pl, const ItemArgs &a, cudaStream_t st);
 cudaError_t collide_set_attributes(int N);
+void reduce_parts(const float2 *part, int nblk, int n, double2 *acc, cudaStream_t st);
 int chunk_terms_for(int N);          // after collide_set_attributes(N)
 int supported_N(int N);
+
+// bz_2d.cu (dim = 2)
+cudaError_t setup_2d(Plan &pl);                       // persistent grid size (pl.fused_G)
+bz_status collide_2d(Plan &pl, int p0, int p1, cudaStream_t st, int *launches);
 
 // bz_rk.cu
 bz_status rk4_steps(Plan &pl, void *fhat, int dtype, double dt, int nsteps, cudaStream_t st,

@@ -99,7 +99,17 @@ static bool product_rule(int M, std::vector<double> &xyz, std::vector<double> &w
 bz_status build_terms(Plan &pl, const double *sphere_xyz, const double *sphere_w) {
     std::vector<double> r, wr, q, wq;
     gauss_legendre(pl.N_rho, 0.0, pl.R, r, wr);
-    if (sphere_xyz && sphere_w) {
+    if (pl.dim == 2) {
+        // midpoint rule on the circle (Sec. 5.2), stored as 3-vectors with a zero third component
+        if (sphere_xyz || sphere_w) return BZ_ERR_ARG;
+        for (int j = 0; j < pl.M; ++j) {
+            const double ph = 2.0 * M_PI * (j + 0.5) / pl.M;
+            q.push_back(std::cos(ph));
+            q.push_back(std::sin(ph));
+            q.push_back(0.0);
+            wq.push_back(2.0 * M_PI / pl.M);
+        }
+    } else if (sphere_xyz && sphere_w) {
         q.assign(sphere_xyz, sphere_xyz + 3 * pl.M);
         wq.assign(sphere_w, sphere_w + pl.M);
     } else if (pl.M == 12) {
@@ -118,17 +128,23 @@ bz_status build_terms(Plan &pl, const double *sphere_xyz, const double *sphere_w
             T.wr[p] = wr[i];
             T.wq[p] = wq[j];
             for (int d = 0; d < 3; ++d) T.q[3 * p + d] = q[3 * j + d];
-            T.c[p] = wr[i] * wq[j] * std::pow(r[i], pl.gamma) * r[i] * r[i];
+            // c_p = w_i w_j Phi(r_i) r_i^(d-1) (eq. approxG)
+            T.c[p] = wr[i] * wq[j] * std::pow(r[i], pl.gamma) * (pl.dim == 2 ? r[i] : r[i] * r[i]);
             T.radial_index[p] = i;
         }
     }
     return BZ_OK;
 }
 
-// g(t) = sin(t) b(cos t) for the plan's kernel.
+// The weight of the part-II theta integral: g(t) = sin(t) b(cos t) in 3D (the sphere's
+// measure), b(cos t) itself in 2D (eqs. b1-b4; the circle's measure is dt).
 static double kernel_g(const Plan &pl, double t) {
     double h = std::sin(0.5 * t);
     switch (pl.kernel) {
+        case BZ_KERNEL_B1: return pl.kc;
+        case BZ_KERNEL_B2: return pl.kc / h;
+        case BZ_KERNEL_B3: return pl.kc / (h * h);
+        case BZ_KERNEL_B4: return pl.kc * std::fabs(std::cos(0.5 * t)) * std::pow(h, -2.5);
         case BZ_KERNEL_FAMILY: return pl.kc * std::pow(h, -1.0 - 2.0 * pl.s);
         case BZ_KERNEL_B5: return pl.kc * std::sin(t);
         default: return pl.kc * std::cos(0.5 * t) * std::pow(h, -2.5);
@@ -154,7 +170,31 @@ static double int_sin_half_pow(double alpha, double eps) {
 bz_status build_kernel_constants(Plan &pl) {
     const double eps = pl.eps;
     const double W = std::sin(0.5 * eps);
+    if ((pl.dim == 2) != (pl.kernel >= BZ_KERNEL_B1 && pl.kernel <= BZ_KERNEL_B4)) return BZ_ERR_ARG;
     switch (pl.kernel) {
+        // 2D kernels b = c sin^beta(t/2): b (1 - cos) = 2 c sin^(beta+2)(t/2), b (1 - cos)^2 =
+        // 4 c sin^(beta+4)(t/2) over [0, eps] (parts I and III of Sec. 4.1 (i))
+        case BZ_KERNEL_B1:
+            pl.kc = 1.0 / (2.0 * M_PI);
+            pl.A[0] = 2.0 * pl.kc * int_sin_half_pow(2.0, eps);
+            pl.A[1] = 4.0 * pl.kc * int_sin_half_pow(4.0, eps);
+            break;
+        case BZ_KERNEL_B2:
+            pl.kc = 3.0 / 32.0;
+            pl.A[0] = 2.0 * pl.kc * int_sin_half_pow(1.0, eps);
+            pl.A[1] = 4.0 * pl.kc * int_sin_half_pow(3.0, eps);
+            break;
+        case BZ_KERNEL_B3:
+            pl.kc = 1.0 / (8.0 * M_PI);
+            pl.A[0] = 2.0 * pl.kc * eps;
+            pl.A[1] = 4.0 * pl.kc * int_sin_half_pow(2.0, eps);
+            break;
+        case BZ_KERNEL_B4:
+            pl.kc = 5.0 / 256.0;
+            // w = sin(t/2), cos(t/2) dt = 2 dw: A1 = 2 c int 2 w^(-1/2) dw, A2 = 4 c int 2 w^(3/2) dw
+            pl.A[0] = 8.0 * pl.kc * std::sqrt(W);
+            pl.A[1] = 3.2 * pl.kc * std::pow(W, 2.5);
+            break;
         case BZ_KERNEL_FAMILY: {
             if (!(pl.s >= 0.0 && pl.s < 1.0)) return BZ_ERR_ARG;
             // lambda = 2 pi c B(1 - s, 3/2) = 1/6
@@ -192,7 +232,7 @@ bz_status build_kernel_constants(Plan &pl) {
 void build_theta_rules(Plan &pl) {
     std::vector<double> gx, gw;
     gauss_legendre(16, -1.0, 1.0, gx, gw);
-    const double kmax = std::sqrt(3.0) * (pl.N / 2);
+    const double kmax = std::sqrt((double)pl.dim) * (pl.N / 2);
     std::vector<double> rr;
     std::vector<double> wr;
     gauss_legendre(pl.N_rho, 0.0, pl.R, rr, wr);

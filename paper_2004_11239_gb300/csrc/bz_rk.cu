@@ -93,7 +93,7 @@ __global__ void k_moments(const void *fhat, int dtype, int N, double L, double *
 
 bz_status rk4_steps(Plan &pl, void *fhat, int dtype, double dt, int nsteps, cudaStream_t st,
                     int *launches) {
-    const int n = pl.N * pl.N * pl.N;
+    const int n = (int)modes(pl);
     const int bs = 256, gs = (n + bs - 1) / bs;
     double2 *f0 = pl.rk, *fsum = pl.rk + n;
     k_rk_init<<<gs, bs, 0, st>>>(fhat, dtype, f0, pl.fin, pl.fin64, n);
