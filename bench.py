@@ -38,6 +38,9 @@ WORKLOADS = {
                   data="mixtures", desc="continuous-batching server: 64 requests, Poisson arrivals at 200/s, "
                   "N in {16,24,32}, N_rho=N, M in {12,32}, gamma in {0,-1,-2}, s in {0.25,0.5}, RK4 to "
                   "t=0.2 (dt=0.02, 10 steps), two-Maxwellian data; plans warmed before the trace; 32 terms per work item"),
+    "single_2d_n64": dict(N=64, N_rho=64, M=32, gamma=0.0, s=0.0, R=6.0, dt=None, data="bkw2d", dim=2,
+                          kernel=6, desc="single 2D collide in the Table 1 setting: N=64, N_rho=64, M=32 circle "
+                                         "points, kernel b4, R=6, L=(3+sqrt2)R/4, BKW samples at t=0"),
     "batch_4096": dict(N=None, N_rho=None, M=32, gamma=None, s=None, R=None, L=10.0, dt=0.01,
                        data="mixtures", desc="4096 instances (3072 at N=16, 1024 at N=32), N_rho=N, "
                        "M=32, gamma in {0,-1}, s in {0.25,0.5,0.75}, two-Maxwellian mixtures, "
@@ -64,13 +67,17 @@ def _fhat(w, L):
         return bi.bkw_fhat(N, L, bi.bkw_K(w["t0"]))
     if w["data"] == "c3":
         return bi.bigaussian_noise_c3(N, L)
+    if w["data"] == "bkw2d":
+        return bi.bkw2d_fhat_samples(N, L, bi.bkw2d_K(0.0))
     return bi.two_maxwellians_c1(N, L)
 
 
-def _flops_per_term(N):
-    """Algorithmic FP32 flops of one term: 2 3D FFTs (5 n log2 n, n = N^3), the twiddle,
-    product and weight multiplies (6 flops each per mode) and the accumulation (2)."""
-    n = N ** 3
+def _flops_per_term(N, dim=3):
+    """Algorithmic FP32 flops of one term: 2 d-dimensional FFTs (5 n log2 n, n = N^d), the
+    twiddle, product and weight multiplies (6 flops each per mode) and the accumulation (2)."""
+    n = N ** dim
+    if dim == 2:
+        return {"fused": 20 * n * math.log2(N) + 20 * n, "reduce": 2 * n}
     return {"plane_inv": 10 * n * math.log2(N) + 6 * n,
             "pencil": 10 * n * math.log2(N) + 6 * n,
             "plane_fwd": 10 * n * math.log2(N) + 6 * n,
@@ -78,11 +85,11 @@ def _flops_per_term(N):
             "fused": 30 * n * math.log2(N) + 20 * n}
 
 
-def _bytes_per_term(N):
+def _bytes_per_term(N, dim=3):
     """Algorithmic HBM bytes per term of each kernel (complex64 = 8 B per mode): the method
     must stream alpha_p once per term; fhat, h and the chunk scratch of the chunked pipeline
     are sized to stay in L2 and are not counted."""
-    n = N ** 3
+    n = N ** dim
     return {"plane_inv": 0, "pencil": 0, "reduce": 0,
             "plane_fwd": 8 * n,          # alpha_p
             "fused": 8 * n}              # alpha_p; the field stays on chip
@@ -214,6 +221,16 @@ def cpu_oracle_sample(w, L, R, n_terms=16, reps=1):
     from oracle import kernels, spectral
     N, P = w["N"], w["N_rho"] * w["M"]
     sel = np.linspace(0, P - 1, n_terms).astype(int)
+    if w.get("dim", 3) == 2:
+        from oracle import spectral2d
+        name = {3: "b1", 4: "b2", 5: "b3", 6: "b4"}[w["kernel"]]
+        plan = spectral2d.OraclePlan2D(N, L, R, w["gamma"], kernels.Kernel2D(name), w["N_rho"], w["M"])
+        f = _fhat(w, L)
+        t0 = time.perf_counter()
+        h = spectral2d.dft2(f, +1)
+        for p in sel:
+            _ = plan.alpha(p) * spectral2d.dft2(h * spectral2d.dft2(f * plan.beta(p), +1), -1) / N ** 2
+        return (time.perf_counter() - t0) * P / n_terms
     plan = spectral.OraclePlan(N, L, R, w["gamma"], kernels.Kernel("family", w["s"]), w["N_rho"],
                                w["M"], terms=sel)
     f = _fhat(w, L)
@@ -267,7 +284,9 @@ def run_ours(args, w):
 
     L, R = _geometry(w)
     N = w["N"]
-    plan = bz.bz_plan_create_ex(N, L, R, w["gamma"], w["s"], w["N_rho"], w["M"], h_precision=args.h_precision)
+    dim = w.get("dim", 3)
+    plan = bz.bz_plan_create_ex(N, L, R, w["gamma"], w["s"], w["N_rho"], w["M"], h_precision=args.h_precision,
+                                kernel=w.get("kernel", 0), dim=dim)
     pipe = bz.bz_plan_pipeline(plan)
     pipe["h_precision"] = {0: "fp64", 1: "fp64", 2: "fp32"}[args.h_precision]
     f_host = _fhat(w, L)
@@ -335,8 +354,8 @@ def run_ours(args, w):
     if dom == "reduce" and kern["fused"][0] > 0:
         terms_per_launch = 0.0            # the partial-sum reduction is not a per-term kernel
     avg_s = ms_k / 1e3 / max(n_launch, 1)
-    fl = _flops_per_term(N)[dom] * terms_per_launch
-    by = _bytes_per_term(N)[dom] * terms_per_launch
+    fl = _flops_per_term(N, dim).get(dom, 0.0) * terms_per_launch
+    by = _bytes_per_term(N, dim).get(dom, 0.0) * terms_per_launch
     clocks = clk.summary()
     sm_clock = peaks.get("sm_max_mhz", 2070.0)
     alu_peak = 152 * 128 * 2 * sm_clock * 1e6 / 1e12      # FP32 FMA lanes x 2 flops x clock
@@ -351,7 +370,7 @@ def run_ours(args, w):
                  "avg_launch_us": avg_s * 1e6, "also": {k: other[k] for k in ("bound", "achieved", "peak", "unit", "frac")}})
 
     mixed = None
-    if N == 32 and not args.no_mixed:
+    if N == 32 and dim == 3 and not args.no_mixed:
         mixed = _measure_mixed(args, w, bz, plan, f_host, L, R, st, peaks, src, barrier)
 
     cpu = None

@@ -8,7 +8,8 @@
 // A column pass writes and reads only its own column of S, so the next term's first pass
 // needs no barrier.  Work items are (term block) per CTA, persistent over a grid of resident
 // CTAs; each item's FP32 sum goes to its partial, summed over blocks in a fixed order by
-// k_reduce_parts.  h = IFFT(fhat) is formed beforehand in FP64 (k_h64_2d) and stored FP32.
+// k_reduce_parts.  h = IFFT(fhat) is formed beforehand in FP64 (k_h64_2d, or the four-step
+// k_h64_2d_64 at N = 64) and stored FP32.
 #include "bz_fft.cuh"
 #include "bz_internal.h"
 
@@ -28,7 +29,7 @@ __device__ __forceinline__ double2 load_c2(const void *f, int dtype, size_t i) {
     return make_double2(v.x, v.y);
 }
 
-// h = IFFT(fhat) in FP64: one CTA, thread c transforms column c, then row c.
+// h = IFFT(fhat) in FP64 for N <= 32: one CTA, thread c transforms column c, then row c.
 template <int N>
 __global__ void __launch_bounds__(N) k_h64_2d(const void *__restrict__ f, int dtype, float2 *__restrict__ h) {
     extern __shared__ double2 sd[];
@@ -46,6 +47,41 @@ __global__ void __launch_bounds__(N) k_h64_2d(const void *__restrict__ f, int dt
     fft_inplace<N, +1>(x);
     #pragma unroll
     for (int j = 0; j < N; ++j) h[(size_t)c * N + j] = make_float2((float)x[j].x, (float)x[j].y);
+}
+
+// N = 64: an FP64 line transform of length 64 = 8 x 8 by the 8 threads of one CTA (four-step
+// Cooley-Tukey): thread t holds x[t + 8 m], transforms over m, multiplies by exp(+2 pi i t k2 / 64)
+// and, after a transpose through shared memory, thread k2 transforms over t, ending with
+// X[k2 + 8 k1].  FP64 rate per SM is low on this GPU, so each line gets its own CTA (64 per
+// pass).  AXIS 0: column c of f -> scr (FP64); AXIS 1: row r of scr -> h (FP32).
+template <int AXIS>
+__global__ void __launch_bounds__(8) k_h64_2d_64(const void *__restrict__ f, int dtype, double2 *__restrict__ scr,
+                                                float2 *__restrict__ h) {
+    constexpr int N = 64;
+    __shared__ double2 tr[8][9];
+    const int line = blockIdx.x, t = threadIdx.x;
+    double2 y[8];
+    #pragma unroll
+    for (int m = 0; m < 8; ++m) {
+        const int n = t + 8 * m;
+        y[m] = AXIS == 0 ? load_c2(f, dtype, (size_t)n * N + line) : scr[(size_t)line * N + n];
+    }
+    fft_inplace<8, +1>(y);                                   // over m -> k2
+    #pragma unroll
+    for (int k2 = 0; k2 < 8; ++k2) {
+        mul_tw<64, +1>(y[k2], t * k2);                       // exp(+2 pi i t k2 / 64)
+        tr[k2][t] = y[k2];
+    }
+    __syncthreads();
+    #pragma unroll
+    for (int u = 0; u < 8; ++u) y[u] = tr[t][u];              // thread k2 = t gathers over t' = u
+    fft_inplace<8, +1>(y);                                   // over t' -> k1; index k = t + 8 k1
+    #pragma unroll
+    for (int k1 = 0; k1 < 8; ++k1) {
+        const int k = t + 8 * k1;
+        if (AXIS == 0) scr[(size_t)k * N + line] = y[k1];
+        else h[(size_t)line * N + k] = make_float2((float)y[k1].x, (float)y[k1].y);
+    }
 }
 
 template <int N>
@@ -100,8 +136,10 @@ k_collide_2d(const float2 *__restrict__ fin, const float2 *__restrict__ h, const
 
 template <int N> cudaError_t setup_n(Plan &pl) {
     cudaError_t e = cudaFuncSetAttribute(k_collide_2d<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)D2<N>::SMEM);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_h64_2d<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)D2<N>::SMEM64);
+    if constexpr (N < 64) {
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_h64_2d<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)D2<N>::SMEM64);
+    }
     if (e != cudaSuccess) return e;
     int per_sm = 0, dev = 0, sms = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_collide_2d<N>, N, D2<N>::SMEM);
@@ -118,9 +156,15 @@ template <int N> bz_status run_n(Plan &pl, int p0, int p1, cudaStream_t st, int 
     const int nt = p1 - p0;
     const int TB = nt > 0 ? (nt + pl.fused_G - 1) / pl.fused_G : 1;
     const int nblk = nt > 0 ? (nt + TB - 1) / TB : 0;
+    const void *src = pl.src ? pl.src : (const void *)pl.fin;
+    const int sdt = pl.src ? pl.src_dtype : BZ_C64;
     tm_begin(pl, st);
-    k_h64_2d<N><<<1, N, D2<N>::SMEM64, st>>>(pl.src ? pl.src : (const void *)pl.fin,
-                                              pl.src ? pl.src_dtype : BZ_C64, pl.h);
+    if constexpr (N == 64) {
+        k_h64_2d_64<0><<<N, 8, 0, st>>>(src, sdt, pl.scr64, nullptr);
+        k_h64_2d_64<1><<<N, 8, 0, st>>>(nullptr, BZ_C128, pl.scr64, pl.h);
+    } else {
+        k_h64_2d<N><<<1, N, D2<N>::SMEM64, st>>>(src, sdt, pl.h);
+    }
     tm_end(pl, st, TK_OTHER);
     tm_begin(pl, st);
     if (nblk > 0)
@@ -131,7 +175,7 @@ template <int N> bz_status run_n(Plan &pl, int p0, int p1, cudaStream_t st, int 
     reduce_parts(pl.part, nblk, n2, pl.acc, st);
     tm_end(pl, st, TK_REDUCE);
     BZ_CUDA_TRY(cudaGetLastError());
-    if (launches) *launches += nblk > 0 ? 3 : 2;
+    if (launches) *launches += (nblk > 0 ? 3 : 2) + (N == 64 ? 1 : 0);
     return BZ_OK;
 }
 

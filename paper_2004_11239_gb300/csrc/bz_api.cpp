@@ -189,13 +189,14 @@ bz_status create(bz_plan **out, const bz_plan_desc *d) {
         // one CTA per term block over a persistent grid; FP64 stage inputs for the h pass
         if (bz::setup_2d(pl) != cudaSuccess ||
             (s = dmalloc(&pl.part, (size_t)pl.fused_G * field)) != BZ_OK ||
-            (s = dmalloc(&pl.fin64, n3 * sizeof(double2))) != BZ_OK) {
+            (s = dmalloc(&pl.fin64, n3 * sizeof(double2))) != BZ_OK ||
+            (s = dmalloc(&pl.scr64, n3 * sizeof(double2))) != BZ_OK) {
             cudaGetLastError();
             free_plan(pl);
             delete h;
             return s != BZ_OK ? s : BZ_ERR_CUDA;
         }
-        pl.ws_bytes += (size_t)pl.fused_G * field + n3 * sizeof(double2);
+        pl.ws_bytes += (size_t)pl.fused_G * field + 2 * n3 * sizeof(double2);
         *out = h;
         return BZ_OK;
     }
