@@ -153,6 +153,51 @@ def grid(N: int, L: float) -> np.ndarray:
     return -L + 2.0 * L * np.arange(N) / N
 
 
+def _samples_to_fhat(fv: np.ndarray, L: float) -> np.ndarray:
+    """fhat_k = N^-d sum_j f(v_j) exp(-i pi k.v_j / L), nodes v_j = -L + 2L j/N, any d (library FFT)."""
+    N, d = fv.shape[0], fv.ndim
+    sign = np.where(signed_modes(N) % 2 == 0, 1.0, -1.0)
+    s = sign
+    for _ in range(d - 1):
+        s = np.multiply.outer(s, sign)
+    return np.fft.fftn(fv) / N ** d * s
+
+
+def delta_w(x, w: float) -> np.ndarray:
+    """Approximate delta (Sec. 5.3, eq. delta): (1 + cos(pi x / w)) / (2w) for |x| <= w, else 0."""
+    x = np.asarray(x, dtype=np.float64)
+    return np.where(np.abs(x) <= w, (1.0 + np.cos(np.pi * x / w)) / (2.0 * w), 0.0)
+
+
+def _speed(N: int, L: float, d: int) -> np.ndarray:
+    v = grid(N, L)
+    V = np.meshgrid(*([v] * d), indexing="ij")
+    return np.sqrt(sum(x * x for x in V))
+
+
+def measure_valued_fhat(N: int, L: float, d: int, rings=((0.0, 1.0 / 3.0), (0.2, 1.0 / 3.0))) -> np.ndarray:
+    """Coefficients of f0(v) = sum_r c_r delta_w(|v| - rho_r) on the d-dimensional grid, with
+    w = 0.5 sqrt(dv), dv = 2L/N (Sec. 5.3, eq. initialdelta; eq. initialdelta1 is rings =
+    ((0.2, 0.5),)), from the grid samples."""
+    w = 0.5 * math.sqrt(2.0 * L / N)
+    sp = _speed(N, L, d)
+    fv = sum(c * delta_w(sp - rho, w) for rho, c in rings)
+    return _samples_to_fhat(fv, L)
+
+
+def discontinuous2d_fhat(N: int, L: float) -> np.ndarray:
+    """Coefficients of the 2D discontinuous data of Sec. 5.5 (eq. disinitial): rho_1 / (2 pi T_1)
+    exp(-|v|^2 / 2 T_1) for v_1 > 0 and rho_2 / (2 pi T_2) exp(-|v|^2 / 2 T_2) for v_1 < 0, with
+    rho = (6/5, 4/5), T = (2/3, 3/2); v_1 = 0 takes the mean.  From the grid samples."""
+    v = grid(N, L)
+    V1, V2 = np.meshgrid(v, v, indexing="ij")
+    v2 = V1 ** 2 + V2 ** 2
+    g1 = 1.2 / (2 * math.pi * (2.0 / 3.0)) * np.exp(-v2 / (2 * (2.0 / 3.0)))
+    g2 = 0.8 / (2 * math.pi * 1.5) * np.exp(-v2 / (2 * 1.5))
+    fv = np.where(V1 > 0, g1, np.where(V1 < 0, g2, 0.5 * (g1 + g2)))
+    return _samples_to_fhat(fv, L)
+
+
 # ---------------------------------------------------------------------------
 # Workload recipes (seeded).  Each returns complex128 [N, N, N].
 # ---------------------------------------------------------------------------

@@ -35,6 +35,7 @@ static double kernel_g(double t, int kid, double s, double c) {
     double h = sin(0.5 * t);
     if (kid == 0) return c * pow(h, -1.0 - 2.0 * s);        /* family: c sin^(-1-2s)(t/2) */
     if (kid == 1) return c * sin(t);                         /* b5: sin(t) / (4 pi)        */
+    if (kid == 7) return fabs(log(2.0 * h)) / (2.0 * h);     /* Debye-Yukawa (eq. ApproximatedDebye) */
     return c * cos(0.5 * t) * pow(h, -2.5);                  /* b8                          */
 }
 
@@ -74,16 +75,25 @@ static int part2_rule(double eps, double zmax, int npts, const double *glx, cons
         }
         lo = hi;
     }
-    int npan = (int)ceil((M_PI - tg) / width);
-    double dw = (M_PI - tg) / npan;
-    for (int pn = 0; pn < npan; ++pn) {
-        double a = tg + pn * dw, b = tg + (pn + 1) * dw;
-        for (int q = 0; q < npts && n < cap; ++q) {
-            double t = 0.5 * (b - a) * glx[q] + 0.5 * (b + a);
-            th[n] = t;
-            wg[n] = 0.5 * (b - a) * glw[q] * kernel_g(t, kid, s, c);
-            n++;
+    /* equal panels from max(lower bound, tg) to pi; the Debye-Yukawa kernel's |log(2 sin(t/2))|
+     * has a kink at pi/3, which gets a panel edge */
+    double stops[2];
+    int nst = 0;
+    if (kid == 7 && lo < M_PI / 3.0) stops[nst++] = M_PI / 3.0;
+    stops[nst++] = M_PI;
+    for (int si = 0; si < nst; ++si) {
+        int npan = (int)ceil((stops[si] - lo) / width);
+        double dw = (stops[si] - lo) / npan;
+        for (int pn = 0; pn < npan; ++pn) {
+            double a = lo + pn * dw, b = lo + (pn + 1) * dw;
+            for (int q = 0; q < npts && n < cap; ++q) {
+                double t = 0.5 * (b - a) * glx[q] + 0.5 * (b + a);
+                th[n] = t;
+                wg[n] = 0.5 * (b - a) * glw[q] * kernel_g(t, kid, s, c);
+                n++;
+            }
         }
+        lo = stops[si];
     }
     if (n >= cap) return -1;   /* rule does not fit: report instead of truncating */
     for (int q = 0; q < n; ++q) {

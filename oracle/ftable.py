@@ -84,7 +84,8 @@ def ftable(N: int, L: float, r, qhat, kernel: Kernel, eps: float = EPS_DEFAULT,
     gx = np.ascontiguousarray(gx)
     gw = np.ascontiguousarray(gw)
     out = np.empty((P, N, N, N), dtype=np.complex128)
-    rc = lib.oracle_ftable(N, L, P, _dp(r), _dp(qhat), kernel.kid, kernel.s, kernel.c, eps,
+    lo = kernel.theta0 if kernel.theta0 > 0 else eps     # lower end of part II
+    rc = lib.oracle_ftable(N, L, P, _dp(r), _dp(qhat), kernel.kid, kernel.s, kernel.c, lo,
                            _dp(A), npts, _dp(gx), _dp(gw), _dp(out.view(np.float64)))
     if rc != 0:
         raise MemoryError("oracle_ftable failed")
@@ -103,8 +104,9 @@ def fentries(N: int, L: float, k, r, qhat, kernel: Kernel, eps: float = EPS_DEFA
     gx = np.ascontiguousarray(gx)
     gw = np.ascontiguousarray(gw)
     out = np.empty(len(r), dtype=np.complex128)
+    lo = kernel.theta0 if kernel.theta0 > 0 else eps
     rc = lib.oracle_fentries(len(r), k.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(r),
-                             _dp(qhat), L, N, kernel.kid, kernel.s, kernel.c, eps, _dp(A), npts,
+                             _dp(qhat), L, N, kernel.kid, kernel.s, kernel.c, lo, _dp(A), npts,
                              _dp(gx), _dp(gw), _dp(out.view(np.float64)))
     if rc != 0:
         raise MemoryError("oracle_fentries failed")
@@ -124,7 +126,8 @@ def ftable2d(N: int, L: float, r, qhat, kernel, eps: float = EPS_DEFAULT,
     gx = np.ascontiguousarray(gx)
     gw = np.ascontiguousarray(gw)
     out = np.empty((P, N, N), dtype=np.complex128)
-    rc = lib.oracle_ftable2d(N, L, P, _dp(r), _dp(qhat), kernel.kid, kernel.c, eps, _dp(A), npts,
+    lo = kernel.theta0 if kernel.theta0 > 0 else eps
+    rc = lib.oracle_ftable2d(N, L, P, _dp(r), _dp(qhat), kernel.kid, kernel.c, lo, _dp(A), npts,
                              _dp(gx), _dp(gw), _dp(out.view(np.float64)))
     if rc != 0:
         raise MemoryError("oracle_ftable2d failed")
@@ -151,6 +154,17 @@ def funk_hecke_eigen(kernel: Kernel, lmax: int) -> np.ndarray:
     """lambda_l - lambda_0 = 2 pi int_0^pi g(t) (P_l(cos t) - 1) dt for l = 0..lmax."""
     from scipy import integrate, special
     out = np.zeros(lmax + 1)
+    if kernel.theta0 > 0 or kernel.name == "debye":
+        # no algebraic end singularity to weight: g (P_l - 1) is bounded (~ t |log t| for the
+        # Debye-Yukawa kernel) or zero near 0; plain adaptive quadrature with the pi/3 kink as a
+        # break point
+        lo = kernel.theta0
+        pts = [p for p in (math.pi / 3.0,) if lo < p]
+        for l in range(1, lmax + 1):
+            fl = lambda t, l=l: float(kernel.g(max(t, 1e-300))) * (special.eval_legendre(l, math.cos(t)) - 1.0)
+            out[l] = 2.0 * math.pi * integrate.quad(fl, lo, math.pi, points=pts or None, epsabs=1e-15,
+                                                   epsrel=1e-13, limit=4000)[0]
+        return out
     alpha = {"family": 1.0 - 2.0 * kernel.s, "b5": 1.0, "b8": -0.5}[kernel.name]
     for l in range(1, lmax + 1):
         ts = min(0.63 / l, 0.5)

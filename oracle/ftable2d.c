@@ -65,10 +65,11 @@ static int part2_rule_2d(double eps, double zmax, int npts, const double *glx, c
         if (n < 0) return -1;
         lo = hi;
     }
-    int npan = (int)ceil((M_PI - tg) / width);
-    double dw = (M_PI - tg) / npan;
+    /* equal panels from max(lower bound, 0.5) to pi (the lower bound is eps, or the cutoff angle) */
+    int npan = (int)ceil((M_PI - lo) / width);
+    double dw = (M_PI - lo) / npan;
     for (int pn = 0; pn < npan && n >= 0; ++pn)
-        n = add_panel(tg + pn * dw, tg + (pn + 1) * dw, npts, glx, glw, kid, c, wg, cth, sth, n, cap);
+        n = add_panel(lo + pn * dw, lo + (pn + 1) * dw, npts, glx, glw, kid, c, wg, cth, sth, n, cap);
     return n;
 }
 

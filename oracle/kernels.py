@@ -9,6 +9,10 @@ All kernels are described by g(theta) = sin(theta) b(cos theta) on (0, pi].
   s = 1/2 its b7 (eqs. b6, b7).
 * ``b5``: the cutoff kernel b = 1/(4 pi) (eq. b5).
 * ``b8``: b = 5 cos(theta/2) / (192 pi sin(theta) sin^(5/2)(theta/2)) (eq. b8).
+* ``debye``: g = |log(2 sin(theta/2))| / (2 sin(theta/2)), the angular part of the
+  Debye-Yukawa kernel (Sec. 5.4, eq. ApproximatedDebye; its |v - v*| factor is Phi = |q|).
+* ``theta0 > 0``: the kernel set to zero for theta < theta0 (eqs. ApproximatedDebyecutoff,
+  b3cutoff); there is then no Taylor part and part II starts at theta0.
 
 Part I of the split of Sec. 4.1 needs three moments over [0, eps]:
 A1 = int g (1 - cos), A2 = int g (1 - cos)^2, A3 = int g sin^2.
@@ -26,8 +30,9 @@ def beta_fn(a: float, b: float) -> float:
 
 @dataclass(frozen=True)
 class Kernel:
-    name: str          # "family", "b5", "b8"
+    name: str          # "family", "b5", "b8", "debye"
     s: float = 0.0     # family parameter (nu = 2 s)
+    theta0: float = 0.0   # angular cutoff (0: none)
 
     @property
     def c(self) -> float:
@@ -37,11 +42,13 @@ class Kernel:
             return 1.0 / (4.0 * math.pi)
         if self.name == "b8":
             return 5.0 / (192.0 * math.pi)
+        if self.name == "debye":
+            return 1.0
         raise ValueError(self.name)
 
     @property
     def kid(self) -> int:
-        return {"family": 0, "b5": 1, "b8": 2}[self.name]
+        return {"family": 0, "b5": 1, "b8": 2, "debye": 7}[self.name]
 
     def g(self, theta):
         """sin(theta) * b(cos theta)."""
@@ -52,11 +59,31 @@ class Kernel:
             return self.c * h ** (-1.0 - 2.0 * self.s)
         if self.name == "b5":
             return self.c * np.sin(th)
+        if self.name == "debye":
+            return np.abs(np.log(2.0 * h)) / (2.0 * h)
         return self.c * np.cos(0.5 * th) * h ** (-2.5)
 
     def taylor_moments(self, eps: float):
         """(A1, A2, A3) over [0, eps] (Sec. 4.1, part I after Taylor expansion)."""
+        if self.theta0 > 0.0:
+            return 0.0, 0.0, 0.0
         W = math.sin(0.5 * eps)
+        if self.name == "debye":
+            # g (1 - cos) = h |log 2h|, g (1 - cos)^2 = 2 h^3 |log 2h| with h = sin(t/2): no closed
+            # form; adaptive quadrature with the logarithmic end weight (library routine)
+            # (library routine).  On [0, eps], |log 2h| = -log t - log(2h / t): the first part with
+            # QUADPACK's log end weight, the second (smooth, ~ t^2/24) by 16-point Gauss-Legendre.
+            import numpy as np
+            from scipy.integrate import quad
+            from .quadrature import gauss_legendre
+            x, w = gauss_legendre(16, 0.0, eps)
+            hx = np.sin(0.5 * x)
+            corr = -np.log(2.0 * hx / x)
+            A1 = -quad(lambda t: math.sin(0.5 * t), 0.0, eps, weight="alg-loga", wvar=(0.0, 0.0))[0] \
+                + float(np.sum(w * hx * corr))
+            A2 = -quad(lambda t: 2.0 * math.sin(0.5 * t) ** 3, 0.0, eps, weight="alg-loga", wvar=(0.0, 0.0))[0] \
+                + float(np.sum(w * 2.0 * hx ** 3 * corr))
+            return A1, A2, 2.0 * A1 - A2
         if self.name == "family":
             def int_sin_pow(alpha):
                 # int_0^eps sin^alpha(theta/2) dtheta = 2 int_0^asin(W) sin^alpha u du
@@ -127,6 +154,7 @@ def _int_sin_pow(alpha: float, W: float) -> float:
 @dataclass(frozen=True)
 class Kernel2D:
     name: str          # "b1", "b2", "b3", "b4"
+    theta0: float = 0.0   # angular cutoff (0: none), eq. b3cutoff
 
     @property
     def kid(self) -> int:
@@ -146,6 +174,8 @@ class Kernel2D:
 
     def taylor_moments(self, eps: float):
         """(A1, A2, A3) = int_0^eps b (1-cos, (1-cos)^2, sin^2) d theta (parts I and III)."""
+        if self.theta0 > 0.0:
+            return 0.0, 0.0, 0.0
         _, c, beta, has_cos = _B2D[self.name]
         W = math.sin(0.5 * eps)
         if has_cos:
