@@ -56,6 +56,12 @@ enum { BZ_C64 = 0, BZ_C128 = 1 };
  *   BZ_KERNEL_B8:     b = 5 cos(theta/2) / (192 pi sin(theta) sin^(5/2)(theta/2)), eq. b8. */
 enum { BZ_KERNEL_FAMILY = 0, BZ_KERNEL_B5 = 1, BZ_KERNEL_B8 = 2 };
 
+/* BZ_KERNEL_DEBYE (3D, Sec. 5.4, eq. ApproximatedDebye): sin(theta) b = |log(2 sin(theta/2))| /
+ * (2 sin(theta/2)), the angular part of the Debye-Yukawa kernel; its |v - v*| factor is
+ * Phi(|q|) = |q|, i.e. gamma = 1.  Its part-I moments have no closed form and are computed by
+ * Gauss-Legendre quadrature after t = eps u^2. */
+enum { BZ_KERNEL_DEBYE = 7 };
+
 /* 2D angular kernels (dim = 2; Sec. 5.2, eqs. b1-b4), b(cos theta) on theta in [0, 2 pi] with
  * the measure d theta on the circle, all with lambda = 1/8 (eq. KK2):
  *   BZ_KERNEL_B1: 1 / (2 pi) (cutoff);          BZ_KERNEL_B2: 3 / (32 sin(theta/2));
@@ -125,6 +131,9 @@ typedef struct {
                          r_i^gamma r_i; FP32, circular).  A 2D plan runs bz_collide, bz_collide_terms,
                          bz_step_rk, bz_ftable_entries (k_idx's third index ignored) and the
                          inspection calls; the others return BZ_ERR_UNSUPPORTED.                */
+    double theta0;    /* angular cutoff: b = 0 for theta < theta0 (and theta > 2 pi - theta0 in 2D), as
+                         eqs. ApproximatedDebyecutoff and b3cutoff; 0 = none, else eps <= theta0 < pi.
+                         With a cutoff there is no Taylor part; the theta rule starts at theta0. */
 } bz_plan_desc;
 
 /* Creates a plan: quadrature terms, the FP64 F table (computed on the device, stored

@@ -32,6 +32,7 @@ _LIB_PATH = os.path.join(_HERE, "_lib", "libbz.so")
 BZ_C64, BZ_C128 = 0, 1
 BZ_KERNEL_FAMILY, BZ_KERNEL_B5, BZ_KERNEL_B8 = 0, 1, 2
 BZ_KERNEL_B1, BZ_KERNEL_B2, BZ_KERNEL_B3, BZ_KERNEL_B4 = 3, 4, 5, 6   # 2D kernels (dim = 2)
+BZ_KERNEL_DEBYE = 7                                                     # 3D Debye-Yukawa (use gamma = 1)
 BZ_PREC_FP32, BZ_PREC_BF16X3 = 0, 1
 BZ_PIPE_AUTO, BZ_PIPE_FUSED, BZ_PIPE_CHUNKED = 0, 1, 2
 BZ_H_AUTO, BZ_H_FP64, BZ_H_FP32 = 0, 1, 2
@@ -66,7 +67,7 @@ class bz_plan_desc(ctypes.Structure):
                 ("eps", ctypes.c_double), ("sphere_xyz", ctypes.POINTER(ctypes.c_double)),
                 ("sphere_w", ctypes.POINTER(ctypes.c_double)), ("chunk_terms", ctypes.c_int),
                 ("pipeline", ctypes.c_int), ("cluster", ctypes.c_int), ("h_precision", ctypes.c_int),
-                ("conv", ctypes.c_int), ("dim", ctypes.c_int)]
+                ("conv", ctypes.c_int), ("dim", ctypes.c_int), ("theta0", ctypes.c_double)]
 
 
 def library_path() -> str:
@@ -202,7 +203,7 @@ def bz_plan_create_ex(N: int, L: float, R: float, gamma: float, s: float, N_rho:
                       kernel: int = BZ_KERNEL_FAMILY, eps: float = 0.0, sphere=None,
                       chunk_terms: int = 0, pipeline: int = BZ_PIPE_AUTO, cluster: int = 0,
                       h_precision: int = BZ_H_AUTO, precision: int = BZ_PREC_FP32,
-                      conv: int = BZ_CONV_CIRCULAR, dim: int = 3) -> Plan:
+                      conv: int = BZ_CONV_CIRCULAR, dim: int = 3, theta0: float = 0.0) -> Plan:
     d = bz_plan_desc()
     d.N, d.L, d.R, d.gamma, d.s, d.N_rho, d.M = N, L, R, gamma, s, N_rho, M
     d.kernel, d.precision, d.eps, d.chunk_terms = kernel, precision, eps, chunk_terms
@@ -211,6 +212,7 @@ def bz_plan_create_ex(N: int, L: float, R: float, gamma: float, s: float, N_rho:
     d.h_precision = h_precision
     d.conv = conv
     d.dim = dim
+    d.theta0 = theta0
     keep = []
     if sphere is not None:
         import numpy as np

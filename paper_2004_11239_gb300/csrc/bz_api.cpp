@@ -126,7 +126,8 @@ bz_status create(bz_plan **out, const bz_plan_desc *d) {
     if (d->precision == BZ_PREC_BF16X3 && (d->N != 32 || d->pipeline == BZ_PIPE_CHUNKED))
         return BZ_ERR_UNSUPPORTED;
     if (d->pipeline < BZ_PIPE_AUTO || d->pipeline > BZ_PIPE_CHUNKED) return BZ_ERR_ARG;
-    if (dim == 3 && (d->kernel < BZ_KERNEL_FAMILY || d->kernel > BZ_KERNEL_B8)) return BZ_ERR_ARG;
+    if (dim == 3 && !((d->kernel >= BZ_KERNEL_FAMILY && d->kernel <= BZ_KERNEL_B8) || d->kernel == BZ_KERNEL_DEBYE))
+        return BZ_ERR_ARG;
     bz_plan *h = new (std::nothrow) bz_plan();
     if (!h) return BZ_ERR_OOM;
     bz::Plan &pl = h->p;
@@ -134,6 +135,8 @@ bz_status create(bz_plan **out, const bz_plan_desc *d) {
     pl.N = padded ? 2 * d->N : d->N; pl.Nin = padded ? d->N : 0; pl.L = d->L; pl.R = d->R; pl.gamma = d->gamma; pl.s = d->s;
     pl.N_rho = d->N_rho; pl.M = d->M; pl.kernel = d->kernel; pl.precision = d->precision;
     pl.eps = d->eps > 0 ? d->eps : M_PI / 1000.0;
+    if (!(d->theta0 == 0.0 || (d->theta0 >= pl.eps && d->theta0 < M_PI))) { delete h; return BZ_ERR_ARG; }
+    pl.theta0 = d->theta0;
     if (d->h_precision < BZ_H_AUTO || d->h_precision > BZ_H_FP32) { delete h; return BZ_ERR_ARG; }
     pl.h_fp64 = d->h_precision != BZ_H_FP32 || d->precision == BZ_PREC_BF16X3;   // BF16X3 reads h formed in FP64
     cudaGetDevice(&pl.device);

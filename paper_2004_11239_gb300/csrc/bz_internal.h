@@ -39,6 +39,7 @@ struct Plan {
     int Nin = 0;                    // BZ_CONV_PADDED: the caller's modes per axis (N = 2 Nin); 0 = circular
     int dim = 3;                    // 3: the 3D operator; 2: the 2D operator on an N x N grid
     double L = 0, R = 0, gamma = 0, s = 0, eps = 0;
+    double theta0 = 0;              // angular cutoff (0: none)
     double A[3] = {0, 0, 0};        // part I kernel moments
     double kc = 0;                  // kernel constant (c_s, 1/(4 pi), 5/(192 pi))
     HostTerms terms;

@@ -145,6 +145,7 @@ static double kernel_g(const Plan &pl, double t) {
         case BZ_KERNEL_B2: return pl.kc / h;
         case BZ_KERNEL_B3: return pl.kc / (h * h);
         case BZ_KERNEL_B4: return pl.kc * std::fabs(std::cos(0.5 * t)) * std::pow(h, -2.5);
+        case BZ_KERNEL_DEBYE: return std::fabs(std::log(2.0 * h)) / (2.0 * h);
         case BZ_KERNEL_FAMILY: return pl.kc * std::pow(h, -1.0 - 2.0 * pl.s);
         case BZ_KERNEL_B5: return pl.kc * std::sin(t);
         default: return pl.kc * std::cos(0.5 * t) * std::pow(h, -2.5);
@@ -172,6 +173,23 @@ bz_status build_kernel_constants(Plan &pl) {
     const double W = std::sin(0.5 * eps);
     if ((pl.dim == 2) != (pl.kernel >= BZ_KERNEL_B1 && pl.kernel <= BZ_KERNEL_B4)) return BZ_ERR_ARG;
     switch (pl.kernel) {
+        case BZ_KERNEL_DEBYE: {
+            // g (1 - cos) = h |log 2h|, g (1 - cos)^2 = 2 h^3 |log 2h| (h = sin(t/2)); with t = eps u^2
+            // the integrands are smooth in u: 32-point Gauss-Legendre
+            pl.kc = 1.0;
+            std::vector<double> x, w;
+            gauss_legendre(32, 0.0, 1.0, x, w);
+            double a1 = 0.0, a2 = 0.0;
+            for (int i = 0; i < 32; ++i) {
+                const double t = eps * x[i] * x[i], jac = 2.0 * eps * x[i];
+                const double h = std::sin(0.5 * t), lg = std::fabs(std::log(2.0 * h));
+                a1 += w[i] * jac * h * lg;
+                a2 += w[i] * jac * 2.0 * h * h * h * lg;
+            }
+            pl.A[0] = a1;
+            pl.A[1] = a2;
+            break;
+        }
         // 2D kernels b = c sin^beta(t/2): b (1 - cos) = 2 c sin^(beta+2)(t/2), b (1 - cos)^2 =
         // 4 c sin^(beta+4)(t/2) over [0, eps] (parts I and III of Sec. 4.1 (i))
         case BZ_KERNEL_B1:
@@ -223,6 +241,7 @@ bz_status build_kernel_constants(Plan &pl) {
         default: return BZ_ERR_ARG;
     }
     pl.A[2] = 2.0 * pl.A[0] - pl.A[1];   // sin^2 t = 2 (1 - cos t) - (1 - cos t)^2
+    if (pl.theta0 > 0.0) pl.A[0] = pl.A[1] = pl.A[2] = 0.0;   // a cutoff kernel vanishes near 0: no part I
     return BZ_OK;
 }
 
@@ -241,7 +260,7 @@ void build_theta_rules(Plan &pl) {
         double z = M_PI * rr[i] * kmax / (2.0 * pl.L);
         double width = std::fmin(0.25, 10.0 / std::fmax(z, 1e-300));
         std::vector<double> edges;
-        double lo = pl.eps;
+        double lo = pl.theta0 > 0.0 ? pl.theta0 : pl.eps;   // part II starts at the cutoff if there is one
         const double tg = 0.25;
         edges.push_back(lo);
         while (lo < tg) {
@@ -250,8 +269,15 @@ void build_theta_rules(Plan &pl) {
             for (int k = 1; k <= ns; ++k) edges.push_back(lo + (hi - lo) * k / ns);
             lo = hi;
         }
-        int nu = (int)std::ceil((M_PI - tg) / width);
-        for (int k = 1; k <= nu; ++k) edges.push_back(tg + (M_PI - tg) * k / nu);
+        // equal panels to pi; the Debye-Yukawa kernel's |log(2 sin(t/2))| has a kink at pi/3
+        std::vector<double> stops;
+        if (pl.kernel == BZ_KERNEL_DEBYE && lo < M_PI / 3.0) stops.push_back(M_PI / 3.0);
+        stops.push_back(M_PI);
+        for (double stop : stops) {
+            int nu = (int)std::ceil((stop - lo) / width);
+            for (int k = 1; k <= nu; ++k) edges.push_back(lo + (stop - lo) * k / nu);
+            lo = stop;
+        }
         ThetaRule &R = pl.rules[i];
         for (size_t e = 0; e + 1 < edges.size(); ++e) {
             double a = edges[e], b = edges[e + 1];
