@@ -13,6 +13,9 @@ Definitions followed (3D, N modes per axis, signed k in {-N/2, ..., N/2-1}):
   low-rank weight of eq. GG1/approxG, summed over pairs (l, m) -- O(N^6 P), small N.
 * `padded=True` keeps l + m = k without wrap-around (the literal Galerkin sum of
   eq. sum): DFTs of size 2N, modes outside the N-range zero.
+* `collide_real`: f is a real function (Sec. 2), so only the Hermitian part of fhat is data;
+  the reading takes that part with the Nyquist planes (a signed index -N/2, which has no
+  partner +N/2 on the grid) set to zero and zeroes the Nyquist planes of the result.
 """
 from __future__ import annotations
 
@@ -92,6 +95,48 @@ def collide(plan: OraclePlan, fhat: np.ndarray, p0: int = 0, p1: int | None = No
         U = dft3(h * g, -1) / N ** 3
         Q += plan.alpha(p) * U
     return Q
+
+
+def nyquist_mask(N: int) -> np.ndarray:
+    """True at every mode with a signed index -N/2 on some axis (the Nyquist planes)."""
+    ny = signed(N) == -(N // 2)
+    return ny[:, None, None] | ny[None, :, None] | ny[None, None, :]
+
+
+def mirror(x: np.ndarray) -> np.ndarray:
+    """y[k] = x[-k], indices modulo N on every axis."""
+    N = x.shape[0]
+    m = (-np.arange(N)) % N
+    return x[np.ix_(m, m, m)]
+
+
+def real_band(fhat: np.ndarray) -> np.ndarray:
+    """Coefficients of the real part of f (Sec. 2: f real means fhat_{-k} = conj fhat_k),
+    (fhat_k + conj fhat_{-k}) / 2, with the Nyquist planes set to zero."""
+    fhat = np.asarray(fhat, dtype=np.complex128)
+    out = 0.5 * (fhat + np.conj(mirror(fhat)))
+    out[nyquist_mask(fhat.shape[0])] = 0.0
+    return out
+
+
+def collide_real(plan: OraclePlan, fhat: np.ndarray, p0: int = 0, p1: int | None = None) -> np.ndarray:
+    """Real-data reading of eq. realQ: the operator of the real, Nyquist-free part of f
+    (`real_band`), with the Nyquist planes of the result set to zero."""
+    Q = collide(plan, real_band(fhat), p0, p1)
+    Q[nyquist_mask(plan.N)] = 0.0
+    return Q
+
+
+def rk4_real(plan: OraclePlan, fhat: np.ndarray, dt: float, nsteps: int) -> np.ndarray:
+    """Classical RK4 (Sec. 5.2) on d fhat/dt = collide_real(fhat)."""
+    f = np.asarray(fhat, dtype=np.complex128).copy()
+    for _ in range(nsteps):
+        k1 = collide_real(plan, f)
+        k2 = collide_real(plan, f + 0.5 * dt * k1)
+        k3 = collide_real(plan, f + 0.5 * dt * k2)
+        k4 = collide_real(plan, f + dt * k3)
+        f = f + dt / 6.0 * (k1 + 2 * k2 + 2 * k3 + k4)
+    return f
 
 
 def _embed(x: np.ndarray, N2: int) -> np.ndarray:
