@@ -14,8 +14,8 @@ Definitions followed (3D, N modes per axis, signed k in {-N/2, ..., N/2-1}):
 * `padded=True` keeps l + m = k without wrap-around (the literal Galerkin sum of
   eq. sum): DFTs of size 2N, modes outside the N-range zero.
 * `collide_real`: f is a real function (Sec. 2), so only the Hermitian part of fhat is data;
-  the reading takes that part with the Nyquist planes (a signed index -N/2, which has no
-  partner +N/2 on the grid) set to zero and zeroes the Nyquist planes of the result.
+  the reading applies eq. realQ to that part with the Nyquist planes (a signed index -N/2,
+  which has no partner +N/2 on the grid) set to zero.
 """
 from __future__ import annotations
 
@@ -121,10 +121,8 @@ def real_band(fhat: np.ndarray) -> np.ndarray:
 
 def collide_real(plan: OraclePlan, fhat: np.ndarray, p0: int = 0, p1: int | None = None) -> np.ndarray:
     """Real-data reading of eq. realQ: the operator of the real, Nyquist-free part of f
-    (`real_band`), with the Nyquist planes of the result set to zero."""
-    Q = collide(plan, real_band(fhat), p0, p1)
-    Q[nyquist_mask(plan.N)] = 0.0
-    return Q
+    (`real_band`), every output mode kept."""
+    return collide(plan, real_band(fhat), p0, p1)
 
 
 def rk4_real(plan: OraclePlan, fhat: np.ndarray, dt: float, nsteps: int) -> np.ndarray:

@@ -6,8 +6,9 @@ planes (signed index -N/2, no partner +N/2), which the reading drops.  CPU only.
   planes are zero (numpy's FFT makes them), gives real grid values for any input, and
   removes a purely imaginary f.
 * `collide_real` equals the O(N^6) double sum of eq. sum (eq. approxG weights) applied to
-  the band, with the Nyquist planes of the result zero (N = 8).
-* Its result is Hermitian for any input, i.e. Q(f, f) is a real function.
+  the band (N = 8), and equals the circular operator on a real f without Nyquist content.
+* Off the Nyquist planes its result is Hermitian for any input (F(-k) = conj F(k)); on them
+  the weight alpha_p(k) at the signed index -N/2 has no mirror, so Q need not be.
 * For a smooth real f (BKW, Sec. 5.1) it differs from the circular operator by less than the
   Nyquist content of f allows.
 """
@@ -47,16 +48,19 @@ def test_collide_real_equals_direct_sum_of_the_band(plan8):
     f = bi.random_fhat(8, seed=5)
     Q = spectral.collide_real(plan8, f)
     D = spectral.direct_sum(plan8, spectral.real_band(f))
-    D[spectral.nyquist_mask(8)] = 0
     assert np.max(np.abs(Q - D)) < 1e-12 * np.max(np.abs(D))
+    fr = _real_grid_band(8, seed=6)                    # real f, no Nyquist content
+    Qc = spectral.collide(plan8, fr)
+    assert np.max(np.abs(spectral.collide_real(plan8, fr) - Qc)) < 1e-14 * np.max(np.abs(Qc))
 
 
-def test_collide_real_is_hermitian(plan8):
+def test_collide_real_is_hermitian_off_the_nyquist_planes(plan8):
+    ny = spectral.nyquist_mask(8)
     for seed in (1, 2):
         Q = spectral.collide_real(plan8, bi.random_fhat(8, seed=seed))
-        assert np.max(np.abs(spectral.mirror(Q) - np.conj(Q))) < 1e-13 * np.max(np.abs(Q))
-        q = np.fft.ifftn(Q)
-        assert np.max(np.abs(q.imag)) < 1e-13 * np.max(np.abs(q.real))
+        d = np.abs(spectral.mirror(Q) - np.conj(Q))
+        assert np.max(d[~ny]) < 1e-13 * np.max(np.abs(Q))
+        assert np.max(d[ny]) > 1e-6 * np.max(np.abs(Q))      # alpha at -N/2 has no mirror
 
 
 def test_term_ranges_add_up(plan8):
@@ -68,8 +72,8 @@ def test_term_ranges_add_up(plan8):
 
 def test_smooth_real_f_is_barely_changed():
     """BKW at t = 6.5 on N = 32 (L = 6.62): its Nyquist planes hold |fhat| ~ 5e-8 of fhat_0, and
-    off the Nyquist planes the real-data reading moves Q by a few 1e-7 of max|Q| (at N = 16 the
-    same f is under-resolved: Nyquist content 1e-2, and Q moves by 5%)."""
+    the real-data reading moves Q by a few 1e-7 of max|Q| (at N = 16 the same f is
+    under-resolved: Nyquist content 1e-2, and Q moves by 5%)."""
     N, R = 32, 6.0
     L = bi.L_from_R(R)
     f = bi.bkw_fhat(N, L, bi.bkw_K(6.5))
@@ -79,6 +83,6 @@ def test_smooth_real_f_is_barely_changed():
     plan = spectral.OraclePlan(N, L, R, 0.0, kernels.Kernel("family", 0.5), 4, 12)
     Q = spectral.collide(plan, f, 0, 8)
     Qr = spectral.collide_real(plan, f, 0, 8)
-    dev = np.max(np.abs((Q - Qr)[~ny])) / np.max(np.abs(Q))
-    print(f"Nyquist content {content:.2e}, off-Nyquist |Q - Q_real| / max|Q| = {dev:.2e}")
+    dev = np.max(np.abs(Q - Qr)) / np.max(np.abs(Q))
+    print(f"Nyquist content {content:.2e}, |Q - Q_real| / max|Q| = {dev:.2e}")
     assert content < 1e-7 and dev < 1e-5
