@@ -104,6 +104,24 @@ enum { BZ_PIPE_AUTO = 0, BZ_PIPE_FUSED = 1, BZ_PIPE_CHUNKED = 2 };
  * inside the fused kernel.  AUTO = FP64. */
 enum { BZ_H_AUTO = 0, BZ_H_FP64 = 1, BZ_H_FP32 = 2 };
 
+/* Data of the operator (Sec. 2: f is a real distribution function, so fhat is Hermitian).
+ *   BZ_DATA_COMPLEX: fhat is any complex array; the operator of eq. realQ as it stands.
+ *   BZ_DATA_REAL:    f is real.  The plan takes the Hermitian part of fhat,
+ *                    (fhat_k + conj fhat_{-k}) / 2, with every mode that has an index -N/2 (the
+ *                    Nyquist planes) set to zero, and returns the operator of that band-limited
+ *                    real f (every output mode).  For such f every g_p = IFFT(beta_p fhat) and h
+ *                    are real, so two terms share one pair of 3D transforms: x = (beta_p +
+ *                    i beta_p') fhat gives g_p + i g_p', and
+ *                    with A = (alpha_p - i alpha_p') / 2 the pair adds W + conj(W(-k)),
+ *                    W = A FFT(h (g_p + i g_p')); the sum of the W over pairs is symmetrised once
+ *                    per collide.  On the Nyquist planes, where alpha_p(-k) != conj alpha_p(k), a
+ *                    second sum with a 3 N^2 table per pair completes every mode, so for a real f
+ *                    without Nyquist content the result is eq. realQ itself.  Half the transforms,
+ *                    exchanges and (nearly) table bytes per term.  3D, FP32, circular, fused
+ *                    pipeline, N = 8, 16 or 32, M even; bz_collide_terms takes even term bounds;
+ *                    batches and bz_collide_noalloc return BZ_ERR_UNSUPPORTED. */
+enum { BZ_DATA_COMPLEX = 0, BZ_DATA_REAL = 1 };
+
 typedef struct bz_plan bz_plan;
 
 typedef struct {
@@ -134,6 +152,7 @@ typedef struct {
     double theta0;    /* angular cutoff: b = 0 for theta < theta0 (and theta > 2 pi - theta0 in 2D), as
                          eqs. ApproximatedDebyecutoff and b3cutoff; 0 = none, else eps <= theta0 < pi.
                          With a cutoff there is no Taylor part; the theta rule starts at theta0. */
+    int data;         /* BZ_DATA_*                                                         */
 } bz_plan_desc;
 
 /* Creates a plan: quadrature terms, the FP64 F table (computed on the device, stored
@@ -146,7 +165,8 @@ bz_status bz_plan_create(bz_plan **out, int N, double L, double R, double gamma,
 bz_status bz_plan_create_ex(bz_plan **out, const bz_plan_desc *desc);
 void bz_plan_destroy(bz_plan *plan);
 
-/* Number of quadrature terms P = N_rho * M; bytes of the alpha table. */
+/* Number of quadrature terms P = N_rho * M; bytes of the alpha table (with the pair table of a
+ * BZ_DATA_REAL plan). */
 bz_status bz_plan_info(const bz_plan *plan, int *P, size_t *alpha_bytes, size_t *workspace_bytes);
 
 /* The collide pipeline the plan runs: *pipeline = BZ_PIPE_FUSED or BZ_PIPE_CHUNKED;

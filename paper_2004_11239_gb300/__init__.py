@@ -37,6 +37,7 @@ BZ_PREC_FP32, BZ_PREC_BF16X3 = 0, 1
 BZ_PIPE_AUTO, BZ_PIPE_FUSED, BZ_PIPE_CHUNKED = 0, 1, 2
 BZ_H_AUTO, BZ_H_FP64, BZ_H_FP32 = 0, 1, 2
 BZ_CONV_CIRCULAR, BZ_CONV_PADDED = 0, 1
+BZ_DATA_COMPLEX, BZ_DATA_REAL = 0, 1
 _STATUS = {0: "BZ_OK", 1: "BZ_ERR_ARG", 2: "BZ_ERR_OOM", 3: "BZ_ERR_CUDA", 4: "BZ_ERR_TIMEOUT",
            5: "BZ_ERR_NONFINITE", 6: "BZ_ERR_BUSY", 7: "BZ_ERR_UNSUPPORTED"}
 
@@ -67,7 +68,8 @@ class bz_plan_desc(ctypes.Structure):
                 ("eps", ctypes.c_double), ("sphere_xyz", ctypes.POINTER(ctypes.c_double)),
                 ("sphere_w", ctypes.POINTER(ctypes.c_double)), ("chunk_terms", ctypes.c_int),
                 ("pipeline", ctypes.c_int), ("cluster", ctypes.c_int), ("h_precision", ctypes.c_int),
-                ("conv", ctypes.c_int), ("dim", ctypes.c_int), ("theta0", ctypes.c_double)]
+                ("conv", ctypes.c_int), ("dim", ctypes.c_int), ("theta0", ctypes.c_double),
+                ("data", ctypes.c_int)]
 
 
 def library_path() -> str:
@@ -203,7 +205,8 @@ def bz_plan_create_ex(N: int, L: float, R: float, gamma: float, s: float, N_rho:
                       kernel: int = BZ_KERNEL_FAMILY, eps: float = 0.0, sphere=None,
                       chunk_terms: int = 0, pipeline: int = BZ_PIPE_AUTO, cluster: int = 0,
                       h_precision: int = BZ_H_AUTO, precision: int = BZ_PREC_FP32,
-                      conv: int = BZ_CONV_CIRCULAR, dim: int = 3, theta0: float = 0.0) -> Plan:
+                      conv: int = BZ_CONV_CIRCULAR, dim: int = 3, theta0: float = 0.0,
+                      data: int = BZ_DATA_COMPLEX) -> Plan:
     d = bz_plan_desc()
     d.N, d.L, d.R, d.gamma, d.s, d.N_rho, d.M = N, L, R, gamma, s, N_rho, M
     d.kernel, d.precision, d.eps, d.chunk_terms = kernel, precision, eps, chunk_terms
@@ -213,6 +216,7 @@ def bz_plan_create_ex(N: int, L: float, R: float, gamma: float, s: float, N_rho:
     d.conv = conv
     d.dim = dim
     d.theta0 = theta0
+    d.data = data
     keep = []
     if sphere is not None:
         import numpy as np

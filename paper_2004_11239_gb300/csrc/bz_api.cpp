@@ -30,8 +30,10 @@ void free_plan(bz::Plan &p) {
     cudaFree(p.alpha); cudaFree(p.tw); cudaFree(p.rule_buf); cudaFree(p.rule_off);
     cudaFree(p.term_dev); cudaFree(p.S); cudaFree(p.h); cudaFree(p.fin); cudaFree(p.acc);
     cudaFree(p.rk); cudaFree(p.mom); cudaFree(p.part); cudaFree(p.fin64); cudaFree(p.scr64);
-    cudaFree(p.wimg); cudaFree(p.dev_err);
-    p.wimg = nullptr; p.dev_err = nullptr;
+    cudaFree(p.wimg); cudaFree(p.dev_err); cudaFree(p.apair); cudaFree(p.fsym); cudaFree(p.fsym64);
+    cudaFree(p.cpair); cudaFree(p.part_s); cudaFree(p.acc_s);
+    p.wimg = nullptr; p.dev_err = nullptr; p.apair = nullptr; p.fsym = nullptr; p.fsym64 = nullptr;
+    p.cpair = nullptr; p.part_s = nullptr; p.acc_s = nullptr;
     p.part = nullptr; p.fin64 = nullptr; p.scr64 = nullptr; p.src = nullptr;
     p.alpha = nullptr; p.tw = nullptr; p.rule_buf = nullptr; p.rule_off = nullptr;
     p.term_dev = nullptr; p.S = nullptr; p.h = nullptr; p.fin = nullptr; p.acc = nullptr;
@@ -69,6 +71,7 @@ bz_status select_fused(bz::Plan &pl, int forced) {
     int nc = mixed ? 1 : bz::fused_candidates(pl.N, cs);
     if (mixed) cs[0] = 8;
     const size_t field = (size_t)pl.N * pl.N * pl.N * sizeof(float2);
+    const size_t fields = (size_t)3 * pl.N * pl.N * sizeof(float2);   // BZ_DATA_REAL: Nyquist-plane sums
     int bestC = 0, bestG = 0;
     float best = 1e30f;
     cudaEvent_t e0, e1;
@@ -77,11 +80,17 @@ bz_status select_fused(bz::Plan &pl, int forced) {
     for (int c = 0; c < nc; ++c) {
         if (forced > 0 && cs[c] != forced) continue;
         int G = 0;
-        const cudaError_t se = mixed ? bz::mixed_setup(pl.N, &G) : bz::fused_setup(pl.N, cs[c], &G);
+        const cudaError_t se = mixed ? bz::mixed_setup(pl.N, &G) : bz::fused_setup(pl.N, cs[c], &G, pl.real != 0);
         if (se != cudaSuccess || G <= 0) { cudaGetLastError(); continue; }
-        float2 *part = nullptr;
+        float2 *part = nullptr, *parts = nullptr;
         if (cudaMalloc(&part, (size_t)G * field) != cudaSuccess) { cudaGetLastError(); continue; }
+        if (pl.real && cudaMalloc(&parts, (size_t)G * fields) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(part);
+            continue;
+        }
         std::swap(part, pl.part);
+        std::swap(parts, pl.part_s);
         pl.use_fused = 1; pl.fused_C = cs[c]; pl.fused_G = G;
         float ms = 1e30f;
         if (bz::collide_fused(pl, 0, pl.P, nullptr, nullptr) == BZ_OK) {      // warm-up
@@ -92,7 +101,9 @@ bz_status select_fused(bz::Plan &pl, int forced) {
         }
         cudaGetLastError();
         std::swap(part, pl.part);
+        std::swap(parts, pl.part_s);
         cudaFree(part);
+        cudaFree(parts);
         if (ms < best) { best = ms; bestC = cs[c]; bestG = G; }
     }
     cudaEventDestroy(e0);
@@ -100,9 +111,10 @@ bz_status select_fused(bz::Plan &pl, int forced) {
     pl.use_fused = 0;
     if (bestC == 0) return BZ_ERR_UNSUPPORTED;
     if (dmalloc(&pl.part, (size_t)bestG * field) != BZ_OK) return BZ_ERR_OOM;
+    if (pl.real && dmalloc(&pl.part_s, (size_t)bestG * fields) != BZ_OK) return BZ_ERR_OOM;
     pl.use_fused = 1; pl.fused_C = bestC; pl.fused_G = bestG;
     pl.fused_ms = best;
-    pl.ws_bytes += (size_t)bestG * field;
+    pl.ws_bytes += (size_t)bestG * (field + (pl.real ? fields : 0));
     return BZ_OK;
 }
 
@@ -126,6 +138,11 @@ bz_status create(bz_plan **out, const bz_plan_desc *d) {
     if (d->precision == BZ_PREC_BF16X3 && (d->N != 32 || d->pipeline == BZ_PIPE_CHUNKED))
         return BZ_ERR_UNSUPPORTED;
     if (d->pipeline < BZ_PIPE_AUTO || d->pipeline > BZ_PIPE_CHUNKED) return BZ_ERR_ARG;
+    if (d->data != BZ_DATA_COMPLEX && d->data != BZ_DATA_REAL) return BZ_ERR_ARG;
+    const bool real = d->data == BZ_DATA_REAL;
+    if (real && (dim != 3 || d->precision != BZ_PREC_FP32 || padded || 32 % d->N != 0 || d->M % 2 != 0 ||
+                 d->pipeline == BZ_PIPE_CHUNKED))
+        return BZ_ERR_UNSUPPORTED;
     if (dim == 3 && !((d->kernel >= BZ_KERNEL_FAMILY && d->kernel <= BZ_KERNEL_B8) || d->kernel == BZ_KERNEL_DEBYE))
         return BZ_ERR_ARG;
     bz_plan *h = new (std::nothrow) bz_plan();
@@ -134,6 +151,7 @@ bz_status create(bz_plan **out, const bz_plan_desc *d) {
     pl.dim = dim;
     pl.N = padded ? 2 * d->N : d->N; pl.Nin = padded ? d->N : 0; pl.L = d->L; pl.R = d->R; pl.gamma = d->gamma; pl.s = d->s;
     pl.N_rho = d->N_rho; pl.M = d->M; pl.kernel = d->kernel; pl.precision = d->precision;
+    pl.real = real ? 1 : 0;
     pl.eps = d->eps > 0 ? d->eps : M_PI / 1000.0;
     if (!(d->theta0 == 0.0 || (d->theta0 >= pl.eps && d->theta0 < M_PI))) { delete h; return BZ_ERR_ARG; }
     pl.theta0 = d->theta0;
@@ -183,6 +201,16 @@ bz_status create(bz_plan **out, const bz_plan_desc *d) {
         return BZ_ERR_CUDA;
     }
     s = bz::ftable_build(pl);
+    if (s == BZ_OK && pl.real) {
+        // term pairs (2q, 2q + 1) share a radial node (M even) and one pair of transforms
+        const size_t ns = (size_t)3 * N * N;
+        if ((s = dmalloc(&pl.apair, (size_t)(pl.P / 2) * field)) == BZ_OK &&
+            (s = dmalloc(&pl.cpair, (size_t)(pl.P / 2) * ns * sizeof(float2))) == BZ_OK &&
+            (s = dmalloc(&pl.acc_s, ns * sizeof(double2))) == BZ_OK &&
+            (s = dmalloc(&pl.fsym, field)) == BZ_OK && (s = dmalloc(&pl.fsym64, n3 * sizeof(double2))) == BZ_OK)
+            s = bz::build_pair_table(pl);
+        pl.ws_bytes += field + n3 * sizeof(double2) + ns * sizeof(double2);
+    }
     if (s != BZ_OK) {
         free_plan(pl);
         delete h;
@@ -211,7 +239,7 @@ bz_status create(bz_plan **out, const bz_plan_desc *d) {
             if (select_fused(pl, d->cluster) != BZ_OK) cudaGetLastError();
         }
     }
-    if ((d->pipeline == BZ_PIPE_FUSED || pl.precision == BZ_PREC_BF16X3) && !pl.use_fused) {
+    if ((d->pipeline == BZ_PIPE_FUSED || pl.precision == BZ_PREC_BF16X3 || pl.real) && !pl.use_fused) {
         free_plan(pl);
         delete h;
         return BZ_ERR_UNSUPPORTED;
@@ -246,7 +274,9 @@ bz_status bz_plan_info(const bz_plan *plan, int *P, size_t *alpha_bytes, size_t 
     const bz::Plan &p = plan->p;
     size_t n3 = bz::modes(p);
     if (P) *P = p.P;
-    if (alpha_bytes) *alpha_bytes = (size_t)p.P * n3 * sizeof(float2);
+    if (alpha_bytes)
+        *alpha_bytes = ((size_t)p.P * n3 + (p.real ? (size_t)(p.P / 2) * (n3 + 3 * (size_t)p.N * p.N) : 0)) *
+                       sizeof(float2);
     if (workspace_bytes) *workspace_bytes = p.ws_bytes;
     return BZ_OK;
 }
@@ -282,6 +312,7 @@ bz_status bz_collide_terms(bz_plan *plan, int p0, int p1, const void *fhat, void
     if (!plan || !fhat || !Qhat || fhat == Qhat) return BZ_ERR_ARG;
     bz::Plan &pl = plan->p;
     if (p0 < 0 || p1 < p0 || p1 > pl.P) return BZ_ERR_ARG;
+    if (pl.real && ((p0 | p1) & 1)) return BZ_ERR_ARG;          // whole term pairs
     if (dtype != BZ_C64 && dtype != BZ_C128) return BZ_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     int nl = 0;

@@ -241,7 +241,7 @@ bz_status bz_batch_create(bz_batch **out, const bz_plan *plan, int capacity, int
     if (!out || !plan || capacity < 1) return BZ_ERR_ARG;
     *out = nullptr;
     Plan *pl = const_cast<Plan *>(plan_internal(plan));
-    if (!pl->use_fused || pl->Nin) return BZ_ERR_UNSUPPORTED;   // batches: fused kernel (N <= 32), circular
+    if (!pl->use_fused || pl->Nin || pl->real) return BZ_ERR_UNSUPPORTED;   // batches: fused kernel (N <= 32), circular, complex data
     bz_batch *B = new (std::nothrow) bz_batch();
     if (!B) return BZ_ERR_OOM;
     B->pl = pl;

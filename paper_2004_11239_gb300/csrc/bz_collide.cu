@@ -445,7 +445,7 @@ extern "C" bz_status bz_collide_noalloc(const bz_plan *plan, const void *fhat, v
     if (!plan || !fhat || !Qhat || fhat == Qhat) return BZ_ERR_ARG;
     if (dtype != BZ_C64 && dtype != BZ_C128) return BZ_ERR_ARG;
     const Plan &pl = *plan_internal(plan);
-    if (pl.Nin || pl.dim == 2) return BZ_ERR_UNSUPPORTED;    // padded and 2D plans: bz_collide
+    if (pl.Nin || pl.dim == 2 || pl.real) return BZ_ERR_UNSUPPORTED;   // padded, 2D and real-data plans: bz_collide
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return BZ_ERR_CUDA;
     if (dev != pl.device) return BZ_ERR_ARG;

@@ -28,15 +28,16 @@ namespace cg = cooperative_groups;
 
 namespace bz {
 
-template <int N, int C_> struct FK {
+template <int N, int C_, bool R_ = false> struct FK {
     static constexpr int C = C_;
     static constexpr int PPC = N / C;                 // planes (and pencil rows) per CTA
     static constexpr int LD = N + 1;                  // padded plane row
     static constexpr int THREADS = N * PPC;
     static constexpr size_t PLANES = (size_t)PPC * N * LD * sizeof(float2);
     static constexpr size_t TILE = (size_t)PPC * N * N * sizeof(float2);   // alpha tile, h slice
-    static constexpr size_t TW = (size_t)3 * N * sizeof(float2);           // one term's twiddles
-    static constexpr size_t SMEM = PLANES + 2 * TILE + 2 * TW;
+    static constexpr size_t TW = (size_t)(R_ ? 6 : 3) * N * sizeof(float2);  // one term's (pair's) twiddles
+    static constexpr size_t XS1 = R_ ? (size_t)N * N * sizeof(float2) : 0;  // Nyquist plane k1 = -N/2 (pair form)
+    static constexpr size_t SMEM = PLANES + 2 * TILE + 2 * TW + XS1;
     // two CTAs per SM where registers and shared memory allow it
     static constexpr int MIN_BLOCKS = (N <= 16 || N * N / C_ <= 128) ? 2 : 1;
 };
@@ -68,20 +69,56 @@ __device__ __forceinline__ void phase_a(const float2 *__restrict__ fin, const fl
     for (int j = 0; j < N; ++j) my[lane * LD + j] = x[j];
 }
 
+// Phase A of a term pair (p, p') (BZ_DATA_REAL): x = (beta_p + i beta_p') fhat, whose inverse
+// transform is g_p + i g_p' with both parts real; tws holds the two terms' [3][N] twiddles.
+template <int N>
+__device__ __forceinline__ void phase_a_pair(const float2 *__restrict__ fin, const float2 *tws, float2 *my,
+                                             int k1, int lane) {
+    constexpr int LD = N + 1;
+    const float2 *f = fin + (size_t)k1 * N * N;
+    const float2 ta = cmul(tws[k1], tws[2 * N + lane]);
+    const float2 tb = cmul(tws[3 * N + k1], tws[5 * N + lane]);
+    float2 x[N];
+    #pragma unroll
+    for (int i = 0; i < N; ++i) {
+        const float2 u = cmul(ta, tws[N + i]), v = cmul(tb, tws[4 * N + i]);
+        x[i] = cmul(f[i * N + lane], make_float2(u.x - v.y, u.y + v.x));       // u + i v
+    }
+    fft_inplace<N, +1>(x);                                    // k2 -> j2
+    #pragma unroll
+    for (int i = 0; i < N; ++i) my[i * LD + lane] = x[i];
+    __syncthreads();
+    #pragma unroll
+    for (int j = 0; j < N; ++j) x[j] = my[lane * LD + j];
+    fft_inplace<N, +1>(x);                                    // k3 -> j3 (row j2 = lane)
+    #pragma unroll
+    for (int j = 0; j < N; ++j) my[lane * LD + j] = x[j];
+}
+
 // Work item w: instance b = w / nblk (array slot slots[b]), term block blk = w % nblk covering
 // terms [p0 + blk TB, min(p1, p0 + (blk + 1) TB)).  The item's FP32 sum over its terms goes to
 // part[slot * nblk + blk]; it depends only on the instance and the block bounds, so a result
 // does not depend on which other instances share the launch.
-template <int N, int CC, bool SCALED>
-__global__ void __launch_bounds__(FK<N, CC>::THREADS, FK<N, CC>::MIN_BLOCKS)
+// REAL: the units are term pairs (BZ_DATA_REAL): a.alpha is the pair table A, h is real and
+// the accumulated sum is V = sum of A Z over the pairs (symmetrised after the reduction).  On
+// the Nyquist planes S a second sum X = sum of C Z is kept (a.cpair; C = 0 off S), one entry
+// per mode of S in three families: k1 = -N/2 ([k2][k3], shared memory of the CTA owning that
+// plane), else k3 = -N/2 ([k1][k2], one register per thread: the value of lane N/2 reaches lane
+// k2 by shuffles), else k2 = -N/2 ([k1][k3], one register per thread); it goes to a.part_s.
+template <int N, int CC, bool SCALED, bool REAL = false>
+__global__ void __launch_bounds__(FK<N, CC, REAL>::THREADS, FK<N, CC, REAL>::MIN_BLOCKS)
 k_fused(ItemArgs a) {
-    using K = FK<N, CC>;
+    static_assert(!(SCALED && REAL), "the pair form has no per-instance radial scale");
+    static_assert(!REAL || 32 % N == 0, "the pair form shuffles within the lanes of one plane");
+    using K = FK<N, CC, REAL>;
+    constexpr int TWN = REAL ? 6 * N : 3 * N;                // twiddles per unit
     constexpr int C = K::C, PPC = K::PPC, LD = K::LD, T = K::THREADS;
     extern __shared__ __align__(16) float2 smem[];
     float2 *planes = smem;                                   // [PPC][N][LD]
     float2 *sal = smem + (size_t)PPC * N * LD;               // alpha tile [PPC][N][N]
     float2 *shs = sal + (size_t)PPC * N * N;                 // h slice [PPC (j2)][N (j1)][N (j3)]
-    float2 *stw = shs + (size_t)PPC * N * N;                 // twiddles, two buffers of [3][N]
+    float2 *stw = shs + (size_t)PPC * N * N;                 // twiddles, two buffers of [TWN]
+    float2 *xs1 = stw + 2 * TWN;                             // REAL: X on plane k1 = -N/2, [k2][k3]
     const int tid = threadIdx.x;
     int rank = 0;
     if constexpr (C > 1) rank = (int)cg::this_cluster().block_rank();
@@ -98,9 +135,9 @@ k_fused(ItemArgs a) {
 
     const int count = a.count_dev ? *a.count_dev : a.count;
     const int nitems = count * a.nblk;
-    auto fetch_tw = [&](int p, int buf) {                    // one term's 3N twiddles, 16 B per copy
+    auto fetch_tw = [&](int p, int buf) {                    // one unit's twiddles, 16 B per copy
         if (p >= 0 && tid < (int)(K::TW / 16))
-            cp_async16((char *)(stw + buf * 3 * N) + 16 * tid, (const char *)(a.tw + (size_t)p * 3 * N) + 16 * tid);
+            cp_async16((char *)(stw + buf * TWN) + 16 * tid, (const char *)(a.tw + (size_t)p * TWN) + 16 * tid);
         cp_async_commit();
     };
 
@@ -133,6 +170,13 @@ k_fused(ItemArgs a) {
         float2 acc[N];
         #pragma unroll
         for (int i = 0; i < N; ++i) acc[i] = make_float2(0.f, 0.f);
+        float2 x2 = make_float2(0.f, 0.f), x3 = make_float2(0.f, 0.f);   // REAL: X at (k1, -N/2, lane), (k1, lane, -N/2)
+        if constexpr (REAL) {
+            if (k1 == N / 2) {
+                #pragma unroll 8
+                for (int i = 0; i < N; ++i) xs1[i * N + lane] = make_float2(0.f, 0.f);
+            }
+        }
         int it = 0;
         for (int p = t0; p < t1; ++p, ++it) {
             const int buf = it & 1;
@@ -148,15 +192,25 @@ k_fused(ItemArgs a) {
             float sc = 1.f;
             if constexpr (SCALED) sc = a.gsc[(size_t)slot * a.N_rho + p / a.M];
             // A
-            phase_a<N>(fin, stw + buf * 3 * N, my, k1, lane);
+            if constexpr (REAL) phase_a_pair<N>(fin, stw + buf * TWN, my, k1, lane);
+            else phase_a<N>(fin, stw + buf * TWN, my, k1, lane);
             cluster_barrier<C>();
             // B: pencil (j2p, lane) over k1, gathered from the cluster
             float2 x[N];
             #pragma unroll
             for (int k = 0; k < N; ++k) x[k] = ld_dsmem(pen[k / PPC] + (uint32_t)(k % PPC) * PLANE_BYTES);
             fft_inplace<N, +1>(x);                            // k1 -> j1
-            #pragma unroll
-            for (int j = 0; j < N; ++j) x[j] = cmul(x[j], shs[((size_t)pid * N + j) * N + lane]);
+            if constexpr (REAL) {
+                #pragma unroll
+                for (int j = 0; j < N; ++j) {                 // h is real
+                    const float hv = shs[((size_t)pid * N + j) * N + lane].x;
+                    x[j].x *= hv;
+                    x[j].y *= hv;
+                }
+            } else {
+                #pragma unroll
+                for (int j = 0; j < N; ++j) x[j] = cmul(x[j], shs[((size_t)pid * N + j) * N + lane]);
+            }
             fft_inplace<N, -1>(x);                            // j1 -> k1
             #pragma unroll
             for (int k = 0; k < N; ++k) st_dsmem(pen[k / PPC] + (uint32_t)(k % PPC) * PLANE_BYTES, x[k]);
@@ -184,11 +238,46 @@ k_fused(ItemArgs a) {
                     acc[i].y = fmaf(x[i].x, al.y, fmaf(x[i].y, al.x, acc[i].y));
                 }
             }
+            if constexpr (REAL) {
+                const float2 *cq = a.cpair + (size_t)p * 3 * N * N;
+                if (k1 == N / 2) {                            // whole plane (warp-uniform)
+                    #pragma unroll
+                    for (int i = 0; i < N; ++i) {
+                        const float2 c = __ldg(cq + i * N + lane);
+                        float2 v = xs1[i * N + lane];
+                        v.x = fmaf(x[i].x, c.x, fmaf(-x[i].y, c.y, v.x));
+                        v.y = fmaf(x[i].x, c.y, fmaf(x[i].y, c.x, v.y));
+                        xs1[i * N + lane] = v;
+                    }
+                }
+                float2 z3 = make_float2(0.f, 0.f);            // Z(k1, k2 = lane, -N/2) from lane N/2
+                #pragma unroll
+                for (int i = 0; i < N; ++i) {
+                    const float zr = __shfl_sync(0xffffffffu, x[i].x, N / 2, N);
+                    const float zi = __shfl_sync(0xffffffffu, x[i].y, N / 2, N);
+                    if (i == lane) z3 = make_float2(zr, zi);
+                }
+                const float2 c2 = __ldg(cq + N * N + k1 * N + lane), c3 = __ldg(cq + 2 * N * N + k1 * N + lane);
+                const float2 z2 = x[N / 2];
+                x2.x = fmaf(z2.x, c2.x, fmaf(-z2.y, c2.y, x2.x));
+                x2.y = fmaf(z2.x, c2.y, fmaf(z2.y, c2.x, x2.y));
+                x3.x = fmaf(z3.x, c3.x, fmaf(-z3.y, c3.y, x3.x));
+                x3.y = fmaf(z3.x, c3.y, fmaf(z3.y, c3.x, x3.y));
+            }
         }
         cp_async_wait_all();
         float2 *out = a.part + ((size_t)slot * a.nblk + blk) * N3 + (size_t)k1 * N * N;
         #pragma unroll
         for (int i = 0; i < N; ++i) out[i * N + lane] = acc[i];
+        if constexpr (REAL) {
+            float2 *xo = a.part_s + ((size_t)slot * a.nblk + blk) * 3 * N * N;
+            xo[N * N + k1 * N + lane] = x2;
+            xo[2 * N * N + k1 * N + lane] = x3;
+            if (k1 == N / 2) {
+                #pragma unroll 8
+                for (int i = 0; i < N; ++i) xo[i * N + lane] = xs1[i * N + lane];
+            }
+        }
     }
 }
 
@@ -357,19 +446,24 @@ __global__ void __launch_bounds__(256) k_reduce_parts(const float2 *__restrict__
     }
 }
 
-template <int N, int C, bool SC> static cudaError_t set_smem() {
-    return cudaFuncSetAttribute(k_fused<N, C, SC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)FK<N, C>::SMEM);
+template <int N, int C, bool SC, bool R> static cudaError_t set_smem() {
+    return cudaFuncSetAttribute(k_fused<N, C, SC, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)FK<N, C, R>::SMEM);
 }
 
-template <int N, int C> static cudaError_t setup_nc(int *G) {
-    using K = FK<N, C>;
-    cudaError_t e = set_smem<N, C, false>();
-    if (e == cudaSuccess) e = set_smem<N, C, true>();
-    if (e != cudaSuccess) return e;
+// Resident clusters (C > 1) or CTAs (C = 1) of the kernel that a plan of this form runs.
+// The pair form (R) exists where the lanes of a plane share a warp (32 % N == 0).
+template <int N> constexpr bool pair_form() { return 32 % N == 0; }
+
+template <int N, int C, bool R> static cudaError_t occupancy(int *G) {
+    using K = FK<N, C, R>;
+    const void *kern;
+    if constexpr (R) kern = (const void *)k_fused<N, C, false, true>;
+    else kern = (const void *)k_fused<N, C, true, false>;
+    cudaError_t e;
     if (C == 1) {
         int per_sm = 0, dev = 0, sms = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused<N, C, true>, K::THREADS, K::SMEM);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, K::THREADS, K::SMEM);
         if (e != cudaSuccess) return e;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -386,10 +480,25 @@ template <int N, int C> static cudaError_t setup_nc(int *G) {
         cfg.dynamicSmemBytes = K::SMEM;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        e = cudaOccupancyMaxActiveClusters(G, k_fused<N, C, true>, &cfg);
+        e = cudaOccupancyMaxActiveClusters(G, kern, &cfg);
         if (e != cudaSuccess) return e;
     }
     return *G > 0 ? cudaSuccess : cudaErrorInvalidConfiguration;
+}
+
+template <int N, int C> static cudaError_t setup_nc(int *G, bool real) {
+    cudaError_t e = set_smem<N, C, false, false>();
+    if (e == cudaSuccess) e = set_smem<N, C, true, false>();
+    if (e != cudaSuccess) return e;
+    if constexpr (pair_form<N>()) {
+        if (real) {
+            e = set_smem<N, C, false, true>();
+            return e == cudaSuccess ? occupancy<N, C, true>(G) : e;
+        }
+    } else {
+        if (real) return cudaErrorInvalidValue;
+    }
+    return occupancy<N, C, false>(G);
 }
 
 // Cluster sizes compiled for each N (the plan times them and keeps the fastest).
@@ -403,24 +512,25 @@ int fused_candidates(int N, int *cs) {
     return 0;
 }
 
-// Resident clusters for (N, C) (0 when the fused path does not apply).
-cudaError_t fused_setup(int N, int C, int *G) {
+// Resident clusters for (N, C) (0 when the fused path does not apply); real: the term-pair
+// kernel of BZ_DATA_REAL.
+cudaError_t fused_setup(int N, int C, int *G, bool real) {
     *G = 0;
-    if (N == 8 && C == 1) return setup_nc<8, 1>(G);
-    if (N == 16 && C == 1) return setup_nc<16, 1>(G);
-    if (N == 16 && C == 2) return setup_nc<16, 2>(G);
-    if (N == 24 && C == 2) return setup_nc<24, 2>(G);
-    if (N == 24 && C == 3) return setup_nc<24, 3>(G);
-    if (N == 32 && C == 4) return setup_nc<32, 4>(G);
-    if (N == 32 && C == 8) return setup_nc<32, 8>(G);
+    if (N == 8 && C == 1) return setup_nc<8, 1>(G, real);
+    if (N == 16 && C == 1) return setup_nc<16, 1>(G, real);
+    if (N == 16 && C == 2) return setup_nc<16, 2>(G, real);
+    if (N == 24 && C == 2) return setup_nc<24, 2>(G, real);
+    if (N == 24 && C == 3) return setup_nc<24, 3>(G, real);
+    if (N == 32 && C == 4) return setup_nc<32, 4>(G, real);
+    if (N == 32 && C == 8) return setup_nc<32, 8>(G, real);
     return cudaErrorInvalidValue;
 }
 
-template <int N, int C, bool SC> static bz_status launch_nc(const Plan &pl, const ItemArgs &a, cudaStream_t st) {
-    using K = FK<N, C>;
+template <int N, int C, bool SC, bool R> static bz_status launch_nc(const Plan &pl, const ItemArgs &a, cudaStream_t st) {
+    using K = FK<N, C, R>;
     const int G = pl.fused_G;
     if (C == 1) {
-        k_fused<N, C, SC><<<G, K::THREADS, K::SMEM, st>>>(a);
+        k_fused<N, C, SC, R><<<G, K::THREADS, K::SMEM, st>>>(a);
     } else {
         cudaLaunchConfig_t cfg = {};
         cudaLaunchAttribute attr[1];
@@ -434,19 +544,23 @@ template <int N, int C, bool SC> static bz_status launch_nc(const Plan &pl, cons
         cfg.stream = st;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        BZ_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_fused<N, C, SC>, a));
+        BZ_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_fused<N, C, SC, R>, a));
     }
     BZ_CUDA_TRY(cudaGetLastError());
     return BZ_OK;
 }
 
 template <int N, int C> static bz_status launch_sc(const Plan &pl, const ItemArgs &a, cudaStream_t st) {
-    return a.gsc ? launch_nc<N, C, true>(pl, a, st) : launch_nc<N, C, false>(pl, a, st);
+    if (a.real) {
+        if constexpr (pair_form<N>()) return a.gsc ? BZ_ERR_UNSUPPORTED : launch_nc<N, C, false, true>(pl, a, st);
+        else return BZ_ERR_UNSUPPORTED;
+    }
+    return a.gsc ? launch_nc<N, C, true, false>(pl, a, st) : launch_nc<N, C, false, false>(pl, a, st);
 }
 
 bz_status launch_fused(const Plan &pl, const ItemArgs &a, cudaStream_t st) {
     const int N = pl.N, C = pl.fused_C;
-    if (pl.precision == BZ_PREC_BF16X3) return launch_mixed(pl, a, st);
+    if (pl.precision == BZ_PREC_BF16X3) return a.real ? BZ_ERR_UNSUPPORTED : launch_mixed(pl, a, st);
     if (N == 8 && C == 1) return launch_sc<8, 1>(pl, a, st);
     if (N == 16 && C == 1) return launch_sc<16, 1>(pl, a, st);
     if (N == 16 && C == 2) return launch_sc<16, 2>(pl, a, st);
@@ -463,23 +577,39 @@ void reduce_parts(const float2 *part, int nblk, int n, double2 *acc, cudaStream_
 }
 
 // One instance (pl.fin), terms [p0, p1): one block of terms per resident cluster, then the
-// fixed-order FP64 sum of the blocks into pl.acc.
+// fixed-order FP64 sum of the blocks into pl.acc.  BZ_DATA_REAL: the input is first reduced to
+// its Hermitian, Nyquist-free part, the blocks are of term pairs [p0 / 2, p1 / 2), and the sum
+// is symmetrised at the end.
 bz_status collide_fused(Plan &pl, int p0, int p1, cudaStream_t st, int *launches) {
     const int n3 = pl.N * pl.N * pl.N;
     ItemArgs a;
     a.fin = pl.fin; a.tw = pl.tw; a.alpha = pl.alpha; a.part = pl.part; a.hg = pl.h;
     a.count = 1; a.p0 = p0; a.p1 = p1; a.M = pl.M; a.N_rho = pl.N_rho;
-    const int nt = p1 - p0;
-    a.TB = nt > 0 ? (nt + pl.fused_G - 1) / pl.fused_G : 1;
-    a.nblk = nt > 0 ? (nt + a.TB - 1) / a.TB : 0;
+    const void *src = pl.src ? pl.src : (const void *)pl.fin;
+    int src_dtype = pl.src ? pl.src_dtype : BZ_C64;
+    int nl = 0;
     bz_status s = BZ_OK;
-    if (pl.h_fp64 || pl.precision == BZ_PREC_BF16X3) {
+    if (pl.real) {
+        if ((p0 | p1) & 1) return BZ_ERR_ARG;
         tm_begin(pl, st);
-        s = h64_launch(pl.N, pl.src ? pl.src : (const void *)pl.fin, pl.src ? pl.src_dtype : BZ_C64,
-                       nullptr, nullptr, 1, pl.scr64, pl.h, st);
+        s = sym_input(pl, src, src_dtype, st);
         if (s != BZ_OK) return s;
         tm_end(pl, st, TK_OTHER);
-        if (launches) *launches += 3;
+        ++nl;
+        src = pl.fsym64;
+        src_dtype = BZ_C128;
+        a.fin = pl.fsym; a.alpha = pl.apair; a.real = 1; a.cpair = pl.cpair; a.part_s = pl.part_s;
+        a.p0 = p0 / 2; a.p1 = p1 / 2;
+    }
+    const int nt = a.p1 - a.p0;
+    a.TB = nt > 0 ? (nt + pl.fused_G - 1) / pl.fused_G : 1;
+    a.nblk = nt > 0 ? (nt + a.TB - 1) / a.TB : 0;
+    if (pl.h_fp64 || pl.precision == BZ_PREC_BF16X3) {
+        tm_begin(pl, st);
+        s = h64_launch(pl.N, src, src_dtype, nullptr, nullptr, 1, pl.scr64, pl.h, st);
+        if (s != BZ_OK) return s;
+        tm_end(pl, st, TK_OTHER);
+        nl += 3;
     } else {
         a.hg = nullptr;                                   // h formed in FP32 in the item prologue
     }
@@ -491,7 +621,16 @@ bz_status collide_fused(Plan &pl, int p0, int p1, cudaStream_t st, int *launches
     k_reduce_parts<<<(n3 + 31) / 32, 256, 0, st>>>(pl.part, a.nblk, n3, pl.acc);
     tm_end(pl, st, TK_REDUCE);
     BZ_CUDA_TRY(cudaGetLastError());
-    if (launches) *launches += 2;
+    nl += 2;
+    if (pl.real) {
+        tm_begin(pl, st);
+        reduce_parts(pl.part_s, a.nblk, 3 * pl.N * pl.N, pl.acc_s, st);
+        s = sym_output(pl, st);
+        if (s != BZ_OK) return s;
+        tm_end(pl, st, TK_OTHER);
+        nl += 2;
+    }
+    if (launches) *launches += nl;
     return BZ_OK;
 }
 

@@ -71,6 +71,15 @@ struct Plan {
     int src_dtype = BZ_C128;
     float2 *part = nullptr;         // [fused_G][N^3] per-cluster partial sums
     uint4 *wimg = nullptr;          // BZ_PREC_BF16X3: split DFT matrix (tensor-core B operand)
+    // BZ_DATA_REAL: terms 2q and 2q + 1 share one pair of transforms
+    int real = 0;
+    float2 *apair = nullptr;        // [P / 2][N^3] A = (alpha_2q - i alpha_2q+1) / 2
+    float2 *cpair = nullptr;        // [P / 2][3][N][N] C = conj B(-k), B = (alpha_2q + i alpha_2q+1) / 2, on the
+                                    // Nyquist planes (families k1 = -N/2, k2 = -N/2, k3 = -N/2), 0 elsewhere
+    float2 *part_s = nullptr;       // [fused_G][3][N][N] per-item sums X on the Nyquist planes
+    double2 *acc_s = nullptr;       // [3][N][N] their FP64 sum
+    float2 *fsym = nullptr;         // [N^3] Hermitian part of fhat, Nyquist planes zero (FP32)
+    double2 *fsym64 = nullptr;      // [N^3] the same in FP64 (source of h)
     int *dev_err = nullptr;         // device flag: a bounded wait of the fused kernel gave up
     size_t ws_bytes = 0;
     int last_launches = 0;
@@ -121,14 +130,22 @@ struct ItemArgs {
     const int *slots = nullptr;      // device [count] or null
     const int *count_dev = nullptr;  // device instance count, or null (use count)
     int count = 1, p0 = 0, p1 = 0, TB = 1, nblk = 0, M = 1, N_rho = 1;
+    int real = 0;                    // BZ_DATA_REAL: p0, p1 count term pairs, alpha = the pair table
+    const float2 *cpair = nullptr;   // BZ_DATA_REAL: [pairs][3][N][N] Nyquist-plane table C
+    float2 *part_s = nullptr;        // BZ_DATA_REAL: [slots][nblk][3][N][N] per-item sums X
 };
 int fused_candidates(int N, int *cs);
-cudaError_t fused_setup(int N, int C, int *G);
+cudaError_t fused_setup(int N, int C, int *G, bool real);
 bz_status launch_fused(const Plan &pl, const ItemArgs &a, cudaStream_t st);
 // h[slot] = IFFT(f[slot]) computed in FP64 and stored FP32 for the active slots (N <= 32).
 bz_status h64_launch(int N, const void *f, int dtype, const int *slots, const int *count_dev, int count,
                      double2 *scr, float2 *h, cudaStream_t st);
 bz_status collide_fused(Plan &pl, int p0, int p1, cudaStream_t st, int *launches);
+// bz_real.cu (BZ_DATA_REAL): the pair table from alpha (after ftable_build); pl.fsym and
+// pl.fsym64 from a c64 / c128 array; pl.acc <- V(k) + conj V(-k) off the Nyquist planes, 0 on them
+bz_status build_pair_table(Plan &pl);
+bz_status sym_input(Plan &pl, const void *f, int dtype, cudaStream_t st);
+bz_status sym_output(Plan &pl, cudaStream_t st);
 
 // bz_mixed.cu (BZ_PREC_BF16X3, N = 32)
 cudaError_t mixed_setup(int N, int *G);

@@ -490,7 +490,7 @@ cudaError_t mixed_setup(int N, int *G) {
     e = cudaOccupancyMaxActiveClusters(G, k_mixed<true>, &cfg);
     if (e != cudaSuccess) return e;
     int G2 = 0;
-    if (fused_setup(XN, XC, &G2) == cudaSuccess && G2 > *G) *G = G2;
+    if (fused_setup(XN, XC, &G2, false) == cudaSuccess && G2 > *G) *G = G2;
     cudaGetLastError();
     return *G > 0 ? cudaSuccess : cudaErrorInvalidConfiguration;
 }

@@ -1,0 +1,172 @@
+"""Real-data form (BZ_DATA_REAL) on the GPU against the oracle's real-data reading
+(`collide_real`: Hermitian part of fhat, Nyquist planes dropped).
+
+The GPU path shares one pair of 3D transforms between terms 2q and 2q + 1 and symmetrises the
+accumulated sum once per collide; the oracle evaluates every term on its own.  Bar: relative
+L-infinity error 1e-5 of max|Q| (FP32 form).  Inputs are complex and unsymmetric on purpose
+(random coefficients, shifted mixtures) so that the symmetrisation of the input is exercised.
+"""
+import numpy as np
+import pytest
+
+import bz_inputs as bi
+from oracle import kernels, spectral
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def bz():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__._libbuild().build()
+    import paper_2004_11239_gb300 as m
+    return m
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+def _real_plan(bz, N, L, R, gamma, s, N_rho, M, kernel=0, **kw):
+    return bz.bz_plan_create_ex(N, L, R, gamma, s, N_rho, M, kernel=kernel, data=bz.BZ_DATA_REAL, **kw)
+
+
+def _collide(bz, plan, fhat, p0=None, p1=None, dtype=torch.complex128):
+    f = torch.from_numpy(np.asarray(fhat)).to("cuda", dtype=dtype)
+    q = torch.empty_like(f)
+    if p0 is None:
+        bz.bz_collide(plan, f, q)
+    else:
+        bz.bz_collide_terms(plan, p0, p1, f, q)
+    torch.cuda.synchronize()
+    return q.cpu().numpy().astype(np.complex128)
+
+
+CASES = [
+    # N, gamma, s, kernel name, kernel id, N_rho, M, data
+    (8, 0.0, 0.5, "family", 0, 3, 12, "random"),
+    (16, -1.0, 0.25, "family", 0, 2, 32, "mixture"),
+    (16, 0.0, 0.0, "b5", 1, 2, 12, "random"),
+    (32, -2.0, 0.0, "b8", 2, 2, 12, "mixture"),
+    (32, 0.0, 0.5, "family", 0, 3, 12, "random"),
+]
+
+
+@pytest.mark.parametrize("N,gamma,s,name,kid,N_rho,M,data", CASES)
+def test_real_collide_matches_oracle(bz, N, gamma, s, name, kid, N_rho, M, data):
+    L = 10.0
+    R = bi.R_from_L(L)
+    fhat = bi.random_fhat(N, seed=40 + N, scale=1e-3) if data == "random" else bi.random_mixture(N, L, seed=N)
+    plan = _real_plan(bz, N, L, R, gamma, s, N_rho, M, kid)
+    info = bz.bz_plan_pipeline(plan)
+    assert info["pipeline"] == "fused"
+    got = _collide(bz, plan, fhat)
+    ref = spectral.collide_real(spectral.OraclePlan(N, L, R, gamma, kernels.Kernel(name, s), N_rho, M), fhat)
+    err = _rel(got, ref)
+    print(f"real N={N} {data} gamma={gamma} {name} s={s} P={N_rho * M} C={info['cluster']}: rel_Linf={err:.2e}")
+    assert err <= TOL
+    ny = spectral.nyquist_mask(N)
+    assert np.array_equal(spectral.mirror(got)[~ny], np.conj(got)[~ny])   # symmetrised exactly off S
+    assert got[0, 0, 0] == 0
+    plan.close()
+
+
+def test_real_term_ranges_fp32_input_and_refusals(bz):
+    N, L = 16, 10.0
+    R = bi.R_from_L(L)
+    fhat = bi.random_mixture(N, L, seed=3)
+    plan = _real_plan(bz, N, L, R, 0.0, 0.5, 2, 12)
+    op = spectral.OraclePlan(N, L, R, 0.0, kernels.Kernel("family", 0.5), 2, 12)
+    full = spectral.collide_real(op, fhat)
+    scale = np.max(np.abs(full))
+    parts = []
+    for p0, p1 in [(0, 10), (10, 24)]:
+        got = _collide(bz, plan, fhat, p0, p1)
+        err = float(np.max(np.abs(got - spectral.collide_real(op, fhat, p0, p1))) / scale)
+        print(f"real terms [{p0},{p1}): error / max|Q| = {err:.2e}")
+        assert err <= TOL
+        parts.append(got)
+    assert float(np.max(np.abs(parts[0] + parts[1] - full)) / scale) <= 2 * TOL
+    assert np.all(_collide(bz, plan, fhat, 6, 6) == 0)
+    got32 = _collide(bz, plan, fhat, dtype=torch.complex64)     # FP32 caller arrays
+    assert _rel(got32, full) <= TOL
+    f = torch.from_numpy(fhat).cuda()
+    for call in (lambda: bz.bz_collide_terms(plan, 1, 10, f, torch.empty_like(f)),      # odd bound
+                 lambda: bz.bz_batch_create(plan, 2, 0),
+                 lambda: bz.bz_collide_noalloc(plan, f, torch.empty_like(f))):
+        with pytest.raises(bz.BzError):
+            call()
+    plan.close()
+    for kw in (dict(precision=bz.BZ_PREC_BF16X3), dict(pipeline=bz.BZ_PIPE_CHUNKED), dict(conv=bz.BZ_CONV_PADDED)):
+        with pytest.raises(bz.BzError):
+            _real_plan(bz, 32 if "precision" in kw else N, L, R, 0.0, 0.5, 2, 12, **kw)
+    with pytest.raises(bz.BzError):                              # M odd: pairs would straddle radial nodes
+        _real_plan(bz, N, L, R, 0.0, 0.5, 2, 9)
+    for n in (24, 48):                                           # N must divide a warp's 32 lanes
+        with pytest.raises(bz.BzError):
+            _real_plan(bz, n, L, R, 0.0, 0.5, 1, 12)
+
+
+def test_real_rk4_matches_oracle(bz):
+    N, R = 16, 6.0
+    L = bi.L_from_R(R)
+    f0 = bi.random_mixture(N, L, seed=11, box=1.5)
+    plan = _real_plan(bz, N, L, R, 0.0, 0.5, 3, 12)
+    f = torch.from_numpy(f0.copy()).cuda()
+    t = bz.bz_step_rk(plan, f, 0.0, 0.1, 3)
+    torch.cuda.synchronize()
+    assert abs(t - 0.3) < 1e-12
+    op = spectral.OraclePlan(N, L, R, 0.0, kernels.Kernel("family", 0.5), 3, 12)
+    ref = spectral.rk4_real(op, f0, 0.1, 3)
+    err = _rel(f.cpu().numpy() - f0, ref - f0)
+    print(f"real RK4 3 steps: rel_Linf of the change = {err:.2e}")
+    assert err <= TOL
+    plan.close()
+
+
+def _summand_scale(oplan, fhat, p0, p1):
+    """max_k sum_p |alpha_p(k)| max|h| max|g_p| over terms [p0, p1) of the real band: the scale
+    the FP32 rounding of the summands grows with (a large shift r qhat leaves a term sum far
+    below its summands)."""
+    fb = spectral.real_band(fhat)
+    hm = np.max(np.abs(spectral.dft3(fb, +1)))
+    tot = 0.0
+    for p in range(p0, p1):
+        tot = tot + np.abs(oplan.alpha(p)) * hm * np.max(np.abs(spectral.dft3(fb * oplan.beta(p), +1)))
+    return float(np.max(tot))
+
+
+def test_real_form_at_full_size(bz):
+    """The bench's workload (N = 32, P = 1024, BKW at t = 6.5; Nyquist content 5e-8 of fhat_0):
+    the whole real-data collide against the oracle's reading and against the circular operator
+    itself (eq. realQ on fhat as given: the real form drops only the Nyquist content of f);
+    sampled term ranges (radial extremes) against the oracle relative to their summands, no
+    worse than the complex form on the same terms."""
+    N, R = 32, 6.0
+    L = bi.L_from_R(R)
+    fhat = bi.bkw_fhat(N, L, bi.bkw_K(6.5))
+    pr = _real_plan(bz, N, L, R, 0.0, 0.5, 32, 32)
+    pc = bz.bz_plan_create(N, L, R, 0.0, 0.5, 32, 32)
+    gr = _collide(bz, pr, fhat)
+    gc = _collide(bz, pc, fhat)
+    op = spectral.OraclePlan(N, L, R, 0.0, kernels.Kernel("family", 0.5), 32, 32)
+    err = _rel(gr, spectral.collide_real(op, fhat))
+    err_c = _rel(gr, spectral.collide(op, fhat))
+    print(f"real N=32 P=1024 BKW: rel_Linf={err:.2e} vs the real-data reading, {err_c:.2e} vs eq. realQ; "
+          f"vs the complex FP32 form {_rel(gr, gc):.2e}")
+    assert err <= TOL and err_c <= TOL
+    for p0 in (0, 500, 1014):
+        p1 = p0 + 10
+        got = _collide(bz, pr, fhat, p0, p1)
+        e_real = float(np.max(np.abs(got - spectral.collide_real(op, fhat, p0, p1))))
+        e_cplx = float(np.max(np.abs(_collide(bz, pc, fhat, p0, p1) - spectral.collide(op, fhat, p0, p1))))
+        scale = _summand_scale(op, fhat, p0, p1)
+        print(f"real N=32 terms [{p0},{p1}): err/summand scale={e_real / scale:.2e} "
+              f"(complex form {e_cplx / scale:.2e})")
+        assert e_real / scale <= TOL
+    pr.close()
+    pc.close()
