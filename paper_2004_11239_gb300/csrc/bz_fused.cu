@@ -36,8 +36,12 @@ template <int N, int C_, bool R_ = false> struct FK {
     static constexpr size_t PLANES = (size_t)PPC * N * LD * sizeof(float2);
     static constexpr size_t TILE = (size_t)PPC * N * N * sizeof(float2);   // alpha tile, h slice
     static constexpr size_t TW = (size_t)(R_ ? 6 : 3) * N * sizeof(float2);  // one term's (pair's) twiddles
-    static constexpr size_t XS1 = R_ ? (size_t)N * N * sizeof(float2) : 0;  // Nyquist plane k1 = -N/2 (pair form)
-    static constexpr size_t SMEM = PLANES + 2 * TILE + 2 * TW + XS1;
+    // pair form: h slice real (half a tile); X on the plane k1 = -N/2 and one pair's Nyquist
+    // table C (that plane, then the CTA's rows of the k2 = -N/2 and k3 = -N/2 families)
+    static constexpr size_t HS = R_ ? TILE / 2 : TILE;
+    static constexpr size_t XS1 = R_ ? (size_t)N * N * sizeof(float2) : 0;
+    static constexpr size_t CS = R_ ? (size_t)(N * N + 2 * PPC * N) * sizeof(float2) : 0;
+    static constexpr size_t SMEM = PLANES + TILE + HS + 2 * TW + XS1 + CS;
     // two CTAs per SM where registers and shared memory allow it
     static constexpr int MIN_BLOCKS = (N <= 16 || N * N / C_ <= 128) ? 2 : 1;
 };
@@ -117,11 +121,16 @@ k_fused(ItemArgs a) {
     float2 *planes = smem;                                   // [PPC][N][LD]
     float2 *sal = smem + (size_t)PPC * N * LD;               // alpha tile [PPC][N][N]
     float2 *shs = sal + (size_t)PPC * N * N;                 // h slice [PPC (j2)][N (j1)][N (j3)]
-    float2 *stw = shs + (size_t)PPC * N * N;                 // twiddles, two buffers of [TWN]
+    float *shr = (float *)shs;                               // REAL: the same, real
+    float2 *stw = (float2 *)((char *)shs + K::HS);           // twiddles, two buffers of [TWN]
     float2 *xs1 = stw + 2 * TWN;                             // REAL: X on plane k1 = -N/2, [k2][k3]
+    float2 *sc1 = xs1 + N * N;                               // REAL: C on plane k1 = -N/2 [k2][k3]
+    float2 *sc2 = sc1 + N * N;                               // REAL: C rows k1 of family k2 = -N/2 [pid][k3]
+    float2 *sc3 = sc2 + PPC * N;                             // REAL: C rows k1 of family k3 = -N/2 [pid][k2]
     const int tid = threadIdx.x;
     int rank = 0;
     if constexpr (C > 1) rank = (int)cg::this_cluster().block_rank();
+    const bool owns_nyq = rank == (N / 2) / PPC;             // REAL: this CTA holds the plane k1 = -N/2
     const int cid = blockIdx.x / C, ncl = gridDim.x / C;
     const int lane = tid % N, pid = tid / N;
     const int k1 = rank * PPC + pid;                         // plane phases
@@ -154,7 +163,11 @@ k_fused(ItemArgs a) {
         if (a.hg) {
             const float2 *hs = a.hg + (size_t)slot * N3;
             #pragma unroll 4
-            for (int j = 0; j < N; ++j) shs[((size_t)pid * N + j) * N + lane] = hs[((size_t)j * N + j2p) * N + lane];
+            for (int j = 0; j < N; ++j) {
+                const float2 hv = hs[((size_t)j * N + j2p) * N + lane];
+                if constexpr (REAL) shr[((size_t)pid * N + j) * N + lane] = hv.x;
+                else shs[((size_t)pid * N + j) * N + lane] = hv;
+            }
         } else {
             phase_a<N>(fin, nullptr, my, k1, lane);
             cluster_barrier<C>();
@@ -163,7 +176,10 @@ k_fused(ItemArgs a) {
             for (int k = 0; k < N; ++k) x[k] = ld_dsmem(pen[k / PPC] + (uint32_t)(k % PPC) * PLANE_BYTES);
             fft_inplace<N, +1>(x);                            // k1 -> j1
             #pragma unroll
-            for (int j = 0; j < N; ++j) shs[((size_t)pid * N + j) * N + lane] = x[j];
+            for (int j = 0; j < N; ++j) {
+                if constexpr (REAL) shr[((size_t)pid * N + j) * N + lane] = x[j].x;
+                else shs[((size_t)pid * N + j) * N + lane] = x[j];
+            }
             cluster_barrier<C>();                             // planes free again in every CTA
         }
 
@@ -186,6 +202,19 @@ k_fused(ItemArgs a) {
                 const char *ga = (const char *)(a.alpha + ((size_t)p * N + (size_t)rank * PPC) * N * N);
                 char *sa = (char *)sal;
                 for (int c = tid; c < (int)(K::TILE / 16); c += T) cp_async16(sa + 16 * c, ga + 16 * c);
+                if constexpr (REAL) {                         // this pair's Nyquist table rows
+                    const float2 *cq = a.cpair + (size_t)p * 3 * N * N;
+                    constexpr int ROW16 = PPC * N * (int)sizeof(float2) / 16;
+                    if (tid < ROW16) {
+                        cp_async16((char *)sc2 + 16 * tid, (const char *)(cq + N * N + rank * PPC * N) + 16 * tid);
+                    } else if (tid < 2 * ROW16) {
+                        const int c = tid - ROW16;
+                        cp_async16((char *)sc3 + 16 * c, (const char *)(cq + 2 * N * N + rank * PPC * N) + 16 * c);
+                    }
+                    if (owns_nyq)
+                        for (int c = tid; c < N * N * (int)sizeof(float2) / 16; c += T)
+                            cp_async16((char *)sc1 + 16 * c, (const char *)cq + 16 * c);
+                }
                 cp_async_commit();
             }
             fetch_tw(p + 1 < t1 ? p + 1 : -1, buf ^ 1);
@@ -203,7 +232,7 @@ k_fused(ItemArgs a) {
             if constexpr (REAL) {
                 #pragma unroll
                 for (int j = 0; j < N; ++j) {                 // h is real
-                    const float hv = shs[((size_t)pid * N + j) * N + lane].x;
+                    const float hv = shr[((size_t)pid * N + j) * N + lane];
                     x[j].x *= hv;
                     x[j].y *= hv;
                 }
@@ -239,11 +268,10 @@ k_fused(ItemArgs a) {
                 }
             }
             if constexpr (REAL) {
-                const float2 *cq = a.cpair + (size_t)p * 3 * N * N;
                 if (k1 == N / 2) {                            // whole plane (warp-uniform)
                     #pragma unroll
                     for (int i = 0; i < N; ++i) {
-                        const float2 c = __ldg(cq + i * N + lane);
+                        const float2 c = sc1[i * N + lane];
                         float2 v = xs1[i * N + lane];
                         v.x = fmaf(x[i].x, c.x, fmaf(-x[i].y, c.y, v.x));
                         v.y = fmaf(x[i].x, c.y, fmaf(x[i].y, c.x, v.y));
@@ -257,7 +285,7 @@ k_fused(ItemArgs a) {
                     const float zi = __shfl_sync(0xffffffffu, x[i].y, N / 2, N);
                     if (i == lane) z3 = make_float2(zr, zi);
                 }
-                const float2 c2 = __ldg(cq + N * N + k1 * N + lane), c3 = __ldg(cq + 2 * N * N + k1 * N + lane);
+                const float2 c2 = sc2[pid * N + lane], c3 = sc3[pid * N + lane];
                 const float2 z2 = x[N / 2];
                 x2.x = fmaf(z2.x, c2.x, fmaf(-z2.y, c2.y, x2.x));
                 x2.y = fmaf(z2.x, c2.y, fmaf(z2.y, c2.x, x2.y));
