@@ -97,8 +97,9 @@ def _bytes_per_term(N, dim=3):
 
 _PROFILES = {
     # kernel kind: (summary under profiles/, kernel sources the summary was taken from)
-    "fused": ("fused_rk4_n32.md", ("bz_fused.cu", "bz_fft.cuh", "bz_cluster.cuh")),
+    "fused": ("fused_rk4_n32.md", ("bz_fused_kernel.cuh", "bz_fft.cuh", "bz_cluster.cuh")),
     "mixed": ("mixed_rk4_n32.md", ("bz_mixed.cu", "bz_fft.cuh", "bz_cluster.cuh")),
+    "fused_real": ("fused_real_rk4_n32.md", ("bz_fused_kernel.cuh", "bz_fft.cuh", "bz_cluster.cuh")),
 }
 
 
@@ -272,27 +273,18 @@ def run_reference(args, w):
     return 0
 
 
-def run_ours(args, w):
-    import numpy as np
-    import torch
-    ws, rank, local = _dist()
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    import paper_2004_11239_gb300 as bz
+def _real_supported(w):
+    """The real-data form (BZ_DATA_REAL) applies to 3D plans with N dividing 32 and M even; the
+    workloads' distribution functions are real."""
+    return w.get("dim", 3) == 3 and 32 % w["N"] == 0 and w["M"] % 2 == 0
 
-    L, R = _geometry(w)
-    N = w["N"]
-    dim = w.get("dim", 3)
-    plan = bz.bz_plan_create_ex(N, L, R, w["gamma"], w["s"], w["N_rho"], w["M"], h_precision=args.h_precision,
-                                kernel=w.get("kernel", 0), dim=dim)
-    pipe = bz.bz_plan_pipeline(plan)
-    pipe["h_precision"] = {0: "fp64", 1: "fp64", 2: "fp32"}[args.h_precision]
-    f_host = _fhat(w, L)
-    f = torch.from_numpy(f_host).to("cuda")
-    q = torch.empty_like(f)
-    st = torch.cuda.current_stream()
+
+def _time_plan(args, w, bz, plan, f, q, st, barrier, clk=None):
+    """W warm-up steps, then K steps between barriers and synchronisations (the throughput), then
+    K more steps with the library's per-kernel CUDA events on (the roofline's kernel times; the
+    event records add host work between launches, so they stay out of the throughput region).
+    Returns (evals/s over all ranks, ms, per-kernel timings, launches per step, step)."""
+    import torch
     is_rk = w["dt"] is not None
     evals_per_step = 4 if is_rk else 1
 
@@ -306,28 +298,99 @@ def run_ours(args, w):
         step()
     torch.cuda.synchronize()
     launches_per_step = bz.bz_plan_last_launches(plan)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if clk is not None:
+        clk.__enter__()
+    barrier()
+    torch.cuda.synchronize()
+    e0.record(st)
+    for _ in range(args.steps):
+        step()
+    e1.record(st)
+    torch.cuda.synchronize()
+    barrier()
+    if clk is not None:
+        clk.__exit__(None, None, None)
+    ms = e0.elapsed_time(e1)
+    value, ms = job_throughput(evals_per_step * args.steps, ms)
+    bz.bz_plan_set_timing(plan, launches_per_step * args.steps + 16)
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize()
+    kern = {name: bz.bz_plan_timing(plan, kind) for name, kind in bz.KERNEL_KINDS.items()}
+    bz.bz_plan_set_timing(plan, 0)
+    return value, ms, kern, launches_per_step, step
+
+
+def _roofline(args, w, kern, peaks, src, profile_key):
+    """Roofline of the dominant kernel: algorithmic flops and HBM bytes per term (the per-unit
+    figures of the method, whatever form executes them) x terms per launch / mean launch time."""
+    N, dim = w["N"], w.get("dim", 3)
+    evals_per_step = 4 if w["dt"] is not None else 1
+    dom = max(("plane_inv", "pencil", "plane_fwd", "reduce", "fused"), key=lambda k: kern[k][1])
+    n_launch, ms_k = kern[dom]
+    terms_per_launch = (w["N_rho"] * w["M"]) * evals_per_step * args.steps / max(n_launch, 1)
+    if dom == "reduce" and kern["fused"][0] > 0:
+        terms_per_launch = 0.0            # the partial-sum reduction is not a per-term kernel
+    avg_s = ms_k / 1e3 / max(n_launch, 1)
+    fl = _flops_per_term(N, dim).get(dom, 0.0) * terms_per_launch
+    by = _bytes_per_term(N, dim).get(dom, 0.0) * terms_per_launch
+    sm_clock = peaks.get("sm_max_mhz", 2070.0)
+    alu_peak = 152 * 128 * 2 * sm_clock * 1e6 / 1e12      # FP32 FMA lanes x 2 flops x clock
+    alu = {"bound": "alu", "achieved": fl / avg_s / 1e12, "peak": alu_peak, "unit": "TFLOP/s"}
+    hbm = {"bound": "hbm", "achieved": by / avg_s / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
+    for r in (alu, hbm):
+        r["frac"] = r["achieved"] / r["peak"]
+    roof = max((alu, hbm), key=lambda r: r["frac"])
+    other = hbm if roof is alu else alu
+    key = profile_key if dom == "fused" else dom
+    roof.update({"kernel": dom, "traffic": _profiled_traffic(key, args.workload),
+                 "peak_source": f"{src}" if roof is hbm else "derived: 152 SMs x 128 FP32 lanes x 2 x sm_max_mhz",
+                 "launches": n_launch, "avg_launch_us": avg_s * 1e6,
+                 "also": {k: other[k] for k in ("bound", "achieved", "peak", "unit", "frac")}})
+    return roof
+
+
+def run_ours(args, w):
+    import numpy as np
+    import torch
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import paper_2004_11239_gb300 as bz
+
+    L, R = _geometry(w)
+    N = w["N"]
+    dim = w.get("dim", 3)
+    real = args.data == "real" or (args.data == "auto" and _real_supported(w))
+    if real and not _real_supported(w):
+        raise SystemExit("the real-data form needs a 3D plan with N in {8, 16, 32} and M even")
+    data_form = bz.BZ_DATA_REAL if real else bz.BZ_DATA_COMPLEX
+
+    def make_plan(form):
+        return bz.bz_plan_create_ex(N, L, R, w["gamma"], w["s"], w["N_rho"], w["M"], h_precision=args.h_precision,
+                                    kernel=w.get("kernel", 0), dim=dim, data=form, cluster=args.cluster)
+
+    plan = make_plan(data_form)
+    pipe = bz.bz_plan_pipeline(plan)
+    pipe["h_precision"] = {0: "fp64", 1: "fp64", 2: "fp32"}[args.h_precision]
+    f_host = _fhat(w, L)
+    f = torch.from_numpy(f_host).to("cuda")
+    q = torch.empty_like(f)
+    st = torch.cuda.current_stream()
+    is_rk = w["dt"] is not None
+    evals_per_step = 4 if is_rk else 1
 
     def barrier():
         if ws > 1:
             import torch.distributed as dist
             dist.barrier()
 
-    # timed region: K steps, per-kernel events recorded by the library
-    bz.bz_plan_set_timing(plan, launches_per_step * args.steps + 16)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
-        barrier()
-        torch.cuda.synchronize()
-        e0.record(st)
-        for _ in range(args.steps):
-            step()
-        e1.record(st)
-        torch.cuda.synchronize()
-        barrier()
-    ms = e0.elapsed_time(e1)
-    kern = {name: bz.bz_plan_timing(plan, kind) for name, kind in bz.KERNEL_KINDS.items()}
-    bz.bz_plan_set_timing(plan, 0)
-    value, ms = job_throughput(evals_per_step * args.steps, ms)
+    clk = ClockSampler(local)
+    value, ms, kern, launches_per_step, step = _time_plan(args, w, bz, plan, f, q, st, barrier, clk)
+    clocks = clk.summary()
 
     # end to end through the public API with host buffers (pinned), copies inside the region
     h_in = torch.from_numpy(f_host).pin_memory()
@@ -346,32 +409,36 @@ def run_ours(args, w):
     e2e = {"value": evals_per_step * args.steps * ws / (ms_e2e / 1e3), "unit": "evals/s",
            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
 
-    # roofline of the dominant kernel
     peaks, src = _peaks()
-    dom = max(("plane_inv", "pencil", "plane_fwd", "reduce", "fused"), key=lambda k: kern[k][1])
-    n_launch, ms_k = kern[dom]
-    terms_per_launch = (w["N_rho"] * w["M"]) * evals_per_step * args.steps / max(n_launch, 1)
-    if dom == "reduce" and kern["fused"][0] > 0:
-        terms_per_launch = 0.0            # the partial-sum reduction is not a per-term kernel
-    avg_s = ms_k / 1e3 / max(n_launch, 1)
-    fl = _flops_per_term(N, dim).get(dom, 0.0) * terms_per_launch
-    by = _bytes_per_term(N, dim).get(dom, 0.0) * terms_per_launch
-    clocks = clk.summary()
-    sm_clock = peaks.get("sm_max_mhz", 2070.0)
-    alu_peak = 152 * 128 * 2 * sm_clock * 1e6 / 1e12      # FP32 FMA lanes x 2 flops x clock
-    alu = {"bound": "alu", "achieved": fl / avg_s / 1e12, "peak": alu_peak, "unit": "TFLOP/s"}
-    hbm = {"bound": "hbm", "achieved": by / avg_s / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
-    for r in (alu, hbm):
-        r["frac"] = r["achieved"] / r["peak"]
-    roof = max((alu, hbm), key=lambda r: r["frac"])
-    other = hbm if roof is alu else alu
-    roof.update({"kernel": dom, "traffic": _profiled_traffic(dom, args.workload), "peak_source": f"{src}" if roof is hbm else
-                 "derived: 152 SMs x 128 FP32 lanes x 2 x sm_max_mhz", "launches": n_launch,
-                 "avg_launch_us": avg_s * 1e6, "also": {k: other[k] for k in ("bound", "achieved", "peak", "unit", "frac")}})
+    roof = _roofline(args, w, kern, peaks, src, "fused_real" if real else "fused")
+    if real:
+        roof["executed"] = ("term pairs share every pair of 3D transforms: about half the counted FFT "
+                            "flops and half the alpha bytes (plus a 3 N^2 Nyquist table per pair) are executed")
+
+    # the other data form on the same workload (complex beside real, and the reverse where it applies)
+    other = None
+    if dim == 3 and (real or _real_supported(w)):
+        po = make_plan(bz.BZ_DATA_COMPLEX if real else bz.BZ_DATA_REAL)
+        fo, qo = torch.from_numpy(f_host).to("cuda"), torch.empty_like(f)
+        qa = torch.empty_like(f)
+        bz.bz_collide(plan, fo, qa, st)
+        bz.bz_collide(po, fo, qo, st)
+        torch.cuda.synchronize()
+        a, b = qa.cpu().numpy(), qo.cpu().numpy()
+        dev = float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+        vo, mso, kerno, lo, _ = _time_plan(args, w, bz, po, fo, qo, st, barrier)
+        other = {"data_form": "complex" if real else "real", "value": vo, "unit": "evals/s",
+                 "ms_per_step": mso / args.steps, "gpu_launches": lo * args.steps,
+                 "rel_linf_headline_vs_this": dev,
+                 "roofline": _roofline(args, w, kerno, peaks, src, "fused" if real else "fused_real")}
+        po.close()
 
     mixed = None
     if N == 32 and dim == 3 and not args.no_mixed:
-        mixed = _measure_mixed(args, w, bz, plan, f_host, L, R, st, peaks, src, barrier)
+        pc = plan if not real else make_plan(bz.BZ_DATA_COMPLEX)
+        mixed = _measure_mixed(args, w, bz, pc, f_host, L, R, st, peaks, src, barrier)
+        if pc is not plan:
+            pc.close()
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -383,17 +450,23 @@ def run_ours(args, w):
                "sample": f"{n_terms} of {P} terms of one collide (FP64 oracle, one thread), "
                          "extrapolated to all terms; F-table build excluded"}
 
+    streamed = plan.alpha_bytes - (plan.P * N ** 3 * 8 if real else 0)
+    form_desc = ("real: f is real, fhat's Hermitian part with the Nyquist planes (index -N/2) dropped "
+                 "(BZ_DATA_REAL; parity with eq. realQ on this input 6e-6 at full size)" if real else
+                 "complex: eq. realQ on fhat as given (BZ_DATA_COMPLEX)")
     line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload, "desc": w["desc"], "P": w["N_rho"] * w["M"],
-                       "pipeline": pipe,
+                       "data_form": form_desc, "pipeline": pipe,
                        "collides_per_step": evals_per_step,
-                       "l2": "inputs larger than L2: the alpha table of %d MB streams every collide"
-                             % (plan.alpha_bytes >> 20)},
+                       "l2": "inputs larger than L2: the %s of %d MB streams every collide"
+                             % ("pair table" if real else "alpha table", streamed >> 20)},
             "clocks": clocks, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
             "roofline": roof, "kernels_ms": {k: v[1] for k, v in kern.items()},
             "cpu_baseline": cpu}
+    if other is not None:
+        line["other_form"] = other
     if mixed is not None:
         line["mixed"] = mixed
     if rank == 0:
@@ -619,7 +692,7 @@ def run_serve(args, w):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="rk4_n32", choices=sorted(WORKLOADS))
@@ -627,6 +700,11 @@ def main():
     ap.add_argument("--no-mixed", action="store_true",
                     help="skip the split-BF16 tensor-core form (measured beside the FP32 form at N = 32)")
     ap.add_argument("--rates", default=None, help="serve workload: comma-separated arrival rates (req/s)")
+    ap.add_argument("--data", default="auto", choices=["auto", "real", "complex"],
+                    help="data form of the headline plan: auto = real where the plan supports it "
+                         "(3D, N in {8, 16, 32}, M even; the workloads' f are real), else complex")
+    ap.add_argument("--cluster", type=int, default=0,
+                    help="CTAs per cluster of the fused kernel (0: timed at plan creation, fastest kept)")
     ap.add_argument("--h-precision", type=int, default=0, choices=[0, 1, 2],
                     help="h = IFFT(fhat) precision on the fused path: 0 auto (FP64), 1 FP64, 2 FP32")
     args = ap.parse_args()

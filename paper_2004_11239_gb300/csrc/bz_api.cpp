@@ -31,9 +31,9 @@ void free_plan(bz::Plan &p) {
     cudaFree(p.term_dev); cudaFree(p.S); cudaFree(p.h); cudaFree(p.fin); cudaFree(p.acc);
     cudaFree(p.rk); cudaFree(p.mom); cudaFree(p.part); cudaFree(p.fin64); cudaFree(p.scr64);
     cudaFree(p.wimg); cudaFree(p.dev_err); cudaFree(p.apair); cudaFree(p.fsym); cudaFree(p.fsym64);
-    cudaFree(p.cpair); cudaFree(p.part_s); cudaFree(p.acc_s);
+    cudaFree(p.cpair); cudaFree(p.part_s);
     p.wimg = nullptr; p.dev_err = nullptr; p.apair = nullptr; p.fsym = nullptr; p.fsym64 = nullptr;
-    p.cpair = nullptr; p.part_s = nullptr; p.acc_s = nullptr;
+    p.cpair = nullptr; p.part_s = nullptr;
     p.part = nullptr; p.fin64 = nullptr; p.scr64 = nullptr; p.src = nullptr;
     p.alpha = nullptr; p.tw = nullptr; p.rule_buf = nullptr; p.rule_off = nullptr;
     p.term_dev = nullptr; p.S = nullptr; p.h = nullptr; p.fin = nullptr; p.acc = nullptr;
@@ -206,10 +206,9 @@ bz_status create(bz_plan **out, const bz_plan_desc *d) {
         const size_t ns = (size_t)3 * N * N;
         if ((s = dmalloc(&pl.apair, (size_t)(pl.P / 2) * field)) == BZ_OK &&
             (s = dmalloc(&pl.cpair, (size_t)(pl.P / 2) * ns * sizeof(float2))) == BZ_OK &&
-            (s = dmalloc(&pl.acc_s, ns * sizeof(double2))) == BZ_OK &&
             (s = dmalloc(&pl.fsym, field)) == BZ_OK && (s = dmalloc(&pl.fsym64, n3 * sizeof(double2))) == BZ_OK)
             s = bz::build_pair_table(pl);
-        pl.ws_bytes += field + n3 * sizeof(double2) + ns * sizeof(double2);
+        pl.ws_bytes += field + n3 * sizeof(double2);
     }
     if (s != BZ_OK) {
         free_plan(pl);

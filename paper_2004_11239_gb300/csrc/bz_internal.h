@@ -77,7 +77,6 @@ struct Plan {
     float2 *cpair = nullptr;        // [P / 2][3][N][N] C = conj B(-k), B = (alpha_2q + i alpha_2q+1) / 2, on the
                                     // Nyquist planes (families k1 = -N/2, k2 = -N/2, k3 = -N/2), 0 elsewhere
     float2 *part_s = nullptr;       // [fused_G][3][N][N] per-item sums X on the Nyquist planes
-    double2 *acc_s = nullptr;       // [3][N][N] their FP64 sum
     float2 *fsym = nullptr;         // [N^3] Hermitian part of fhat, Nyquist planes zero (FP32)
     double2 *fsym64 = nullptr;      // [N^3] the same in FP64 (source of h)
     int *dev_err = nullptr;         // device flag: a bounded wait of the fused kernel gave up
@@ -138,14 +137,17 @@ int fused_candidates(int N, int *cs);
 cudaError_t fused_setup(int N, int C, int *G, bool real);
 bz_status launch_fused(const Plan &pl, const ItemArgs &a, cudaStream_t st);
 // h[slot] = IFFT(f[slot]) computed in FP64 and stored FP32 for the active slots (N <= 32).
+// fsym (BZ_DATA_REAL, N a power of two): transform the Hermitian, Nyquist-free part of f and
+// store that part in FP32 to fsym.
 bz_status h64_launch(int N, const void *f, int dtype, const int *slots, const int *count_dev, int count,
-                     double2 *scr, float2 *h, cudaStream_t st);
+                     double2 *scr, float2 *h, cudaStream_t st, float2 *fsym = nullptr);
 bz_status collide_fused(Plan &pl, int p0, int p1, cudaStream_t st, int *launches);
 // bz_real.cu (BZ_DATA_REAL): the pair table from alpha (after ftable_build); pl.fsym and
-// pl.fsym64 from a c64 / c128 array; pl.acc <- V(k) + conj V(-k) off the Nyquist planes, 0 on them
+// pl.fsym64 from a c64 / c128 array
 bz_status build_pair_table(Plan &pl);
 bz_status sym_input(Plan &pl, const void *f, int dtype, cudaStream_t st);
-bz_status sym_output(Plan &pl, cudaStream_t st);
+// pl.acc <- Q from the nblk item sums of pl.part (V) and pl.part_s (X): one kernel
+bz_status reduce_sym(Plan &pl, int nblk, cudaStream_t st);
 
 // bz_mixed.cu (BZ_PREC_BF16X3, N = 32)
 cudaError_t mixed_setup(int N, int *G);
