@@ -238,6 +238,31 @@ def random_fhat(N: int, seed: int, scale: float = 1.0) -> np.ndarray:
     return scale * (re + 1j * im)
 
 
+def inhom_cells(N: int, L: float, nx: int, Lx: float, eps: float = 0.2) -> np.ndarray:
+    """[nx][N^3] coefficients of f(x_c, v) = (1 + eps cos(2 pi x_c / Lx)) (M(v - u_c e1) + M(v + u_c e1)) / 2,
+    x_c = c Lx / nx, u_c = 1 + 0.5 sin(2 pi x_c / Lx), unit-temperature Maxwellians M: a density
+    wave on a two-stream velocity profile whose separation varies along x."""
+    out = np.empty((nx, N, N, N), dtype=np.complex128)
+    for c in range(nx):
+        x = c * Lx / nx
+        rho = 1.0 + eps * math.cos(2 * math.pi * x / Lx)
+        u = 1.0 + 0.5 * math.sin(2 * math.pi * x / Lx)
+        out[c] = gaussian_mixture_fhat(N, L, [0.5 * rho, 0.5 * rho], [(u, 0.0, 0.0), (-u, 0.0, 0.0)], [1.0, 1.0])
+    return out
+
+
+def drifting_wave_samples(N: int, L: float, nx: int, Lx: float, eps: float, u: float, T: float) -> np.ndarray:
+    """[nx][N^3] coefficients from the node values of f(x_c, v) = (1 + eps cos(2 pi x_c / Lx)) M_T(v - u e1)
+    (M_T the Maxwellian of temperature T), taken by the library FFT of the samples."""
+    v = grid(N, L)
+    V1, V2, V3 = np.meshgrid(v, v, v, indexing="ij")
+    M = (2 * math.pi * T) ** -1.5 * np.exp(-((V1 - u) ** 2 + V2 ** 2 + V3 ** 2) / (2 * T))
+    out = np.empty((nx, N, N, N), dtype=np.complex128)
+    for c in range(nx):
+        out[c] = _samples_to_fhat((1.0 + eps * math.cos(2 * math.pi * c / nx)) * M, L)
+    return out
+
+
 def poisson_arrivals(n: int, rate: float, seed: int) -> np.ndarray:
     """Arrival times of a Poisson process (exponential gaps from SplitMix64)."""
     u = SplitMix64(seed).uniform(n)
