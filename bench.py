@@ -41,6 +41,11 @@ WORKLOADS = {
     "single_2d_n64": dict(N=64, N_rho=64, M=32, gamma=0.0, s=0.0, R=6.0, dt=None, data="bkw2d", dim=2,
                           kernel=6, desc="single 2D collide in the Table 1 setting: N=64, N_rho=64, M=32 circle "
                                          "points, kernel b4, R=6, L=(3+sqrt2)R/4, BKW samples at t=0"),
+    "inhom_n16": dict(N=16, N_rho=16, M=12, gamma=0.0, s=0.5, R=6.0, dt=0.01, nx=32, Lx=4.0, data="inhom",
+                      desc="spatially inhomogeneous df/dt + v1 df/dx = Q(f,f): 32 cells on a periodic x-interval "
+                           "of length 4, N=16, N_rho=16, M=12 (icosahedron), gamma=0, s=0.5, R=6, L=(3+sqrt2)R/4; "
+                           "one Strang step (free streaming dt/2, RK4 collision in every cell, free streaming dt/2) "
+                           "per bench step, dt=0.01; density wave on a two-stream profile"),
     "batch_4096": dict(N=None, N_rho=None, M=32, gamma=None, s=None, R=None, L=10.0, dt=0.01,
                        data="mixtures", desc="4096 instances (3072 at N=16, 1024 at N=32), N_rho=N, "
                        "M=32, gamma in {0,-1}, s in {0.25,0.5,0.75}, two-Maxwellian mixtures, "
@@ -69,6 +74,8 @@ def _fhat(w, L):
         return bi.bigaussian_noise_c3(N, L)
     if w["data"] == "bkw2d":
         return bi.bkw2d_fhat_samples(N, L, bi.bkw2d_K(0.0))
+    if w["data"] == "inhom":
+        return bi.inhom_cells(N, L, w["nx"], w["Lx"])[0]      # one cell (the oracle's collide rate)
     return bi.two_maxwellians_c1(N, L)
 
 
@@ -617,6 +624,84 @@ def run_batch(args, w):
     return 0
 
 
+def run_inhom(args, w):
+    """The inhomogeneous workload: Strang steps over nx cells (free streaming and the batched RK4
+    collision of every cell); evals = 4 collides per cell per step."""
+    import numpy as np
+    import torch
+    import bz_inputs as bi
+    import paper_2004_11239_gb300 as bz
+    torch.cuda.set_device(0)
+    L, R = _geometry(w)
+    N, nx, Lx = w["N"], w["nx"], w["Lx"]
+    plan = bz.bz_plan_create(N, L, R, w["gamma"], w["s"], w["N_rho"], w["M"])
+    batch = bz.bz_batch_create(plan, nx, 0)
+    f_host = bi.inhom_cells(N, L, nx, Lx)
+    fd = torch.from_numpy(f_host).cuda()
+    st = torch.cuda.current_stream()
+
+    def step():
+        bz.bz_inhom_step(batch, nx, Lx, fd, w["dt"], 1, st)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    launches = bz.bz_batch_last_launches(batch)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        torch.cuda.synchronize()
+        e0.record(st)
+        for _ in range(args.steps):
+            step()
+        e1.record(st)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    # the free-streaming share: the same number of transport calls alone (two per step)
+    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2.record(st)
+    for _ in range(args.steps):
+        bz.bz_transport_x(N, L, nx, Lx, fd, 0.5 * w["dt"], st)
+        bz.bz_transport_x(N, L, nx, Lx, fd, 0.5 * w["dt"], st)
+    e3.record(st)
+    torch.cuda.synchronize()
+    ms_tr = e2.elapsed_time(e3)
+    # end to end: host cells copied in and out around every step
+    h_in = torch.from_numpy(f_host).pin_memory()
+    h_out = torch.empty_like(h_in).pin_memory()
+    e4, e5 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e4.record(st)
+    for _ in range(args.steps):
+        fd.copy_(h_in, non_blocking=True)
+        step()
+        h_out.copy_(fd, non_blocking=True)
+    e5.record(st)
+    torch.cuda.synchronize()
+    ms_e2e = e4.elapsed_time(e5)
+    evals = 4 * nx * args.steps
+    nbytes = fd.numel() * fd.element_size()
+    flops = 4 * nx * plan.P * _flops_per_term(N)["fused"] * args.steps
+    peaks, _ = _peaks()
+    alu_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    achieved = flops / (ms / 1e3) / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak,
+            "kernel": "whole step (k_fused dominant)", "traffic": None,
+            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x sm_max_mhz",
+            "work": "30 N^3 log2 N + 20 N^3 flops per term, 4 collides per cell per step"}
+    line = {"metric": METRIC, "value": evals / (ms / 1e3), "unit": "evals/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": {"workload": args.workload, "desc": w["desc"], "cells": nx,
+                                            "P": plan.P, "transport_ms_per_step": ms_tr / args.steps,
+                                            "transport_share": ms_tr / ms},
+            "clocks": clk.summary(), "gpu_launches": launches * args.steps, "roofline": roof,
+            "e2e": {"value": evals / (ms_e2e / 1e3), "unit": "evals/s", "h2d_bytes_per_step": nbytes,
+                    "d2h_bytes_per_step": nbytes}}
+    print(json.dumps(line))
+    batch.close()
+    plan.close()
+    return 0
+
+
 def run_serve(args, w):
     """Seeded Poisson trace through bz_submit / bz_poll; latency percentiles and throughput."""
     import numpy as np
@@ -715,6 +800,8 @@ def main():
         return run_serve(args, w)
     if args.impl == "reference":
         return run_reference(args, w)
+    if args.workload == "inhom_n16":
+        return run_inhom(args, w)
     return run_ours(args, w)
 
 

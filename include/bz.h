@@ -281,6 +281,26 @@ bz_status bz_batch_step_rk(bz_batch *batch, int count, const int *slots, void *f
 int bz_batch_last_launches(const bz_batch *batch);
 
 /* ---------------------------------------------------------------------------------------
+ * Spatially inhomogeneous coupling: df/dt + v_1 df/dx = Q(f, f) on a periodic interval
+ * [0, Lx) of nx cells, x_c = c Lx / nx, with the homogeneous operator as a black box per cell
+ * (the paper's closing remark, Sec. 6; the splitting is this library's reading).  Cell arrays
+ * are [nx][N][N][N] coefficients (c64 or c128, device), cell-major.
+ * --------------------------------------------------------------------------------------- */
+
+/* Free streaming df/dt + v_1 df/dx = 0 over time t (any sign), in place: exact at the velocity
+ * nodes v_j = -L + 2 L j / N and spectral in x (x-DFT over the cells, phase
+ * exp(-2 pi i kappa v_1 t / Lx) with the signed x-mode kappa, -nx/2 included, inverse x-DFT),
+ * computed in FP64 along the k1 axis only (the phase depends on v_1 alone).  N and nx in
+ * {8, 16, 24, 32}; BZ_ERR_UNSUPPORTED otherwise. */
+bz_status bz_transport_x(int N, double L, int nx, double Lx, void *fcells, int dtype, double t, void *stream);
+
+/* nsteps Strang steps of size dt: free streaming dt/2, one RK4 step (Sec. 5.2) of the collision
+ * in every cell (the batch's slots 0 .. nx - 1, whose plan gives N and L), free streaming dt/2
+ * (the half steps between two steps are taken as one).  nx <= the batch's capacity. */
+bz_status bz_inhom_step(bz_batch *batch, int nx, double Lx, void *fcells, int dtype, double dt, int nsteps,
+                        void *stream);
+
+/* ---------------------------------------------------------------------------------------
  * Serving: a worker thread runs homogeneous relaxation solves (RK4 on d fhat/dt = Q) for
  * submitted requests with continuous batching.  Each iteration admits queued requests in
  * arrival order while the HBM budget and group slots allow, advances every active request

@@ -24,6 +24,7 @@ __all__ = [
     "bz_quadrature", "bz_kernel_constants",
     "bz_batch_create", "bz_batch_destroy", "bz_batch_set_gamma", "bz_batch_collide", "bz_batch_step_rk",
     "bz_batch_last_launches", "bz_server_create", "bz_submit", "bz_poll", "bz_server_stats",
+    "bz_transport_x", "bz_inhom_step",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -103,6 +104,8 @@ def _load():
         "bz_batch_set_gamma": [vp, c_int, c_double],
         "bz_batch_collide": [vp, c_int, ip, vp, vp, c_int, vp],
         "bz_batch_step_rk": [vp, c_int, ip, vp, c_int, c_double, c_int, vp],
+        "bz_transport_x": [c_int, c_double, c_int, c_double, vp, c_int, c_double, vp],
+        "bz_inhom_step": [vp, c_int, c_double, vp, c_int, c_double, c_int, vp],
         "bz_server_create": [ctypes.POINTER(vp), c_size, c_int, c_int],
         "bz_submit": [vp, ctypes.POINTER(bz_request), ctypes.POINTER(ctypes.c_uint64)],
         "bz_poll": [vp, ctypes.c_uint64, ctypes.POINTER(bz_result), vp, c_int],
@@ -429,6 +432,24 @@ def bz_batch_step_rk(batch: Batch, slots, fhat, dt: float, nsteps: int, stream=N
 
 def bz_batch_last_launches(batch: Batch) -> int:
     return lib.bz_batch_last_launches(batch.handle)
+
+
+def _dev_cells(t, nx: int, N: int):
+    if not t.is_cuda or not t.is_contiguous() or t.numel() != nx * N ** 3:
+        raise ValueError(f"expected a contiguous CUDA tensor of nx * N^3 = {nx * N ** 3} complex values")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def bz_transport_x(N: int, L: float, nx: int, Lx: float, fcells, t: float, stream=None):
+    """Free streaming of the [nx][N^3] cells over time t, in place."""
+    _check(lib.bz_transport_x(N, L, nx, Lx, _dev_cells(fcells, nx, N), _dtype(fcells), t, _stream(stream)),
+           "bz_transport_x")
+
+
+def bz_inhom_step(batch: Batch, nx: int, Lx: float, fcells, dt: float, nsteps: int, stream=None):
+    """nsteps Strang steps (free streaming, RK4 collision per cell) of the [nx][N^3] cells, in place."""
+    _check(lib.bz_inhom_step(batch.handle, nx, Lx, _dev_cells(fcells, nx, batch.plan.N), _dtype(fcells), dt,
+                             nsteps, _stream(stream)), "bz_inhom_step")
 
 
 class Server:

@@ -378,6 +378,32 @@ bz_status bz_batch_step_rk(bz_batch *batch, int count, const int *slots, void *f
     return BZ_OK;
 }
 
+bz_status bz_inhom_step(bz_batch *batch, int nx, double Lx, void *fcells, int dtype, double dt, int nsteps,
+                        void *stream) {
+    if (!batch || !fcells || nx < 1 || nx > batch->capacity || !(Lx > 0) || nsteps < 0 || !std::isfinite(dt))
+        return BZ_ERR_ARG;
+    if (dtype != BZ_C64 && dtype != BZ_C128) return BZ_ERR_ARG;
+    const bz::Plan &pl = *batch->pl;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<int> slots(nx);
+    for (int c = 0; c < nx; ++c) slots[c] = c;
+    int launches = 0;
+    for (int step = 0; step < nsteps; ++step) {
+        // free streaming dt/2 before the first collision step, dt between two, dt/2 after the last
+        bz_status s = bz::transport_x(pl.N, pl.L, nx, Lx, fcells, dtype, step == 0 ? 0.5 * dt : dt, st);
+        if (s == BZ_OK) s = bz_batch_step_rk(batch, nx, slots.data(), fcells, dtype, dt, 1, stream);
+        if (s != BZ_OK) return s;
+        launches += 1 + batch->last_launches;
+    }
+    if (nsteps > 0) {
+        bz_status s = bz::transport_x(pl.N, pl.L, nx, Lx, fcells, dtype, 0.5 * dt, st);
+        if (s != BZ_OK) return s;
+        ++launches;
+    }
+    batch->last_launches = launches;
+    return BZ_OK;
+}
+
 int bz_batch_last_launches(const bz_batch *batch) { return batch ? batch->last_launches : 0; }
 
 void bz_batch_destroy(bz_batch *batch) {

@@ -162,6 +162,9 @@ int supported_N(int N);
 cudaError_t setup_2d(Plan &pl);                       // persistent grid size (pl.fused_G)
 bz_status collide_2d(Plan &pl, int p0, int p1, cudaStream_t st, int *launches);
 
+// bz_inhom.cu: free streaming of nx cells (bz_transport_x)
+bz_status transport_x(int N, double L, int nx, double Lx, void *f, int dtype, double t, cudaStream_t st);
+
 // bz_rk.cu
 bz_status rk4_steps(Plan &pl, void *fhat, int dtype, double dt, int nsteps, cudaStream_t st,
                     int *launches);

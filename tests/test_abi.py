@@ -71,6 +71,17 @@ def test_precision_checks_without_gpu(libpath):
         assert h.value is None
 
 
+def test_transport_checks_without_gpu(libpath):
+    """bz_transport_x validates its arguments before any CUDA call."""
+    import paper_2004_11239_gb300 as bz
+    dummy = ctypes.c_void_p(16)
+    for N, L, nx, Lx, dt, t, want in [(12, 6.0, 8, 3.0, 1, 0.1, 7), (16, 6.0, 64, 3.0, 1, 0.1, 7), (16, 6.0, 8, -1.0, 1, 0.1, 1),
+                                      (16, 0.0, 8, 3.0, 1, 0.1, 1), (16, 6.0, 8, 3.0, 5, 0.1, 1),
+                                      (16, 6.0, 8, 3.0, 1, float("nan"), 1)]:
+        assert bz.lib.bz_transport_x(N, L, nx, Lx, dummy, dt, t, None) == want
+    assert bz.lib.bz_inhom_step(None, 8, 3.0, dummy, 1, 0.1, 1, None) == 1
+
+
 @pytest.mark.parametrize("N_rho,M,gamma", [(16, 12, 0.0), (32, 32, -1.0), (5, 72, -2.0), (8, 64, 0.5)])
 def test_library_quadrature_matches_oracle(libpath, N_rho, M, gamma):
     """The library's host quadrature (Newton Gauss-Legendre, its own sphere rules) equals the oracle's."""
