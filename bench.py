@@ -107,6 +107,7 @@ _PROFILES = {
     "fused": ("fused_rk4_n32.md", ("bz_fused_kernel.cuh", "bz_fft.cuh", "bz_cluster.cuh")),
     "mixed": ("mixed_rk4_n32.md", ("bz_mixed.cu", "bz_fft.cuh", "bz_cluster.cuh")),
     "fused_real": ("fused_real_rk4_n32.md", ("bz_fused_kernel.cuh", "bz_fft.cuh", "bz_cluster.cuh")),
+    "pair3": ("pair3_rk4_n32.md", ("bz_pair3.cu", "bz_fft.cuh", "bz_cluster.cuh")),
 }
 
 
@@ -417,7 +418,9 @@ def run_ours(args, w):
            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
 
     peaks, src = _peaks()
-    roof = _roofline(args, w, kern, peaks, src, "fused_real" if real else "fused")
+    kname = pipe.get("kernel", "k_fused")
+    roof = _roofline(args, w, kern, peaks, src, "pair3" if kname == "k_pair3" else ("fused_real" if real else "fused"))
+    roof["kernel_name"] = kname
     if real:
         roof["executed"] = ("term pairs share every pair of 3D transforms: about half the counted FFT "
                             "flops and half the alpha bytes (plus a 3 N^2 Nyquist table per pair) are executed")

@@ -153,6 +153,10 @@ typedef struct {
                          eqs. ApproximatedDebyecutoff and b3cutoff; 0 = none, else eps <= theta0 < pi.
                          With a cutoff there is no Taylor part; the theta rule starts at theta0. */
     int data;         /* BZ_DATA_*                                                         */
+    int ctas_per_sm;  /* fused pipeline, BZ_DATA_REAL at N = 32 with FP64 h: 2 runs k_fused, 3 the
+                         three-CTA-per-SM pair kernel k_pair3 (sum over pairs and fhat column in
+                         tensor memory); <= 0 times both at creation and keeps the faster.  Any
+                         other plan: must be <= 0 or 2, else BZ_ERR_UNSUPPORTED.              */
 } bz_plan_desc;
 
 /* Creates a plan: quadrature terms, the FP64 F table (computed on the device, stored
@@ -173,6 +177,11 @@ bz_status bz_plan_info(const bz_plan *plan, int *P, size_t *alpha_bytes, size_t 
  * for FUSED, *cluster = CTAs per cluster, *clusters = resident clusters (persistent grid),
  * *tuned_ms = the timed collide that selected the cluster size.  Any pointer may be NULL. */
 bz_status bz_plan_pipeline(const bz_plan *plan, int *pipeline, int *cluster, int *clusters, float *tuned_ms);
+
+/* Name of the kernel that carries the plan's per-term work: "k_fused", "k_pair3" (the
+ * three-CTA-per-SM pair kernel of a BZ_DATA_REAL plan at N = 32), "k_mixed", "k_collide_2d"
+ * or "chunked"; NULL for a NULL plan.  The string is static. */
+const char *bz_plan_kernel(const bz_plan *plan);
 
 /* Copies the term list to host arrays of length P (any may be NULL):
  * r[p], w_r[p], qhat[3p..3p+2], w_q[p], c[p] = w_r w_q r^(gamma+2).  Synchronous. */

@@ -24,7 +24,7 @@ __all__ = [
     "bz_quadrature", "bz_kernel_constants",
     "bz_batch_create", "bz_batch_destroy", "bz_batch_set_gamma", "bz_batch_collide", "bz_batch_step_rk",
     "bz_batch_last_launches", "bz_server_create", "bz_submit", "bz_poll", "bz_server_stats",
-    "bz_transport_x", "bz_inhom_step",
+    "bz_transport_x", "bz_inhom_step", "bz_plan_kernel",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -70,7 +70,7 @@ class bz_plan_desc(ctypes.Structure):
                 ("sphere_w", ctypes.POINTER(ctypes.c_double)), ("chunk_terms", ctypes.c_int),
                 ("pipeline", ctypes.c_int), ("cluster", ctypes.c_int), ("h_precision", ctypes.c_int),
                 ("conv", ctypes.c_int), ("dim", ctypes.c_int), ("theta0", ctypes.c_double),
-                ("data", ctypes.c_int)]
+                ("data", ctypes.c_int), ("ctas_per_sm", ctypes.c_int)]
 
 
 def library_path() -> str:
@@ -105,6 +105,7 @@ def _load():
         "bz_batch_collide": [vp, c_int, ip, vp, vp, c_int, vp],
         "bz_batch_step_rk": [vp, c_int, ip, vp, c_int, c_double, c_int, vp],
         "bz_transport_x": [c_int, c_double, c_int, c_double, vp, c_int, c_double, vp],
+        "bz_plan_kernel": [vp],
         "bz_inhom_step": [vp, c_int, c_double, vp, c_int, c_double, c_int, vp],
         "bz_server_create": [ctypes.POINTER(vp), c_size, c_int, c_int],
         "bz_submit": [vp, ctypes.POINTER(bz_request), ctypes.POINTER(ctypes.c_uint64)],
@@ -132,6 +133,8 @@ def _load():
     L.bz_plan_last_launches.restype = c_int
     L.bz_status_str.argtypes = [c_int]
     L.bz_status_str.restype = ctypes.c_char_p
+    L.bz_plan_kernel.argtypes = [vp]
+    L.bz_plan_kernel.restype = ctypes.c_char_p
     return L
 
 
@@ -209,7 +212,7 @@ def bz_plan_create_ex(N: int, L: float, R: float, gamma: float, s: float, N_rho:
                       chunk_terms: int = 0, pipeline: int = BZ_PIPE_AUTO, cluster: int = 0,
                       h_precision: int = BZ_H_AUTO, precision: int = BZ_PREC_FP32,
                       conv: int = BZ_CONV_CIRCULAR, dim: int = 3, theta0: float = 0.0,
-                      data: int = BZ_DATA_COMPLEX) -> Plan:
+                      data: int = BZ_DATA_COMPLEX, ctas_per_sm: int = 0) -> Plan:
     d = bz_plan_desc()
     d.N, d.L, d.R, d.gamma, d.s, d.N_rho, d.M = N, L, R, gamma, s, N_rho, M
     d.kernel, d.precision, d.eps, d.chunk_terms = kernel, precision, eps, chunk_terms
@@ -220,6 +223,7 @@ def bz_plan_create_ex(N: int, L: float, R: float, gamma: float, s: float, N_rho:
     d.dim = dim
     d.theta0 = theta0
     d.data = data
+    d.ctas_per_sm = ctas_per_sm
     keep = []
     if sphere is not None:
         import numpy as np
@@ -248,7 +252,7 @@ def bz_plan_pipeline(plan: Plan):
     _check(lib.bz_plan_pipeline(plan.handle, ctypes.byref(p), ctypes.byref(c), ctypes.byref(g), ctypes.byref(t)),
            "bz_plan_pipeline")
     return {"pipeline": "fused" if p.value == BZ_PIPE_FUSED else "chunked", "cluster": c.value,
-            "clusters": g.value, "tuned_ms": t.value}
+            "clusters": g.value, "tuned_ms": t.value, "kernel": lib.bz_plan_kernel(plan.handle).decode()}
 
 
 def bz_quadrature(N_rho: int, R: float, M: int, gamma: float):

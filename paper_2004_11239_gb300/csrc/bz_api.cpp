@@ -65,22 +65,27 @@ std::vector<float2> make_twiddles(const bz::Plan &pl) {
 
 // Times one full collide of a zero field for each compiled cluster size (or only `forced`)
 // and keeps the fastest; allocates the partial-sum buffer for it.
-bz_status select_fused(bz::Plan &pl, int forced) {
+bz_status select_fused(bz::Plan &pl, int forced, int ctas) {
     int cs[4];
     const bool mixed = pl.precision == BZ_PREC_BF16X3;
     int nc = mixed ? 1 : bz::fused_candidates(pl.N, cs);
     if (mixed) cs[0] = 8;
+    // the real-data form at N = 32 (FP64 h) also times the three-CTA pair kernel, k_pair3 (C = 8)
+    const int pair3_c = (pl.real && pl.N == 32 && pl.h_fp64 && ctas != 2) ? nc : -1;
+    if (pair3_c >= 0) cs[nc++] = 8;
     const size_t field = (size_t)pl.N * pl.N * pl.N * sizeof(float2);
     const size_t fields = (size_t)3 * pl.N * pl.N * sizeof(float2);   // BZ_DATA_REAL: Nyquist-plane sums
-    int bestC = 0, bestG = 0;
+    int bestC = 0, bestG = 0, bestP3 = 0;
     float best = 1e30f;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return BZ_ERR_CUDA;
     if (cudaMemset(pl.fin, 0, field) != cudaSuccess) return BZ_ERR_CUDA;
     for (int c = 0; c < nc; ++c) {
         if (forced > 0 && cs[c] != forced) continue;
+        if (ctas == 3 && c != pair3_c) continue;
         int G = 0;
-        const cudaError_t se = mixed ? bz::mixed_setup(pl.N, &G) : bz::fused_setup(pl.N, cs[c], &G, pl.real != 0);
+        const cudaError_t se = mixed ? bz::mixed_setup(pl.N, &G)
+                               : c == pair3_c ? bz::pair3_setup(&G) : bz::fused_setup(pl.N, cs[c], &G, pl.real != 0);
         if (se != cudaSuccess || G <= 0) { cudaGetLastError(); continue; }
         float2 *part = nullptr, *parts = nullptr;
         if (cudaMalloc(&part, (size_t)G * field) != cudaSuccess) { cudaGetLastError(); continue; }
@@ -91,7 +96,7 @@ bz_status select_fused(bz::Plan &pl, int forced) {
         }
         std::swap(part, pl.part);
         std::swap(parts, pl.part_s);
-        pl.use_fused = 1; pl.fused_C = cs[c]; pl.fused_G = G;
+        pl.use_fused = 1; pl.fused_C = cs[c]; pl.fused_G = G; pl.pair3 = c == pair3_c;
         float ms = 1e30f;
         if (bz::collide_fused(pl, 0, pl.P, nullptr, nullptr) == BZ_OK) {      // warm-up
             cudaEventRecord(e0);
@@ -104,7 +109,7 @@ bz_status select_fused(bz::Plan &pl, int forced) {
         std::swap(parts, pl.part_s);
         cudaFree(part);
         cudaFree(parts);
-        if (ms < best) { best = ms; bestC = cs[c]; bestG = G; }
+        if (ms < best) { best = ms; bestC = cs[c]; bestG = G; bestP3 = pl.pair3; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -112,7 +117,7 @@ bz_status select_fused(bz::Plan &pl, int forced) {
     if (bestC == 0) return BZ_ERR_UNSUPPORTED;
     if (dmalloc(&pl.part, (size_t)bestG * field) != BZ_OK) return BZ_ERR_OOM;
     if (pl.real && dmalloc(&pl.part_s, (size_t)bestG * fields) != BZ_OK) return BZ_ERR_OOM;
-    pl.use_fused = 1; pl.fused_C = bestC; pl.fused_G = bestG;
+    pl.use_fused = 1; pl.fused_C = bestC; pl.fused_G = bestG; pl.pair3 = bestP3;
     pl.fused_ms = best;
     pl.ws_bytes += (size_t)bestG * (field + (pl.real ? fields : 0));
     return BZ_OK;
@@ -143,6 +148,8 @@ bz_status create(bz_plan **out, const bz_plan_desc *d) {
     if (real && (dim != 3 || d->precision != BZ_PREC_FP32 || padded || 32 % d->N != 0 || d->M % 2 != 0 ||
                  d->pipeline == BZ_PIPE_CHUNKED))
         return BZ_ERR_UNSUPPORTED;
+    if (d->ctas_per_sm == 3 && !(real && d->N == 32 && d->h_precision != BZ_H_FP32)) return BZ_ERR_UNSUPPORTED;
+    if (d->ctas_per_sm > 0 && d->ctas_per_sm != 2 && d->ctas_per_sm != 3) return BZ_ERR_UNSUPPORTED;
     if (dim == 3 && !((d->kernel >= BZ_KERNEL_FAMILY && d->kernel <= BZ_KERNEL_B8) || d->kernel == BZ_KERNEL_DEBYE))
         return BZ_ERR_ARG;
     bz_plan *h = new (std::nothrow) bz_plan();
@@ -235,7 +242,7 @@ bz_status create(bz_plan **out, const bz_plan_desc *d) {
     if (d->pipeline != BZ_PIPE_CHUNKED && N <= 32) {
         if (dmalloc(&pl.fin64, n3 * sizeof(double2)) == BZ_OK && dmalloc(&pl.scr64, n3 * sizeof(double2)) == BZ_OK) {
             pl.ws_bytes += 2 * n3 * sizeof(double2);
-            if (select_fused(pl, d->cluster) != BZ_OK) cudaGetLastError();
+            if (select_fused(pl, d->cluster, d->ctas_per_sm) != BZ_OK) cudaGetLastError();
         }
     }
     if ((d->pipeline == BZ_PIPE_FUSED || pl.precision == BZ_PREC_BF16X3 || pl.real) && !pl.use_fused) {
@@ -278,6 +285,15 @@ bz_status bz_plan_info(const bz_plan *plan, int *P, size_t *alpha_bytes, size_t 
                        sizeof(float2);
     if (workspace_bytes) *workspace_bytes = p.ws_bytes;
     return BZ_OK;
+}
+
+const char *bz_plan_kernel(const bz_plan *plan) {
+    if (!plan) return nullptr;
+    const bz::Plan &p = plan->p;
+    if (p.dim == 2) return "k_collide_2d";
+    if (!p.use_fused) return "chunked";
+    if (p.precision == BZ_PREC_BF16X3) return "k_mixed";
+    return p.pair3 ? "k_pair3" : "k_fused";
 }
 
 bz_status bz_plan_pipeline(const bz_plan *plan, int *pipeline, int *cluster, int *clusters, float *tuned_ms) {

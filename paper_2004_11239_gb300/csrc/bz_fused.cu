@@ -303,6 +303,7 @@ template <int N, int C> static bz_status launch_sc(const Plan &pl, const ItemArg
 bz_status launch_fused(const Plan &pl, const ItemArgs &a, cudaStream_t st) {
     const int N = pl.N, C = pl.fused_C;
     if (pl.precision == BZ_PREC_BF16X3) return a.real ? BZ_ERR_UNSUPPORTED : launch_mixed(pl, a, st);
+    if (pl.pair3 && a.real) return launch_pair3(pl, a, st);
     if (N == 8 && C == 1) return launch_sc<8, 1>(pl, a, st);
     if (N == 16 && C == 1) return launch_sc<16, 1>(pl, a, st);
     if (N == 16 && C == 2) return launch_sc<16, 2>(pl, a, st);

@@ -73,6 +73,7 @@ struct Plan {
     uint4 *wimg = nullptr;          // BZ_PREC_BF16X3: split DFT matrix (tensor-core B operand)
     // BZ_DATA_REAL: terms 2q and 2q + 1 share one pair of transforms
     int real = 0;
+    int pair3 = 0;                  // N = 32: the three-CTA-per-SM pair kernel (k_pair3) instead of k_fused
     float2 *apair = nullptr;        // [P / 2][N^3] A = (alpha_2q - i alpha_2q+1) / 2
     float2 *cpair = nullptr;        // [P / 2][3][N][N] C = conj B(-k), B = (alpha_2q + i alpha_2q+1) / 2, on the
                                     // Nyquist planes (families k1 = -N/2, k2 = -N/2, k3 = -N/2), 0 elsewhere
@@ -148,6 +149,10 @@ bz_status build_pair_table(Plan &pl);
 bz_status sym_input(Plan &pl, const void *f, int dtype, cudaStream_t st);
 // pl.acc <- Q from the nblk item sums of pl.part (V) and pl.part_s (X): one kernel
 bz_status reduce_sym(Plan &pl, int nblk, cudaStream_t st);
+
+// bz_pair3.cu (BZ_DATA_REAL, N = 32, FP64 h): resident clusters and launch of k_pair3
+cudaError_t pair3_setup(int *G);
+bz_status launch_pair3(const Plan &pl, const ItemArgs &a, cudaStream_t st);
 
 // bz_mixed.cu (BZ_PREC_BF16X3, N = 32)
 cudaError_t mixed_setup(int N, int *G);

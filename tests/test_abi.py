@@ -61,6 +61,13 @@ def test_precision_checks_without_gpu(libpath):
         d.precision, d.pipeline, d.conv = prec, pipe, conv
         assert bz.lib.bz_plan_create_ex(ctypes.byref(h), ctypes.byref(d)) == want
         assert h.value is None
+    # CTAs per SM: 3 only for the real-data form at N = 32 with FP64 h
+    for N, data, ctas, hp, want in [(32, 0, 3, 0, 7), (16, 1, 3, 0, 7), (32, 1, 3, 2, 7), (32, 1, 4, 0, 7)]:
+        d = bz.bz_plan_desc()
+        d.N, d.L, d.R, d.gamma, d.s, d.N_rho, d.M = N, 10.0, 9.0, 0.0, 0.5, 2, 12
+        d.data, d.ctas_per_sm, d.h_precision = data, ctas, hp
+        assert bz.lib.bz_plan_create_ex(ctypes.byref(h), ctypes.byref(d)) == want
+        assert h.value is None
     # the real-data form: 3D FP32 circular fused (N <= 32), M even
     for N, M, prec, pipe, data, want in [(32, 12, 0, 0, 2, 1), (32, 12, bz.BZ_PREC_BF16X3, 0, 1, 7), (32, 9, 0, 0, 1, 7),
                                          (48, 12, 0, 0, 1, 7), (16, 12, 0, bz.BZ_PIPE_CHUNKED, 1, 7)]:

@@ -47,27 +47,32 @@ def _collide(bz, plan, fhat, p0=None, p1=None, dtype=torch.complex128):
 
 
 CASES = [
-    # N, gamma, s, kernel name, kernel id, N_rho, M, data
-    (8, 0.0, 0.5, "family", 0, 3, 12, "random"),
-    (16, -1.0, 0.25, "family", 0, 2, 32, "mixture"),
-    (16, 0.0, 0.0, "b5", 1, 2, 12, "random"),
-    (32, -2.0, 0.0, "b8", 2, 2, 12, "mixture"),
-    (32, 0.0, 0.5, "family", 0, 3, 12, "random"),
+    # N, gamma, s, kernel name, kernel id, N_rho, M, data, CTAs per SM (N = 32: 2 k_fused, 3 k_pair3)
+    (8, 0.0, 0.5, "family", 0, 3, 12, "random", 0),
+    (16, -1.0, 0.25, "family", 0, 2, 32, "mixture", 0),
+    (16, 0.0, 0.0, "b5", 1, 2, 12, "random", 0),
+    (32, -2.0, 0.0, "b8", 2, 2, 12, "mixture", 2),
+    (32, -2.0, 0.0, "b8", 2, 2, 12, "mixture", 3),
+    (32, 0.0, 0.5, "family", 0, 3, 12, "random", 2),
+    (32, 0.0, 0.5, "family", 0, 3, 12, "random", 3),
 ]
 
 
-@pytest.mark.parametrize("N,gamma,s,name,kid,N_rho,M,data", CASES)
-def test_real_collide_matches_oracle(bz, N, gamma, s, name, kid, N_rho, M, data):
+@pytest.mark.parametrize("N,gamma,s,name,kid,N_rho,M,data,ctas", CASES)
+def test_real_collide_matches_oracle(bz, N, gamma, s, name, kid, N_rho, M, data, ctas):
     L = 10.0
     R = bi.R_from_L(L)
     fhat = bi.random_fhat(N, seed=40 + N, scale=1e-3) if data == "random" else bi.random_mixture(N, L, seed=N)
-    plan = _real_plan(bz, N, L, R, gamma, s, N_rho, M, kid)
+    plan = _real_plan(bz, N, L, R, gamma, s, N_rho, M, kid, ctas_per_sm=ctas)
     info = bz.bz_plan_pipeline(plan)
     assert info["pipeline"] == "fused"
+    if ctas:
+        assert info["kernel"] == ("k_pair3" if ctas == 3 else "k_fused")
     got = _collide(bz, plan, fhat)
     ref = spectral.collide_real(spectral.OraclePlan(N, L, R, gamma, kernels.Kernel(name, s), N_rho, M), fhat)
     err = _rel(got, ref)
-    print(f"real N={N} {data} gamma={gamma} {name} s={s} P={N_rho * M} C={info['cluster']}: rel_Linf={err:.2e}")
+    print(f"real N={N} {data} gamma={gamma} {name} s={s} P={N_rho * M} {info['kernel']} C={info['cluster']} "
+          f"G={info['clusters']}: rel_Linf={err:.2e}")
     assert err <= TOL
     ny = spectral.nyquist_mask(N)
     assert np.array_equal(spectral.mirror(got)[~ny], np.conj(got)[~ny])   # symmetrised exactly off S
@@ -140,7 +145,8 @@ def _summand_scale(oplan, fhat, p0, p1):
     return float(np.max(tot))
 
 
-def test_real_form_at_full_size(bz):
+@pytest.mark.parametrize("ctas", [2, 3])
+def test_real_form_at_full_size(bz, ctas):
     """The bench's workload (N = 32, P = 1024, BKW at t = 6.5; Nyquist content 5e-8 of fhat_0):
     the whole real-data collide against the oracle's reading and against the circular operator
     itself (eq. realQ on fhat as given: the real form drops only the Nyquist content of f);
@@ -149,14 +155,15 @@ def test_real_form_at_full_size(bz):
     N, R = 32, 6.0
     L = bi.L_from_R(R)
     fhat = bi.bkw_fhat(N, L, bi.bkw_K(6.5))
-    pr = _real_plan(bz, N, L, R, 0.0, 0.5, 32, 32)
+    pr = _real_plan(bz, N, L, R, 0.0, 0.5, 32, 32, ctas_per_sm=ctas)
     pc = bz.bz_plan_create(N, L, R, 0.0, 0.5, 32, 32)
+    assert bz.bz_plan_pipeline(pr)["kernel"] == ("k_pair3" if ctas == 3 else "k_fused")
     gr = _collide(bz, pr, fhat)
     gc = _collide(bz, pc, fhat)
     op = spectral.OraclePlan(N, L, R, 0.0, kernels.Kernel("family", 0.5), 32, 32)
     err = _rel(gr, spectral.collide_real(op, fhat))
     err_c = _rel(gr, spectral.collide(op, fhat))
-    print(f"real N=32 P=1024 BKW: rel_Linf={err:.2e} vs the real-data reading, {err_c:.2e} vs eq. realQ; "
+    print(f"real ({ctas} CTAs/SM) N=32 P=1024 BKW: rel_Linf={err:.2e} vs the real-data reading, {err_c:.2e} vs eq. realQ; "
           f"vs the complex FP32 form {_rel(gr, gc):.2e}")
     assert err <= TOL and err_c <= TOL
     for p0 in (0, 500, 1014):
