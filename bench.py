@@ -379,7 +379,8 @@ def run_ours(args, w):
 
     def make_plan(form):
         return bz.bz_plan_create_ex(N, L, R, w["gamma"], w["s"], w["N_rho"], w["M"], h_precision=args.h_precision,
-                                    kernel=w.get("kernel", 0), dim=dim, data=form, cluster=args.cluster)
+                                    kernel=w.get("kernel", 0), dim=dim, data=form, cluster=args.cluster,
+                                    ctas_per_sm=args.ctas_per_sm if form == bz.BZ_DATA_REAL else 0)
 
     plan = make_plan(data_form)
     pipe = bz.bz_plan_pipeline(plan)
@@ -793,6 +794,8 @@ def main():
                          "(3D, N in {8, 16, 32}, M even; the workloads' f are real), else complex")
     ap.add_argument("--cluster", type=int, default=0,
                     help="CTAs per cluster of the fused kernel (0: timed at plan creation, fastest kept)")
+    ap.add_argument("--ctas-per-sm", type=int, default=0, choices=[0, 2, 3],
+                    help="real-data form at N = 32: 2 runs k_fused, 3 k_pair3, 0 times both at plan creation")
     ap.add_argument("--h-precision", type=int, default=0, choices=[0, 1, 2],
                     help="h = IFFT(fhat) precision on the fused path: 0 auto (FP64), 1 FP64, 2 FP32")
     args = ap.parse_args()

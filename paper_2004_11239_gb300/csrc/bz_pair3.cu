@@ -8,8 +8,11 @@
 //     written with tcgen05.ld / tcgen05.st on the thread's own lane;
 //   * the pair table tile is not staged in shared memory: one thread prefetches the CTA's
 //     32 KB of A to L2 when the pair starts and each thread loads its entries in the epilogue.
-// Shared memory: planes (33.8 KB), the real h slice (16 KB), twiddles (3 KB), X on the plane
-// k1 = -N/2 (8 KB) and the pair's Nyquist table rows (10 KB).
+// At N = 32 with 8-CTA clusters a plane is one warp, so the two in-plane transposes of phases A
+// and C need only __syncwarp: each warp stages its own Nyquist table rows (cp.async, waited
+// by the warp) and reads the pair's twiddles through L1; the two cluster barriers per pair are
+// the only block-wide synchronisation.  Shared memory: planes (33.8 KB), the real h slice
+// (16 KB), X on the plane k1 = -N/2 (8 KB) and the pair's Nyquist table rows (10 KB).
 #include "bz_cluster.cuh"
 #include "bz_fft.cuh"
 #include "bz_internal.h"
@@ -21,10 +24,10 @@ namespace {
 constexpr int PN = 32, PC = 8, PPP = PN / PC, PT = PN * PPP, PLD = PN + 1;
 constexpr size_t P_PLANES = (size_t)PPP * PN * PLD * sizeof(float2);
 constexpr size_t P_HS = (size_t)PPP * PN * PN * sizeof(float);
-constexpr size_t P_TW = (size_t)6 * PN * sizeof(float2);
 constexpr size_t P_XS1 = (size_t)PN * PN * sizeof(float2);
 constexpr size_t P_CS = (size_t)(PN * PN + 2 * PPP * PN) * sizeof(float2);
-constexpr size_t P_SMEM = P_PLANES + P_HS + 2 * P_TW + P_XS1 + P_CS;
+constexpr size_t P_SMEM = P_PLANES + P_HS + P_XS1 + P_CS;
+static_assert(PPP * PN == PT && PN == 32, "one warp per plane");
 constexpr uint32_t P_TMEM_COLS = 128;          // acc (64 columns) + fhat column (64)
 constexpr uint32_t TM_ACC = 0, TM_FH = 64;
 static_assert(3 * (P_SMEM + 1024) <= 228 * 1024, "three CTAs per SM");
@@ -56,19 +59,17 @@ __device__ __forceinline__ void t_st16(uint32_t ta, const float *v) {
 }
 
 __global__ void __launch_bounds__(PT, 3) k_pair3(ItemArgs a) {
-    constexpr int N = PN, C = PC, PPC = PPP, LD = PLD, T = PT, TWN = 6 * N;
+    constexpr int N = PN, C = PC, PPC = PPP, LD = PLD, TWN = 6 * N;
     extern __shared__ __align__(16) float2 smem[];
     __shared__ uint32_t s_tmem;
     float2 *planes = smem;                                            // [PPC][N][LD]
     float *shr = (float *)((char *)smem + P_PLANES);                  // real h slice [PPC][N][N]
-    float2 *stw = (float2 *)((char *)shr + P_HS);                     // twiddles [2][TWN]
-    float2 *xs1 = stw + 2 * TWN;                                      // X on plane k1 = -N/2 [k2][k3]
+    float2 *xs1 = (float2 *)((char *)shr + P_HS);                     // X on plane k1 = -N/2 [k2][k3]
     float2 *sc1 = xs1 + N * N;                                        // C on plane k1 = -N/2
     float2 *sc2 = sc1 + N * N;                                        // C rows, family k2 = -N/2 [pid][k3]
     float2 *sc3 = sc2 + PPC * N;                                      // C rows, family k3 = -N/2 [pid][k2]
     const int tid = threadIdx.x, w = tid >> 5;
     const int rank = (int)cooperative_groups::this_cluster().block_rank();
-    const bool owns_nyq = rank == (N / 2) / PPC;
     const int cid = blockIdx.x / C, ncl = gridDim.x / C;
     const int lane = tid % N, pid = tid / N;
     const int k1 = rank * PPC + pid, j2p = rank * PPC + pid;
@@ -91,11 +92,6 @@ __global__ void __launch_bounds__(PT, 3) k_pair3(ItemArgs a) {
 
     const int count = a.count_dev ? *a.count_dev : a.count;
     const int nitems = count * a.nblk;
-    auto fetch_tw = [&](int p, int buf) {
-        if (p >= 0 && tid < (int)(P_TW / 16))
-            cp_async16((char *)(stw + buf * TWN) + 16 * tid, (const char *)(a.tw + (size_t)p * TWN) + 16 * tid);
-        cp_async_commit();
-    };
 
     for (int it_ = cid; it_ < nitems; it_ += ncl) {
         const int b = it_ / a.nblk, blk = it_ % a.nblk;
@@ -103,8 +99,7 @@ __global__ void __launch_bounds__(PT, 3) k_pair3(ItemArgs a) {
         const int t0 = a.p0 + blk * a.TB;
         const int t1 = min(a.p1, t0 + a.TB);
         const float2 *fin = a.fin + (size_t)slot * N3;
-        __syncthreads();
-        fetch_tw(t0, 0);
+        __syncthreads();                                              // the previous item is done
         {
             const float2 *hs = a.hg + (size_t)slot * N3;
             #pragma unroll 4
@@ -132,48 +127,42 @@ __global__ void __launch_bounds__(PT, 3) k_pair3(ItemArgs a) {
             #pragma unroll 8
             for (int i = 0; i < N; ++i) xs1[i * N + lane] = make_float2(0.f, 0.f);
         }
-        int it = 0;
-        for (int p = t0; p < t1; ++p, ++it) {
-            const int buf = it & 1;
+        for (int p = t0; p < t1; ++p) {
             const float2 *ap = a.alpha + ((size_t)p * N + (size_t)rank * PPC) * N * N;   // the CTA's A tile
-            cp_async_wait_all();
-            __syncthreads();
             if (tid == 0)
                 asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(ap),
                              "r"((uint32_t)(PPC * N * N * sizeof(float2))) : "memory");
             {
+                // this warp's Nyquist table rows: k2 = -N/2 family (lanes 0-15), k3 = -N/2 family
+                // (lanes 16-31), and the whole plane k1 = -N/2 in the warp that holds it
                 const float2 *cq = a.cpair + (size_t)p * 3 * N * N;
-                constexpr int ROW16 = PPC * N * (int)sizeof(float2) / 16;
-                if (tid < ROW16) {
-                    cp_async16((char *)sc2 + 16 * tid, (const char *)(cq + N * N + rank * PPC * N) + 16 * tid);
-                } else if (tid < 2 * ROW16) {
-                    const int c = tid - ROW16;
-                    cp_async16((char *)sc3 + 16 * c, (const char *)(cq + 2 * N * N + rank * PPC * N) + 16 * c);
-                }
-                if (owns_nyq)
-                    for (int c = tid; c < N * N * (int)sizeof(float2) / 16; c += T)
+                const int l16 = lane & 15;
+                __syncwarp();                                 // the warp is done with the previous rows
+                if (lane < 16) cp_async16((char *)(sc2 + pid * N) + 16 * l16, (const char *)(cq + N * N + k1 * N) + 16 * l16);
+                else cp_async16((char *)(sc3 + pid * N) + 16 * l16, (const char *)(cq + 2 * N * N + k1 * N) + 16 * l16);
+                if (k1 == N / 2)
+                    for (int c = lane; c < N * N * (int)sizeof(float2) / 16; c += 32)
                         cp_async16((char *)sc1 + 16 * c, (const char *)cq + 16 * c);
                 cp_async_commit();
             }
-            fetch_tw(p + 1 < t1 ? p + 1 : -1, buf ^ 1);
             // A: x = (beta_p + i beta_p') fhat over k2, inverse over k2, then rows over k3
             {
-                const float2 *tws = stw + buf * TWN;
-                const float2 ta = cmul(tws[k1], tws[2 * N + lane]);
-                const float2 tb = cmul(tws[3 * N + k1], tws[5 * N + lane]);
+                const float2 *tws = a.tw + (size_t)p * TWN;  // the pair's twiddles, through L1
+                const float2 ta = cmul(__ldg(tws + k1), __ldg(tws + 2 * N + lane));
+                const float2 tb = cmul(__ldg(tws + 3 * N + k1), __ldg(tws + 5 * N + lane));
                 float2 x[N];
                 #pragma unroll
                 for (int g = 0; g < 4; ++g) t_ld16(tl + TM_FH + 16 * g, (float *)(x + 8 * g));
                 t_wait_ld();
                 #pragma unroll
                 for (int i = 0; i < N; ++i) {
-                    const float2 u = cmul(ta, tws[N + i]), v = cmul(tb, tws[4 * N + i]);
+                    const float2 u = cmul(ta, __ldg(tws + N + i)), v = cmul(tb, __ldg(tws + 4 * N + i));
                     x[i] = cmul(x[i], make_float2(u.x - v.y, u.y + v.x));
                 }
                 fft_inplace<N, +1>(x);
                 #pragma unroll
                 for (int i = 0; i < N; ++i) my[i * LD + lane] = x[i];
-                __syncthreads();
+                __syncwarp();                                 // the plane is this warp's
                 #pragma unroll
                 for (int j = 0; j < N; ++j) x[j] = my[lane * LD + j];
                 fft_inplace<N, +1>(x);
@@ -202,16 +191,26 @@ __global__ void __launch_bounds__(PT, 3) k_pair3(ItemArgs a) {
             fft_inplace<N, -1>(x);
             #pragma unroll
             for (int j = 0; j < N; ++j) my[lane * LD + j] = x[j];
-            cp_async_wait_1();                                // the Nyquist rows (the next twiddles may pend)
-            __syncthreads();
+            cp_async_wait_all();                              // this warp's Nyquist rows
+            __syncwarp();
             #pragma unroll
             for (int i = 0; i < N; ++i) x[i] = my[i * LD + lane];
+            // the pair table entries (L2) are loaded one chunk of eight ahead of their use, the
+            // first chunk during the last transform
+            const float2 *apl = ap + (size_t)pid * N * N + lane;
+            float2 an[8];
+            #pragma unroll
+            for (int u = 0; u < 8; ++u) an[u] = __ldg(apl + u * N);
             fft_inplace<N, -1>(x);
             #pragma unroll
             for (int g = 0; g < 4; ++g) {
                 float2 al[8];
                 #pragma unroll
-                for (int u = 0; u < 8; ++u) al[u] = __ldg(ap + ((size_t)pid * N + 8 * g + u) * N + lane);
+                for (int u = 0; u < 8; ++u) al[u] = an[u];
+                if (g < 3) {
+                    #pragma unroll
+                    for (int u = 0; u < 8; ++u) an[u] = __ldg(apl + (8 * (g + 1) + u) * N);
+                }
                 float s[16];
                 t_ld16(tl + TM_ACC + 16 * g, s);
                 t_wait_ld();
