@@ -574,8 +574,9 @@ def run_batch(args, w):
         g_ = gvals[int(u[2 * i + 1] * 2)]
         groups.setdefault((N, s_), []).append((i, g_))
     runs = []
+    form = bz.BZ_DATA_COMPLEX if args.data == "complex" else bz.BZ_DATA_REAL    # M = 32 and N | 32: real applies
     for (N, s_), members in sorted(groups.items()):
-        plan = bz.bz_plan_create(N, L, R, 0.0, s_, N, w["M"])
+        plan = bz.bz_plan_create_ex(N, L, R, 0.0, s_, N, w["M"], data=form)
         batch = bz.bz_batch_create(plan, len(members), 0)
         for slot, (i, g_) in enumerate(members):
             if g_ != 0.0:
@@ -621,6 +622,7 @@ def run_batch(args, w):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic", "config": {"workload": args.workload, "desc": w["desc"],
+                                            "data_form": "complex" if form == bz.BZ_DATA_COMPLEX else "real",
                                             "groups": {f"N={k[0]},s={k[1]}": len(v) for k, v in sorted(groups.items())},
                                             "terms_per_item": {f"N={r[0]},s={r[1]}": r[3].terms_per_item for r in runs}},
             "clocks": clk.summary(), "gpu_launches": launches, "wall_s": wall, "roofline": roof}
@@ -638,7 +640,8 @@ def run_inhom(args, w):
     torch.cuda.set_device(0)
     L, R = _geometry(w)
     N, nx, Lx = w["N"], w["nx"], w["Lx"]
-    plan = bz.bz_plan_create(N, L, R, w["gamma"], w["s"], w["N_rho"], w["M"])
+    form = bz.BZ_DATA_COMPLEX if args.data == "complex" else bz.BZ_DATA_REAL
+    plan = bz.bz_plan_create_ex(N, L, R, w["gamma"], w["s"], w["N_rho"], w["M"], data=form)
     batch = bz.bz_batch_create(plan, nx, 0)
     f_host = bi.inhom_cells(N, L, nx, Lx)
     fd = torch.from_numpy(f_host).cuda()
@@ -695,6 +698,7 @@ def run_inhom(args, w):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic", "config": {"workload": args.workload, "desc": w["desc"], "cells": nx,
+                                            "data_form": "complex" if form == bz.BZ_DATA_COMPLEX else "real",
                                             "P": plan.P, "transport_ms_per_step": ms_tr / args.steps,
                                             "transport_share": ms_tr / ms},
             "clocks": clk.summary(), "gpu_launches": launches * args.steps, "roofline": roof,

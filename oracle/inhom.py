@@ -48,11 +48,14 @@ def transport(fcells: np.ndarray, L: float, Lx: float, t: float) -> np.ndarray:
     return np.stack([_to_coeffs(fv[c]) for c in range(nx)])
 
 
-def strang(plan: spectral.OraclePlan, fcells: np.ndarray, Lx: float, dt: float, nsteps: int) -> np.ndarray:
+def strang(plan: spectral.OraclePlan, fcells: np.ndarray, Lx: float, dt: float, nsteps: int,
+           real: bool = False) -> np.ndarray:
+    """real: the collision step uses the real-data reading (`spectral.rk4_real`)."""
+    rk = spectral.rk4_real if real else spectral.rk4
     f = np.asarray(fcells, dtype=np.complex128).copy()
     for _ in range(nsteps):
         f = transport(f, plan.L, Lx, 0.5 * dt)
-        f = np.stack([spectral.rk4(plan, f[c], dt, 1) for c in range(f.shape[0])])
+        f = np.stack([rk(plan, f[c], dt, 1) for c in range(f.shape[0])])
         f = transport(f, plan.L, Lx, 0.5 * dt)
     return f
 

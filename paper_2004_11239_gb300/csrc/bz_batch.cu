@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "bz_internal.h"
+#include "bz_real.cuh"
 
 struct bz_plan;
 
@@ -35,6 +36,9 @@ struct bz_batch {
     double2 *f0 = nullptr, *fsum = nullptr;   // [capacity][N^3]
     double2 *fin64 = nullptr, *scr64 = nullptr;   // [capacity][N^3] FP64 stage input and h scratch
     float2 *h = nullptr;            // [capacity][N^3] h per instance
+    int units = 0;                  // work units of the plan: terms, or term pairs (BZ_DATA_REAL)
+    float2 *fsym = nullptr;         // BZ_DATA_REAL: [capacity][N^3] Hermitian, Nyquist-free inputs
+    float2 *part_s = nullptr;       // BZ_DATA_REAL: [capacity][nblk][3][N][N] Nyquist sums
     int *slots_dev = nullptr;       // [capacity]
     int *count_dev = nullptr;       // [1]
     int *host_stage = nullptr;      // pinned [capacity + 1]
@@ -62,7 +66,7 @@ __global__ void k_batch_load(const void *fhat, int dtype, const int *slots, cons
 
 // Sum of an instance's block partials in block order, Kahan-compensated on the FP32 pipes
 // (the FP64 units of this GPU are far slower); returned in FP64.
-__device__ __forceinline__ double2 sum_blocks(const float2 *part, int slot, int nblk, int n3, int k) {
+__device__ __forceinline__ double2 sum_blocks(const float2 *part, int slot, int nblk, int n3, size_t k) {
     float sr = 0.f, si = 0.f, cr = 0.f, ci = 0.f;
     const float2 *p = part + (size_t)slot * nblk * n3 + k;
     for (int blk = 0; blk < nblk; ++blk) {
@@ -134,6 +138,92 @@ __global__ void k_batch_rk_stage(const float2 *part, int nblk, const int *slots,
     fin64[idx] = y;
 }
 
+// BZ_DATA_REAL: Q of mode k from the block sums V (part) and X (part_s): V(k) + conj V(-k) off
+// the Nyquist planes, V(k) + conj X(-k) on them.  The thread of the smaller index of each
+// mirror pair {k, -k} off the Nyquist planes produces both entries (mm = the mirror, or -1 when
+// this thread has nothing to do); returns Q(k) and, for a pair, Q(-k) in qm.
+__device__ __forceinline__ bool real_q(const float2 *part, const float2 *part_s, int slot, int nblk, int N, int k,
+                                       double2 &qk, double2 &qm, long long &mm) {
+    const int n3 = N * N * N;
+    const int i1 = k / (N * N), i2 = (k / N) % N, i3 = k % N;
+    const int m1 = (N - i1) % N, m2 = (N - i2) % N, m3 = (N - i3) % N;
+    mm = -1;
+    const double2 v = sum_blocks(part, slot, nblk, n3, (size_t)k);
+    if (nyquist(i1, i2, i3, N)) {
+        const double2 x = sum_blocks(part_s, slot, nblk, 3 * N * N, (size_t)family_index(m1, m2, m3, N));
+        qk = make_double2(v.x + x.x, v.y - x.y);
+        return true;
+    }
+    const size_t m = ((size_t)m1 * N + m2) * N + m3;
+    if ((size_t)k > m) return false;
+    if ((size_t)k == m) {
+        qk = make_double2(2.0 * v.x, 0.0);
+        return true;
+    }
+    const double2 w = sum_blocks(part, slot, nblk, n3, m);
+    qk = make_double2(v.x + w.x, v.y - w.y);
+    qm = make_double2(w.x + v.x, w.y - v.y);
+    mm = (long long)m;
+    return true;
+}
+
+__global__ void k_batch_out_real(const float2 *part, const float2 *part_s, int nblk, const int *slots,
+                                 const int *count_dev, int N, void *Qhat, int dtype) {
+    const int n3 = N * N * N;
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int b = (int)(e / n3), k = (int)(e % n3);
+    if (b >= *count_dev) return;
+    const int slot = slots[b];
+    double2 qk, qm;
+    long long mm;
+    if (!real_q(part, part_s, slot, nblk, N, k, qk, qm, mm)) return;
+    const size_t base = (size_t)slot * n3;
+    auto put = [&](size_t i, double2 q) {
+        if (dtype == BZ_C128) ((double2 *)Qhat)[base + i] = q;
+        else ((float2 *)Qhat)[base + i] = make_float2((float)q.x, (float)q.y);
+    };
+    put((size_t)k, qk);
+    if (mm >= 0) put((size_t)mm, qm);
+}
+
+// Stage s of RK4 on one mode (the same combination as k_batch_rk_stage).
+__device__ __forceinline__ void rk_stage_mode(size_t idx, double2 kv, double2 *f0, double2 *fsum, float2 *fin,
+                                              double2 *fin64, int stage, double dt) {
+    const double2 a = f0[idx];
+    double2 y;
+    if (stage == 1) {
+        fsum[idx] = make_double2(a.x + dt / 6.0 * kv.x, a.y + dt / 6.0 * kv.y);
+        y = make_double2(a.x + 0.5 * dt * kv.x, a.y + 0.5 * dt * kv.y);
+    } else if (stage == 2 || stage == 3) {
+        const double2 s = fsum[idx];
+        fsum[idx] = make_double2(s.x + dt / 3.0 * kv.x, s.y + dt / 3.0 * kv.y);
+        const double c = stage == 2 ? 0.5 * dt : dt;
+        y = make_double2(a.x + c * kv.x, a.y + c * kv.y);
+    } else {
+        const double2 s = fsum[idx];
+        y = make_double2(s.x + dt / 6.0 * kv.x, s.y + dt / 6.0 * kv.y);
+        f0[idx] = y;
+    }
+    fin[idx] = make_float2((float)y.x, (float)y.y);
+    fin64[idx] = y;
+}
+
+__global__ void k_batch_rk_stage_real(const float2 *part, const float2 *part_s, int nblk, const int *slots,
+                                      const int *count_dev, int N, double2 *f0, double2 *fsum, float2 *fin,
+                                      double2 *fin64, int stage, double dt) {
+    const int n3 = N * N * N;
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int b = (int)(e / n3), k = (int)(e % n3);
+    if (b >= *count_dev) return;
+    const int slot = slots[b];
+    double2 qk, qm;
+    long long mm;
+    if (!real_q(part, part_s, slot, nblk, N, k, qk, qm, mm)) return;
+    const size_t base = (size_t)slot * n3;
+    rk_stage_mode(base + k, qk, f0, fsum, fin, fin64, stage, dt);
+    if (mm >= 0) rk_stage_mode(base + (size_t)mm, qm, f0, fsum, fin, fin64, stage, dt);
+}
+
 __global__ void k_batch_rk_out(const double2 *f0, const int *slots, const int *count_dev, int n3, void *fhat,
                                int dtype) {
     const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -150,7 +240,10 @@ ItemArgs item_args(const bz_batch &B) {
     a.fin = B.fin; a.tw = pl.tw; a.alpha = pl.alpha; a.gsc = B.gsc; a.part = B.part;
     a.hg = pl.h_fp64 ? B.h : nullptr;
     a.slots = B.slots_dev; a.count_dev = B.count_dev; a.count = 0;
-    a.p0 = 0; a.p1 = pl.P; a.TB = B.TB; a.nblk = B.nblk; a.M = pl.M; a.N_rho = pl.N_rho;
+    a.p0 = 0; a.p1 = B.units; a.TB = B.TB; a.nblk = B.nblk; a.M = pl.M; a.N_rho = pl.N_rho;
+    if (pl.real) {                                   // units are term pairs
+        a.real = 1; a.fin = B.fsym; a.alpha = pl.apair; a.cpair = pl.cpair; a.part_s = B.part_s;
+    }
     return a;
 }
 
@@ -180,7 +273,7 @@ void free_batch(bz_batch *B) {
     for (auto &g : B->graphs) cudaGraphExecDestroy(g.second);
     B->graphs.clear();
     cudaFree(B->gsc); cudaFree(B->fin); cudaFree(B->part); cudaFree(B->f0); cudaFree(B->fsum);
-    cudaFree(B->fin64); cudaFree(B->scr64); cudaFree(B->h);
+    cudaFree(B->fin64); cudaFree(B->scr64); cudaFree(B->h); cudaFree(B->fsym); cudaFree(B->part_s);
     cudaFree(B->slots_dev); cudaFree(B->count_dev);
     if (B->host_stage) cudaFreeHost(B->host_stage);
     if (B->cap_stream) cudaStreamDestroy(B->cap_stream);
@@ -210,9 +303,9 @@ int autotune_tb(bz_batch &B, int trial, cudaStream_t st) {
     for (int b = 0; b < trial; ++b) slots[b] = b;
     stage_slots(B, trial, slots.data(), st);
     for (int tb : cands) {
-        if (tb > pl.P && best > 0) break;
-        B.TB = tb < pl.P ? tb : pl.P;
-        B.nblk = (pl.P + B.TB - 1) / B.TB;
+        if (tb > B.units && best > 0) break;
+        B.TB = tb < B.units ? tb : B.units;
+        B.nblk = (B.units + B.TB - 1) / B.TB;
         ItemArgs a = item_args(B);
         launch_fused(pl, a, st);                      // warm-up
         cudaEventRecord(e0, st);
@@ -222,7 +315,7 @@ int autotune_tb(bz_batch &B, int trial, cudaStream_t st) {
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
         if (ms < best_ms) { best_ms = ms; best = B.TB; }
-        if (B.TB == pl.P) break;
+        if (B.TB == B.units) break;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -241,10 +334,12 @@ bz_status bz_batch_create(bz_batch **out, const bz_plan *plan, int capacity, int
     if (!out || !plan || capacity < 1) return BZ_ERR_ARG;
     *out = nullptr;
     Plan *pl = const_cast<Plan *>(plan_internal(plan));
-    if (!pl->use_fused || pl->Nin || pl->real) return BZ_ERR_UNSUPPORTED;   // batches: fused kernel (N <= 32), circular, complex data
+    // batches: fused kernel (N <= 32), circular; the real-data form with h formed in FP64
+    if (!pl->use_fused || pl->Nin || (pl->real && !pl->h_fp64)) return BZ_ERR_UNSUPPORTED;
     bz_batch *B = new (std::nothrow) bz_batch();
     if (!B) return BZ_ERR_OOM;
     B->pl = pl;
+    B->units = pl->real ? pl->P / 2 : pl->P;
     B->capacity = capacity;
     B->gamma.assign(capacity, pl->gamma);
     const size_t n3 = (size_t)pl->N * pl->N * pl->N;
@@ -257,6 +352,7 @@ bz_status bz_batch_create(bz_batch **out, const bz_plan *plan, int capacity, int
         cudaMalloc(&B->fin64, (size_t)capacity * n3 * sizeof(double2)) != cudaSuccess ||
         cudaMalloc(&B->scr64, (size_t)capacity * n3 * sizeof(double2)) != cudaSuccess ||
         cudaMalloc(&B->h, (size_t)capacity * field) != cudaSuccess ||
+        (pl->real && cudaMalloc(&B->fsym, (size_t)capacity * field) != cudaSuccess) ||
         cudaMalloc(&B->slots_dev, (size_t)capacity * sizeof(int)) != cudaSuccess ||
         cudaMalloc(&B->count_dev, sizeof(int)) != cudaSuccess ||
         cudaMallocHost(&B->host_stage, (size_t)(capacity + 1) * sizeof(int)) != cudaSuccess ||
@@ -265,26 +361,33 @@ bz_status bz_batch_create(bz_batch **out, const bz_plan *plan, int capacity, int
         return fail(BZ_ERR_OOM);
     }
     if (upload_gsc(*B) != BZ_OK) return fail(BZ_ERR_CUDA);
-    int tb = terms_per_item;
+    int tb = pl->real && terms_per_item > 0 ? (terms_per_item + 1) / 2 : terms_per_item;   // in units
     if (tb <= 0) {
         // autotune on a trial of up to 4 instances per resident cluster
         int trial = capacity < 4 * pl->fused_G ? capacity : 4 * pl->fused_G;
-        int nblk_max = (pl->P + 15) / 16;
-        if (cudaMalloc(&B->part, (size_t)trial * nblk_max * field) != cudaSuccess) {
+        int nblk_max = (B->units + 15) / 16;
+        if (cudaMalloc(&B->part, (size_t)trial * nblk_max * field) != cudaSuccess ||
+            (pl->real && cudaMalloc(&B->part_s, (size_t)trial * nblk_max * 3 * pl->N * pl->N * sizeof(float2)) !=
+                             cudaSuccess)) {
             cudaGetLastError();
             return fail(BZ_ERR_OOM);
         }
+        if (pl->real && cudaMemset(B->fsym, 0, (size_t)trial * field) != cudaSuccess) return fail(BZ_ERR_CUDA);
         if (cudaMemset(B->fin, 0, (size_t)trial * field) != cudaSuccess ||
             cudaMemset(B->h, 0, (size_t)trial * field) != cudaSuccess) return fail(BZ_ERR_CUDA);
         tb = autotune_tb(*B, trial, B->cap_stream);
         cudaStreamSynchronize(B->cap_stream);
         cudaFree(B->part);
+        cudaFree(B->part_s);
         B->part = nullptr;
+        B->part_s = nullptr;
         if (tb <= 0) return fail(BZ_ERR_CUDA);
     }
-    B->TB = tb < pl->P ? tb : pl->P;
-    B->nblk = (pl->P + B->TB - 1) / B->TB;
-    if (cudaMalloc(&B->part, (size_t)capacity * B->nblk * field) != cudaSuccess) {
+    B->TB = tb < B->units ? tb : B->units;
+    B->nblk = (B->units + B->TB - 1) / B->TB;
+    if (cudaMalloc(&B->part, (size_t)capacity * B->nblk * field) != cudaSuccess ||
+        (pl->real && cudaMalloc(&B->part_s, (size_t)capacity * B->nblk * 3 * pl->N * pl->N * sizeof(float2)) !=
+                         cudaSuccess)) {
         cudaGetLastError();
         return fail(BZ_ERR_OOM);
     }
@@ -307,7 +410,7 @@ bz_status bz_batch_info(const bz_batch *batch, int *capacity, int *terms_per_ite
     if (!batch) return BZ_ERR_ARG;
     const size_t n3 = (size_t)batch->pl->N * batch->pl->N * batch->pl->N;
     if (capacity) *capacity = batch->capacity;
-    if (terms_per_item) *terms_per_item = batch->TB;
+    if (terms_per_item) *terms_per_item = batch->TB * (batch->pl->real ? 2 : 1);
     if (workspace_bytes)
         *workspace_bytes = (size_t)batch->capacity * n3 * (sizeof(float2) * (1 + batch->nblk) + 2 * sizeof(double2));
     return BZ_OK;
@@ -322,16 +425,21 @@ bz_status bz_batch_collide(bz_batch *batch, int count, const int *slots, const v
     bz_status s = stage_slots(B, count, slots, st);
     if (s != BZ_OK) return s;
     const int n3 = B.pl->N * B.pl->N * B.pl->N;
-    k_batch_load<<<grid_for(B), 256, 0, st>>>(fhat, dtype, B.slots_dev, B.count_dev, n3, B.fin);
-    if (B.pl->h_fp64) {
-        s = h64_launch(B.pl->N, fhat, dtype, B.slots_dev, B.count_dev, B.capacity, B.scr64, B.h, st);
+    if (!B.pl->real)
+        k_batch_load<<<grid_for(B), 256, 0, st>>>(fhat, dtype, B.slots_dev, B.count_dev, n3, B.fin);
+    if (B.pl->h_fp64) {                                   // (the real-data form's inputs come from the first pass)
+        s = h64_launch(B.pl->N, fhat, dtype, B.slots_dev, B.count_dev, B.capacity, B.scr64, B.h, st, B.fsym);
         if (s != BZ_OK) return s;
     }
     s = launch_fused(*B.pl, item_args(B), st);
     if (s != BZ_OK) return s;
-    k_batch_out<<<grid_for(B), 256, 0, st>>>(B.part, B.nblk, B.slots_dev, B.count_dev, n3, Qhat, dtype);
+    if (B.pl->real)
+        k_batch_out_real<<<grid_for(B), 256, 0, st>>>(B.part, B.part_s, B.nblk, B.slots_dev, B.count_dev, B.pl->N,
+                                                     Qhat, dtype);
+    else
+        k_batch_out<<<grid_for(B), 256, 0, st>>>(B.part, B.nblk, B.slots_dev, B.count_dev, n3, Qhat, dtype);
     BZ_CUDA_TRY(cudaGetLastError());
-    B.last_launches = 6;
+    B.last_launches = B.pl->real ? 5 : 6;
     return BZ_OK;
 }
 
@@ -353,10 +461,15 @@ bz_status bz_batch_step_rk(bz_batch *batch, int count, const int *slots, void *f
         for (int stage = 1; stage <= 4 && cs == BZ_OK; ++stage) {
             if (B.pl->h_fp64)
                 cs = h64_launch(B.pl->N, B.fin64, BZ_C128, B.slots_dev, B.count_dev, B.capacity, B.scr64, B.h,
-                                B.cap_stream);
+                                B.cap_stream, B.fsym);
             if (cs == BZ_OK) cs = launch_fused(*B.pl, item_args(B), B.cap_stream);
-            k_batch_rk_stage<<<grid_for(B), 256, 0, B.cap_stream>>>(B.part, B.nblk, B.slots_dev, B.count_dev, n3,
-                                                                   B.f0, B.fsum, B.fin, B.fin64, stage, dt);
+            if (B.pl->real)
+                k_batch_rk_stage_real<<<grid_for(B), 256, 0, B.cap_stream>>>(B.part, B.part_s, B.nblk, B.slots_dev,
+                                                                            B.count_dev, B.pl->N, B.f0, B.fsum,
+                                                                            B.fin, B.fin64, stage, dt);
+            else
+                k_batch_rk_stage<<<grid_for(B), 256, 0, B.cap_stream>>>(B.part, B.nblk, B.slots_dev, B.count_dev, n3,
+                                                                       B.f0, B.fsum, B.fin, B.fin64, stage, dt);
         }
         cudaError_t ce = cudaStreamEndCapture(B.cap_stream, &g);
         if (cs != BZ_OK || ce != cudaSuccess) {

@@ -235,6 +235,7 @@ template <int N, int C> static cudaError_t setup_nc(int *G, bool real) {
     if constexpr (pair_form<N>()) {
         if (real) {
             e = set_smem<N, C, false, true>();
+            if (e == cudaSuccess) e = set_smem<N, C, true, true>();
             return e == cudaSuccess ? occupancy<N, C, true>(G) : e;
         }
     } else {
@@ -294,7 +295,7 @@ template <int N, int C, bool SC, bool R> static bz_status launch_nc(const Plan &
 
 template <int N, int C> static bz_status launch_sc(const Plan &pl, const ItemArgs &a, cudaStream_t st) {
     if (a.real) {
-        if constexpr (pair_form<N>()) return a.gsc ? BZ_ERR_UNSUPPORTED : launch_nc<N, C, false, true>(pl, a, st);
+        if constexpr (pair_form<N>()) return a.gsc ? launch_nc<N, C, true, true>(pl, a, st) : launch_nc<N, C, false, true>(pl, a, st);
         else return BZ_ERR_UNSUPPORTED;
     }
     return a.gsc ? launch_nc<N, C, true, false>(pl, a, st) : launch_nc<N, C, false, false>(pl, a, st);

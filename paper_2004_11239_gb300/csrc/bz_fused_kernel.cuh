@@ -114,7 +114,6 @@ __device__ __forceinline__ void phase_a_pair(const float2 *__restrict__ fin, con
 template <int N, int CC, bool SCALED, bool REAL = false>
 __global__ void __launch_bounds__(FK<N, CC, REAL>::THREADS, FK<N, CC, REAL>::MIN_BLOCKS)
 k_fused(ItemArgs a) {
-    static_assert(!(SCALED && REAL), "the pair form has no per-instance radial scale");
     static_assert(!REAL || 32 % N == 0, "the pair form shuffles within the lanes of one plane");
     using K = FK<N, CC, REAL>;
     constexpr int TWN = REAL ? 6 * N : 3 * N;                // twiddles per unit
@@ -221,7 +220,7 @@ k_fused(ItemArgs a) {
             }
             fetch_tw(p + 1 < t1 ? p + 1 : -1, buf ^ 1);
             float sc = 1.f;
-            if constexpr (SCALED) sc = a.gsc[(size_t)slot * a.N_rho + p / a.M];
+            if constexpr (SCALED) sc = a.gsc[(size_t)slot * a.N_rho + (REAL ? 2 * p : p) / a.M];   // a pair shares its node
             // A
             if constexpr (REAL) phase_a_pair<N>(fin, stw + buf * TWN, my, k1, lane);
             else phase_a<N>(fin, stw + buf * TWN, my, k1, lane);
@@ -273,7 +272,8 @@ k_fused(ItemArgs a) {
                 if (k1 == N / 2) {                            // whole plane (warp-uniform)
                     #pragma unroll
                     for (int i = 0; i < N; ++i) {
-                        const float2 c = sc1[i * N + lane];
+                        float2 c = sc1[i * N + lane];
+                        if constexpr (SCALED) { c.x *= sc; c.y *= sc; }
                         float2 v = xs1[i * N + lane];
                         v.x = fmaf(x[i].x, c.x, fmaf(-x[i].y, c.y, v.x));
                         v.y = fmaf(x[i].x, c.y, fmaf(x[i].y, c.x, v.y));
@@ -287,7 +287,10 @@ k_fused(ItemArgs a) {
                     const float zi = __shfl_sync(0xffffffffu, x[i].y, N / 2, N);
                     if (i == lane) z3 = make_float2(zr, zi);
                 }
-                const float2 c2 = sc2[pid * N + lane], c3 = sc3[pid * N + lane];
+                float2 c2 = sc2[pid * N + lane], c3 = sc3[pid * N + lane];
+                if constexpr (SCALED) {                       // the pair's radial scale (one node per pair)
+                    c2.x *= sc; c2.y *= sc; c3.x *= sc; c3.y *= sc;
+                }
                 const float2 z2 = x[N / 2];
                 x2.x = fmaf(z2.x, c2.x, fmaf(-z2.y, c2.y, x2.x));
                 x2.y = fmaf(z2.x, c2.y, fmaf(z2.y, c2.x, x2.y));

@@ -58,6 +58,7 @@ __device__ __forceinline__ void t_st16(uint32_t ta, const float *v) {
                    "r"(__float_as_uint(v[15])) : "memory");
 }
 
+template <bool SCALED>
 __global__ void __launch_bounds__(PT, 3) k_pair3(ItemArgs a) {
     constexpr int N = PN, C = PC, PPC = PPP, LD = PLD, TWN = 6 * N;
     extern __shared__ __align__(16) float2 smem[];
@@ -129,6 +130,9 @@ __global__ void __launch_bounds__(PT, 3) k_pair3(ItemArgs a) {
         }
         for (int p = t0; p < t1; ++p) {
             const float2 *ap = a.alpha + ((size_t)p * N + (size_t)rank * PPC) * N * N;   // the CTA's A tile
+            // batches: the instance's radial scale r_i^(gamma_b - gamma_plan) of the pair's node
+            float sc = 1.f;
+            if constexpr (SCALED) sc = a.gsc[(size_t)slot * a.N_rho + (2 * p) / a.M];
             if (tid == 0)
                 asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(ap),
                              "r"((uint32_t)(PPC * N * N * sizeof(float2))) : "memory");
@@ -217,15 +221,16 @@ __global__ void __launch_bounds__(PT, 3) k_pair3(ItemArgs a) {
                 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
                     const float2 z = x[8 * g + u];
-                    s[2 * u] = fmaf(z.x, al[u].x, fmaf(-z.y, al[u].y, s[2 * u]));
-                    s[2 * u + 1] = fmaf(z.x, al[u].y, fmaf(z.y, al[u].x, s[2 * u + 1]));
+                    const float2 A = make_float2(sc * al[u].x, sc * al[u].y);
+                    s[2 * u] = fmaf(z.x, A.x, fmaf(-z.y, A.y, s[2 * u]));
+                    s[2 * u + 1] = fmaf(z.x, A.y, fmaf(z.y, A.x, s[2 * u + 1]));
                 }
                 t_st16(tl + TM_ACC + 16 * g, s);
             }
             if (k1 == N / 2) {
                 #pragma unroll
                 for (int i = 0; i < N; ++i) {
-                    const float2 c = sc1[i * N + lane];
+                    const float2 c = make_float2(sc * sc1[i * N + lane].x, sc * sc1[i * N + lane].y);
                     float2 v = xs1[i * N + lane];
                     v.x = fmaf(x[i].x, c.x, fmaf(-x[i].y, c.y, v.x));
                     v.y = fmaf(x[i].x, c.y, fmaf(x[i].y, c.x, v.y));
@@ -239,7 +244,8 @@ __global__ void __launch_bounds__(PT, 3) k_pair3(ItemArgs a) {
                 const float zi = __shfl_sync(0xffffffffu, x[i].y, N / 2, N);
                 if (i == lane) z3 = make_float2(zr, zi);
             }
-            const float2 c2 = sc2[pid * N + lane], c3 = sc3[pid * N + lane];
+            const float2 c2 = make_float2(sc * sc2[pid * N + lane].x, sc * sc2[pid * N + lane].y);
+            const float2 c3 = make_float2(sc * sc3[pid * N + lane].x, sc * sc3[pid * N + lane].y);
             const float2 zz = x[N / 2];
             x2.x = fmaf(zz.x, c2.x, fmaf(-zz.y, c2.y, x2.x));
             x2.y = fmaf(zz.x, c2.y, fmaf(zz.y, c2.x, x2.y));
@@ -297,7 +303,7 @@ cudaLaunchConfig_t pair3_config(int G, cudaStream_t st, cudaLaunchAttribute *att
 
 cudaError_t pair3_setup(int *G) {
     *G = 0;
-    for (const void *k : {(const void *)k_pair3, (const void *)k_pair3_shape}) {
+    for (const void *k : {(const void *)k_pair3<false>, (const void *)k_pair3<true>, (const void *)k_pair3_shape}) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P_SMEM);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         if (e != cudaSuccess) return e;
@@ -310,10 +316,11 @@ cudaError_t pair3_setup(int *G) {
 }
 
 bz_status launch_pair3(const Plan &pl, const ItemArgs &a, cudaStream_t st) {
-    if (pl.N != PN || !a.real || !a.hg || a.gsc) return BZ_ERR_UNSUPPORTED;
+    if (pl.N != PN || !a.real || !a.hg) return BZ_ERR_UNSUPPORTED;
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = pair3_config(pl.fused_G, st, attr);
-    BZ_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_pair3, a));
+    if (a.gsc) BZ_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_pair3<true>, a));
+    else BZ_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_pair3<false>, a));
     BZ_CUDA_TRY(cudaGetLastError());
     return BZ_OK;
 }

@@ -14,20 +14,11 @@
 // the kernel also accumulates X = sum of C Z with C(k) = conj B(-k), and Q(k) = V(k) +
 // conj X(-k).  Q is eq. realQ applied to fs, every mode kept.
 #include "bz_internal.h"
+#include "bz_real.cuh"
 
 namespace bz {
 
 namespace {
-
-// Flat index of -k (mod N per axis) and whether k has an index N/2 (signed -N/2).
-__device__ __forceinline__ bool nyquist(int i1, int i2, int i3, int N) {
-    const int h = N / 2;
-    return i1 == h || i2 == h || i3 == h;
-}
-__device__ __forceinline__ size_t mirror(int i1, int i2, int i3, int N) {
-    const int m1 = (N - i1) % N, m2 = (N - i2) % N, m3 = (N - i3) % N;
-    return ((size_t)m1 * N + m2) * N + m3;
-}
 
 // fs (FP32 and FP64) from the caller's array (c64 or c128).
 __global__ void k_sym_in(const void *__restrict__ f, int dtype, int N, float2 *__restrict__ fs,
@@ -52,15 +43,6 @@ __global__ void k_sym_in(const void *__restrict__ f, int dtype, int N, float2 *_
     }
     fs[k] = make_float2((float)v.x, (float)v.y);
     fs64[k] = v;
-}
-
-// Position of a Nyquist-plane mode in the [3][N][N] family layout of X and C: k1 = -N/2 ->
-// family 0 [k2][k3]; else k3 = -N/2 -> family 2 [k1][k2]; else (k2 = -N/2) family 1 [k1][k3].
-__device__ __forceinline__ int family_index(int i1, int i2, int i3, int N) {
-    const int h = N / 2;
-    if (i1 == h) return i2 * N + i3;
-    if (i3 == h) return 2 * N * N + i1 * N + i2;
-    return N * N + i1 * N + i3;
 }
 
 // Kahan-compensated FP32 sum.

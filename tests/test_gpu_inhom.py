@@ -59,21 +59,22 @@ def test_transport_density_wave_closed_form_and_reversal(bz):
     assert np.max(np.abs(fd.cpu().numpy() - f0)) < 1e-12 * np.max(np.abs(f0))
 
 
-def test_inhom_strang_steps_match_oracle(bz):
+@pytest.mark.parametrize("real", [False, True])
+def test_inhom_strang_steps_match_oracle(bz, real):
     N, L, nx, Lx, dt, steps = 8, 6.0, 8, 3.0, 0.1, 2
     R = bi.R_from_L(L)
     f0 = bi.inhom_cells(N, L, nx, Lx)
-    plan = bz.bz_plan_create(N, L, R, 0.0, 0.5, 2, 12)
+    plan = bz.bz_plan_create_ex(N, L, R, 0.0, 0.5, 2, 12, data=bz.BZ_DATA_REAL if real else bz.BZ_DATA_COMPLEX)
     batch = bz.bz_batch_create(plan, nx, 0)
     fd = torch.from_numpy(f0).cuda()
     bz.bz_inhom_step(batch, nx, Lx, fd, dt, steps)
     torch.cuda.synchronize()
     got = fd.cpu().numpy()
     op = spectral.OraclePlan(N, L, R, 0.0, kernels.Kernel("family", 0.5), 2, 12)
-    ref = inhom.strang(op, f0, Lx, dt, steps)
+    ref = inhom.strang(op, f0, Lx, dt, steps, real=real)
     err = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref - f0)))
     coll = float(np.max(np.abs(ref - inhom.transport(f0, L, Lx, dt * steps))) / np.max(np.abs(ref - f0)))
-    print(f"inhom Strang N={N} nx={nx} {steps} steps: rel_Linf of the change={err:.2e} "
+    print(f"inhom Strang N={N} nx={nx} {steps} steps ({'real' if real else 'complex'} form): rel_Linf of the change={err:.2e} "
           f"(collision share of the change {coll:.2f})")
     assert err <= 1e-5
     mass0, mass1 = inhom.density(f0, L).sum(), inhom.density(got, L).sum()

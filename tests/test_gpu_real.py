@@ -101,7 +101,6 @@ def test_real_term_ranges_fp32_input_and_refusals(bz):
     assert _rel(got32, full) <= TOL
     f = torch.from_numpy(fhat).cuda()
     for call in (lambda: bz.bz_collide_terms(plan, 1, 10, f, torch.empty_like(f)),      # odd bound
-                 lambda: bz.bz_batch_create(plan, 2, 0),
                  lambda: bz.bz_collide_noalloc(plan, f, torch.empty_like(f))):
         with pytest.raises(bz.BzError):
             call()
@@ -177,3 +176,46 @@ def test_real_form_at_full_size(bz, ctas):
         assert e_real / scale <= TOL
     pr.close()
     pc.close()
+
+
+@pytest.mark.parametrize("N,ctas", [(16, 0), (32, 2), (32, 3)])
+def test_real_batch_matches_oracle_and_is_batch_invariant(bz, N, ctas):
+    """Batches of a real-data plan: per-slot gamma (the radial scale of a pair's node), the
+    batched collide and RK4 against the oracle's real-data reading, and the same bits alone and
+    in the batch."""
+    L = 10.0
+    R = bi.R_from_L(L)
+    plan = _real_plan(bz, N, L, R, 0.0, 0.5, 2, 12, ctas_per_sm=ctas)
+    cap = 4
+    batch = bz.bz_batch_create(plan, cap, 0)
+    gam = {2: -1.0, 0: 0.0, 3: -2.0}
+    for slot, g in gam.items():
+        bz.bz_batch_set_gamma(batch, slot, g)
+    f = np.stack([bi.random_mixture(N, L, seed=500 + b) for b in range(cap)])
+    fd = torch.from_numpy(f).cuda()
+    qd = torch.zeros_like(fd)
+    bz.bz_batch_collide(batch, [2, 0, 3], fd, qd)
+    torch.cuda.synchronize()
+    q = qd.cpu().numpy()
+    ops = {g: spectral.OraclePlan(N, L, R, g, kernels.Kernel("family", 0.5), 2, 12) for g in set(gam.values())}
+    for slot, g in gam.items():
+        err = _rel(q[slot], spectral.collide_real(ops[g], f[slot]))
+        print(f"real batch N={N} ({bz.bz_plan_pipeline(plan)['kernel']}) slot {slot} gamma={g}: rel_Linf={err:.2e}")
+        assert err <= TOL
+    assert np.all(q[1] == 0)
+    alone = torch.zeros_like(fd)
+    bz.bz_batch_collide(batch, [3], fd, alone)
+    torch.cuda.synchronize()
+    assert np.array_equal(alone.cpu().numpy()[3], q[3])      # the same bits alone and in the batch
+    fr = fd.clone()
+    bz.bz_batch_step_rk(batch, [0, 2], fr, 0.05, 2)
+    torch.cuda.synchronize()
+    got = fr.cpu().numpy()
+    for slot in (0, 2):
+        ref = spectral.rk4_real(ops[gam[slot]], f[slot], 0.05, 2)
+        err = _rel(got[slot] - f[slot], ref - f[slot])
+        print(f"real batch RK4 slot {slot}: rel_Linf of the change = {err:.2e}")
+        assert err <= TOL
+    assert np.array_equal(got[1], f[1]) and np.array_equal(got[3], f[3])   # inactive slots untouched
+    batch.close()
+    plan.close()
