@@ -119,7 +119,8 @@ enum { BZ_H_AUTO = 0, BZ_H_FP64 = 1, BZ_H_FP32 = 2 };
  *                    without Nyquist content the result is eq. realQ itself.  Half the transforms,
  *                    exchanges and (nearly) table bytes per term.  3D, FP32, circular, fused
  *                    pipeline, N = 8, 16 or 32, M even; bz_collide_terms takes even term bounds;
- *                    batches and bz_collide_noalloc return BZ_ERR_UNSUPPORTED. */
+ *                    batches need h in FP64 (the default); bz_collide_noalloc returns
+ *                    BZ_ERR_UNSUPPORTED. */
 enum { BZ_DATA_COMPLEX = 0, BZ_DATA_REAL = 1 };
 
 typedef struct bz_plan bz_plan;
