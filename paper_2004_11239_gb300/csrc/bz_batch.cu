@@ -439,7 +439,7 @@ bz_status bz_batch_collide(bz_batch *batch, int count, const int *slots, const v
     else
         k_batch_out<<<grid_for(B), 256, 0, st>>>(B.part, B.nblk, B.slots_dev, B.count_dev, n3, Qhat, dtype);
     BZ_CUDA_TRY(cudaGetLastError());
-    B.last_launches = B.pl->real ? 5 : 6;
+    B.last_launches = (B.pl->real ? 2 : 3) + (B.pl->h_fp64 ? h64_launches(B.pl->N) : 0);
     return BZ_OK;
 }
 
@@ -487,7 +487,7 @@ bz_status bz_batch_step_rk(bz_batch *batch, int count, const int *slots, void *f
     for (int step = 0; step < nsteps; ++step) BZ_CUDA_TRY(cudaGraphLaunch(it->second, st));
     k_batch_rk_out<<<grid_for(B), 256, 0, st>>>(B.f0, B.slots_dev, B.count_dev, n3, fhat, dtype);
     BZ_CUDA_TRY(cudaGetLastError());
-    B.last_launches = 2 + 20 * nsteps;
+    B.last_launches = 2 + 4 * (2 + (B.pl->h_fp64 ? h64_launches(B.pl->N) : 0)) * nsteps;
     return BZ_OK;
 }
 

@@ -115,14 +115,91 @@ k_h64_warp(const void *f, int dtype, const int *slots, const int *count_dev, dou
     else scr[o] = v;
 }
 
+// One line transform of length 32 across the lanes of a warp (radix-2 decimation in frequency,
+// as k_h64_warp): lane l holds x_l on entry and X_bitrev(l) on return.
+__device__ __forceinline__ double2 warp_fft32(double2 v, int l) {
+    int st = 0;
+    #pragma unroll
+    for (int hs = 16; hs >= 1; hs >>= 1, ++st) {
+        const double2 tw = c_twd.v[tw_off<32>() + (l % hs) * (32 / (2 * hs))];
+        double2 p;
+        p.x = __shfl_xor_sync(0xffffffffu, v.x, hs);
+        p.y = __shfl_xor_sync(0xffffffffu, v.y, hs);
+        if (l & hs) v = cmul(csub(p, v), tw);
+        else v = cadd(v, p);
+    }
+    return v;
+}
+
+// N = 32: the first two FP64 passes (axes k3 and k2, both inside a plane k1) in one kernel.  A
+// cluster of 4 CTAs holds one plane: CTA r transforms the k3 lines of rows k2 = 8r .. 8r + 7 (one
+// warp per line) into its shared memory, and after a cluster barrier the k2 lines of columns
+// j3 = 8r .. 8r + 7, gathering each line from the four CTAs (DSMEM), into scr for the k1 pass.
+// fsym: as k_h64_warp<N, 3>.  Grid (32 planes x 4, instances).
+__global__ void __launch_bounds__(256) k_h64_plane32(const void *f, int dtype, const int *slots, const int *count_dev,
+                                                    double2 *scr, float2 *fsym) {
+    constexpr int N = 32, N2 = N * N;
+    __shared__ double2 rows[8][N];                           // [k2 - 8r][j3]
+    const int b = blockIdx.y;
+    if (count_dev && b >= *count_dev) return;               // uniform over the cluster
+    const int slot = slots ? slots[b] : b;
+    const int r = (int)cooperative_groups::this_cluster().block_rank();
+    const int k1 = blockIdx.x / 4, w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    const size_t vol = (size_t)slot * N * N2;
+    {                                                        // k3 line of row k2 = 8r + w
+        const int k2 = 8 * r + w;
+        const size_t base = vol + ((size_t)k1 * N + k2) * N;
+        double2 v;
+        if (!fsym) {
+            v = load_c(f, dtype, base + l);
+        } else {
+            const int h2 = N / 2;
+            v = make_double2(0.0, 0.0);
+            if (k1 != h2 && k2 != h2 && l != h2) {
+                const double2 a = load_c(f, dtype, base + l);
+                const double2 c = load_c(f, dtype, vol + ((size_t)((N - k1) % N) * N + (N - k2) % N) * N + (N - l) % N);
+                v = make_double2(0.5 * (a.x + c.x), 0.5 * (a.y - c.y));
+            }
+            fsym[base + l] = make_float2((float)v.x, (float)v.y);
+        }
+        rows[w][bitrev_n<N>(l)] = warp_fft32(v, l);
+    }
+    cooperative_groups::this_cluster().sync();
+    {                                                        // k2 line of column j3 = 8r + w
+        const int j3 = 8 * r + w;
+        const uint32_t src = dsmem_addr(&rows[l % 8][j3], (uint32_t)(l / 8));   // element (k2 = l, j3)
+        double2 v;
+        asm volatile("ld.shared::cluster.v2.f64 {%0, %1}, [%2];\n" : "=d"(v.x), "=d"(v.y) : "r"(src) : "memory");
+        v = warp_fft32(v, l);
+        scr[vol + ((size_t)k1 * N + bitrev_n<N>(l)) * N + j3] = v;
+    }
+    cooperative_groups::this_cluster().sync();               // no CTA leaves while its rows are read
+}
+
 template <int N>
 static bz_status h64_n(const void *f, int dtype, const int *slots, const int *count_dev, int count, double2 *scr,
                        float2 *h, float2 *fsym, cudaStream_t st) {
     if constexpr ((N & (N - 1)) == 0) {
         constexpr int LINES = 8 * (32 / N);
         const dim3 grid((N * N + LINES - 1) / LINES, count);
-        k_h64_warp<N, 3><<<grid, 256, 0, st>>>(f, dtype, slots, count_dev, scr, h, fsym);
-        k_h64_warp<N, 2><<<grid, 256, 0, st>>>(f, dtype, slots, count_dev, scr, h, nullptr);
+        if constexpr (N == 32) {
+            // axes k3 and k2 in one clustered pass, then the k1 pass
+            cudaLaunchConfig_t cfg = {};
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = 4;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.gridDim = dim3(4 * N, count);
+            cfg.blockDim = dim3(256);
+            cfg.stream = st;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            BZ_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_h64_plane32, f, dtype, slots, count_dev, scr, fsym));
+        } else {
+            k_h64_warp<N, 3><<<grid, 256, 0, st>>>(f, dtype, slots, count_dev, scr, h, fsym);
+            k_h64_warp<N, 2><<<grid, 256, 0, st>>>(f, dtype, slots, count_dev, scr, h, nullptr);
+        }
         k_h64_warp<N, 1><<<grid, 256, 0, st>>>(f, dtype, slots, count_dev, scr, h, nullptr);
     } else {
         if (fsym) return BZ_ERR_UNSUPPORTED;
@@ -354,7 +431,7 @@ bz_status collide_fused(Plan &pl, int p0, int p1, cudaStream_t st, int *launches
         s = h64_launch(pl.N, src, src_dtype, nullptr, nullptr, 1, pl.scr64, pl.h, st, pl.real ? pl.fsym : nullptr);
         if (s != BZ_OK) return s;
         tm_end(pl, st, TK_OTHER);
-        nl += 3;
+        nl += h64_launches(pl.N);
     } else {
         a.hg = nullptr;                                   // h formed in FP32 in the item prologue
     }

@@ -138,6 +138,8 @@ int fused_candidates(int N, int *cs);
 cudaError_t fused_setup(int N, int C, int *G, bool real);
 bz_status launch_fused(const Plan &pl, const ItemArgs &a, cudaStream_t st);
 // h[slot] = IFFT(f[slot]) computed in FP64 and stored FP32 for the active slots (N <= 32).
+// Kernel launches of one h64_launch: three line passes (N = 32: the k3 and k2 passes as one).
+inline int h64_launches(int N) { return N == 32 ? 2 : 3; }
 // fsym (BZ_DATA_REAL, N a power of two): transform the Hermitian, Nyquist-free part of f and
 // store that part in FP32 to fsym.
 bz_status h64_launch(int N, const void *f, int dtype, const int *slots, const int *count_dev, int count,
