@@ -70,3 +70,44 @@ def test_plant_transposed_axis_breaks_library_dft_pin(monkeypatch):
         y = np.einsum("cb,abd->acd", W, y)
         return np.einsum("db,acb->adc", W, y)   # last two axes swapped
     assert not np.allclose(bad(x, -1), np.fft.fftn(x), atol=1e-9)
+
+
+def test_plant_real_band_without_conjugate_breaks_identity_pin(monkeypatch):
+    """real_band with the mirror taken without conjugation is not the identity on a real f."""
+    N = 8
+    u = bi.SplitMix64(3).uniform(N ** 3).reshape(N, N, N)
+    fh = np.fft.fftn(u - 0.5) / N ** 3
+    fh[spectral.nyquist_mask(N)] = 0
+    assert np.max(np.abs(spectral.real_band(fh) - fh)) < 1e-15
+
+    def bad(f):
+        f = np.asarray(f, dtype=np.complex128)
+        out = 0.5 * (f + spectral.mirror(f))
+        out[spectral.nyquist_mask(f.shape[0])] = 0.0
+        return out
+    monkeypatch.setattr(spectral, "real_band", bad)
+    assert np.max(np.abs(spectral.real_band(fh) - fh)) > 1e-6
+
+
+def test_plant_streaming_phase_sign_breaks_density_wave_pin(monkeypatch):
+    """Free streaming with the phase conjugated moves the drifting wave the wrong way."""
+    from oracle import inhom
+    N, L, nx, Lx, eps, u, T, t = 32, 6.0, 8, 4.0, 0.3, 0.7, 0.5, 0.37
+    f0 = bi.drifting_wave_samples(N, L, nx, Lx, eps, u, T)
+    x = np.arange(nx) * Lx / nx
+    exact = 1 + eps * math.exp(-(2 * math.pi * t / Lx) ** 2 * T / 2) * np.cos(2 * math.pi * (x - u * t) / Lx)
+    assert np.max(np.abs(inhom.density(inhom.transport(f0, L, Lx, t), L) - exact)) < 1e-12
+    monkeypatch.setattr(inhom, "transport", _transport_flipped)
+    assert np.max(np.abs(inhom.density(inhom.transport(f0, L, Lx, t), L) - exact)) > 1e-3
+
+
+def _transport_flipped(fcells, L, Lx, t):
+    from oracle import inhom
+    nx, N = fcells.shape[0], fcells.shape[1]
+    fv = np.stack([spectral.to_grid(fcells[c], L) for c in range(nx)])
+    v1 = -L + 2.0 * L * np.arange(N) / N
+    kappa = spectral.signed(nx).astype(np.float64)
+    gx = np.einsum("ab,bijk->aijk", inhom._x_dft_matrix(nx, -1), fv)
+    gx = gx * np.exp(+2j * math.pi * np.outer(kappa, v1) * t / Lx)[:, :, None, None]     # wrong sign
+    fv = np.einsum("ab,bijk->aijk", inhom._x_dft_matrix(nx, +1), gx) / nx
+    return np.stack([inhom._to_coeffs(fv[c]) for c in range(nx)])
