@@ -31,9 +31,9 @@ void free_plan(bz::Plan &p) {
     cudaFree(p.term_dev); cudaFree(p.S); cudaFree(p.h); cudaFree(p.fin); cudaFree(p.acc);
     cudaFree(p.rk); cudaFree(p.mom); cudaFree(p.part); cudaFree(p.fin64); cudaFree(p.scr64);
     cudaFree(p.wimg); cudaFree(p.dev_err); cudaFree(p.apair); cudaFree(p.fsym); cudaFree(p.fsym64);
-    cudaFree(p.cpair); cudaFree(p.part_s);
+    cudaFree(p.cpair); cudaFree(p.part_s); cudaFree(p.S_s); cudaFree(p.acc_s);
     p.wimg = nullptr; p.dev_err = nullptr; p.apair = nullptr; p.fsym = nullptr; p.fsym64 = nullptr;
-    p.cpair = nullptr; p.part_s = nullptr;
+    p.cpair = nullptr; p.part_s = nullptr; p.S_s = nullptr; p.acc_s = nullptr;
     p.part = nullptr; p.fin64 = nullptr; p.scr64 = nullptr; p.src = nullptr;
     p.alpha = nullptr; p.tw = nullptr; p.rule_buf = nullptr; p.rule_off = nullptr;
     p.term_dev = nullptr; p.S = nullptr; p.h = nullptr; p.fin = nullptr; p.acc = nullptr;
@@ -145,8 +145,9 @@ bz_status create(bz_plan **out, const bz_plan_desc *d) {
     if (d->pipeline < BZ_PIPE_AUTO || d->pipeline > BZ_PIPE_CHUNKED) return BZ_ERR_ARG;
     if (d->data != BZ_DATA_COMPLEX && d->data != BZ_DATA_REAL) return BZ_ERR_ARG;
     const bool real = d->data == BZ_DATA_REAL;
-    if (real && (dim != 3 || d->precision != BZ_PREC_FP32 || padded || 32 % d->N != 0 || d->M % 2 != 0 ||
-                 d->pipeline == BZ_PIPE_CHUNKED))
+    // the real-data form: fused for N dividing 32, the chunked pipeline otherwise (or on request)
+    if (real && (dim != 3 || d->precision != BZ_PREC_FP32 || padded || d->M % 2 != 0 ||
+                 (d->pipeline == BZ_PIPE_FUSED && 32 % d->N != 0)))
         return BZ_ERR_UNSUPPORTED;
     if (d->ctas_per_sm == 3 && !(real && d->N == 32 && d->h_precision != BZ_H_FP32)) return BZ_ERR_UNSUPPORTED;
     if (d->ctas_per_sm > 0 && d->ctas_per_sm != 2 && d->ctas_per_sm != 3) return BZ_ERR_UNSUPPORTED;
@@ -213,9 +214,11 @@ bz_status create(bz_plan **out, const bz_plan_desc *d) {
         const size_t ns = (size_t)3 * N * N;
         if ((s = dmalloc(&pl.apair, (size_t)(pl.P / 2) * field)) == BZ_OK &&
             (s = dmalloc(&pl.cpair, (size_t)(pl.P / 2) * ns * sizeof(float2))) == BZ_OK &&
+            (s = dmalloc(&pl.S_s, (size_t)pl.chunk * ns * sizeof(float2))) == BZ_OK &&
+            (s = dmalloc(&pl.acc_s, ns * sizeof(double2))) == BZ_OK &&
             (s = dmalloc(&pl.fsym, field)) == BZ_OK && (s = dmalloc(&pl.fsym64, n3 * sizeof(double2))) == BZ_OK)
             s = bz::build_pair_table(pl);
-        pl.ws_bytes += field + n3 * sizeof(double2);
+        pl.ws_bytes += field + n3 * sizeof(double2) + (size_t)pl.chunk * ns * sizeof(float2) + ns * sizeof(double2);
     }
     if (s != BZ_OK) {
         free_plan(pl);
@@ -245,7 +248,7 @@ bz_status create(bz_plan **out, const bz_plan_desc *d) {
             if (select_fused(pl, d->cluster, d->ctas_per_sm) != BZ_OK) cudaGetLastError();
         }
     }
-    if ((d->pipeline == BZ_PIPE_FUSED || pl.precision == BZ_PREC_BF16X3 || pl.real) && !pl.use_fused) {
+    if ((d->pipeline == BZ_PIPE_FUSED || pl.precision == BZ_PREC_BF16X3) && !pl.use_fused) {
         free_plan(pl);
         delete h;
         return BZ_ERR_UNSUPPORTED;

@@ -28,7 +28,9 @@ template <int N> struct Cfg {
 // ---------------------------------------------------------------------------------------
 // plane_inv: one CTA holds PPC planes k1 of one term; N threads per plane.
 // ---------------------------------------------------------------------------------------
-template <int N>
+// PAIR (BZ_DATA_REAL): unit t is the term pair (2u, 2u + 1), u = p0 + t, and the twiddle is
+// beta_2u + i beta_2u+1 (both terms' [3][N] vectors, contiguous).
+template <int N, bool PAIR = false>
 __global__ void __launch_bounds__(Cfg<N>::THREADS)
 k_plane_inv(const float2 *__restrict__ fin, const float2 *__restrict__ tw, float2 *__restrict__ S,
             int p0, int use_tw) {
@@ -39,13 +41,21 @@ k_plane_inv(const float2 *__restrict__ fin, const float2 *__restrict__ tw, float
     const int t = blockIdx.y;
     float2 *s = sm + pid * N * LD;
     const float2 *f = fin + (size_t)k1 * N * N;
-    const float2 *twp = tw + (size_t)(p0 + t) * 3 * N;
-    float2 t13 = make_float2(1.f, 0.f);
+    const float2 *twp = tw + (size_t)(p0 + t) * (PAIR ? 6 : 3) * N;
+    float2 t13 = make_float2(1.f, 0.f), t13b = make_float2(0.f, 0.f);
     if (use_tw) t13 = cmul(twp[k1], twp[2 * N + lane]);
+    if (PAIR && use_tw) t13b = cmul(twp[3 * N + k1], twp[5 * N + lane]);
     #pragma unroll 4
     for (int i = 0; i < N; ++i) {
         float2 v = f[i * N + lane];
-        if (use_tw) v = cmul(v, cmul(t13, twp[N + i]));
+        if (use_tw) {
+            if constexpr (PAIR) {
+                const float2 u = cmul(t13, twp[N + i]), w = cmul(t13b, twp[4 * N + i]);
+                v = cmul(v, make_float2(u.x - w.y, u.y + w.x));
+            } else {
+                v = cmul(v, cmul(t13, twp[N + i]));
+            }
+        }
         s[i * LD + lane] = v;
     }
     __syncthreads();
@@ -68,6 +78,7 @@ k_plane_inv(const float2 *__restrict__ fin, const float2 *__restrict__ tw, float
 // pencil: one thread per (j2, j3) line along axis 1 of one term.
 //   MODE 0: out = IFFT_1(S)                         (forms h)
 //   MODE 1: S = FFT_1( h . IFFT_1(S) )              (in place)
+//   MODE 2: as MODE 1 with the real part of h (BZ_DATA_REAL: h is real)
 // ---------------------------------------------------------------------------------------
 template <int N, int MODE>
 __global__ void __launch_bounds__(128, 3)
@@ -85,7 +96,15 @@ k_pencil(float2 *__restrict__ S, const float2 *__restrict__ h, float2 *__restric
         for (int j = 0; j < N; ++j) out[j * N2 + g] = x[j];
     } else {
         #pragma unroll
-        for (int j = 0; j < N; ++j) x[j] = cmul(x[j], h[j * N2 + g]);
+        for (int j = 0; j < N; ++j) {
+            if constexpr (MODE == 2) {
+                const float hv = h[j * N2 + g].x;
+                x[j].x *= hv;
+                x[j].y *= hv;
+            } else {
+                x[j] = cmul(x[j], h[j * N2 + g]);
+            }
+        }
         fft_inplace<N, -1>(x);                   // axis 1: j1 -> k1
         #pragma unroll
         for (int k = 0; k < N; ++k) base[k * N2] = x[k];
@@ -95,9 +114,12 @@ k_pencil(float2 *__restrict__ S, const float2 *__restrict__ h, float2 *__restric
 // ---------------------------------------------------------------------------------------
 // plane_fwd: forward transform along axes 2 and 3, times alpha_p, in place.
 // ---------------------------------------------------------------------------------------
-template <int N>
+// PAIR (BZ_DATA_REAL): alpha is the pair table A, and the chunk's Nyquist sums X = C Z go to
+// Ss[t][3][N][N] (family layout; every entry written, zero where C is zero).
+template <int N, bool PAIR = false>
 __global__ void __launch_bounds__(Cfg<N>::THREADS)
-k_plane_fwd(float2 *__restrict__ S, const float2 *__restrict__ alpha, int p0) {
+k_plane_fwd(float2 *__restrict__ S, const float2 *__restrict__ alpha, int p0, const float2 *__restrict__ cpair = nullptr,
+            float2 *__restrict__ Ss = nullptr) {
     constexpr int PPC = Cfg<N>::PPC, LD = Cfg<N>::LD;
     extern __shared__ float2 sm[];
     const int lane = threadIdx.x % N, pid = threadIdx.x / N;
@@ -121,6 +143,17 @@ k_plane_fwd(float2 *__restrict__ S, const float2 *__restrict__ alpha, int p0) {
     const float2 *al = alpha + (size_t)(p0 + t) * N * N * N + (size_t)k1 * N * N;
     #pragma unroll 4
     for (int i = 0; i < N; ++i) pl[i * N + lane] = cmul(s[i * LD + lane], al[i * N + lane]);
+    if constexpr (PAIR) {
+        const float2 *cq = cpair + (size_t)(p0 + t) * 3 * N * N;
+        float2 *xs = Ss + (size_t)t * 3 * N * N;
+        // family k2 = -N/2 at [k1][k3 = lane]; family k3 = -N/2 at [k1][k2 = lane]
+        xs[N * N + k1 * N + lane] = cmul(s[(N / 2) * LD + lane], cq[N * N + k1 * N + lane]);
+        xs[2 * N * N + k1 * N + lane] = cmul(s[lane * LD + N / 2], cq[2 * N * N + k1 * N + lane]);
+        if (k1 == N / 2) {                                    // the plane k1 = -N/2: [k2][k3]
+            #pragma unroll 4
+            for (int i = 0; i < N; ++i) xs[i * N + lane] = cmul(s[i * LD + lane], cq[i * N + lane]);
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -206,18 +239,20 @@ int supported_N(int N) {
 }
 
 template <int N> static cudaError_t set_attrs() {
-    cudaError_t e = cudaFuncSetAttribute(k_plane_inv<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)Cfg<N>::SMEM);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_plane_fwd<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)Cfg<N>::SMEM);
+    const void *ks[4] = {(const void *)k_plane_inv<N, false>, (const void *)k_plane_inv<N, true>,
+                         (const void *)k_plane_fwd<N, false>, (const void *)k_plane_fwd<N, true>};
+    for (const void *k : ks) {
+        const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg<N>::SMEM);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 // Terms per chunk: as many as one wave of plane CTAs holds (resident CTAs / CTAs per term),
 // capped by an L2-sized scratch of 32 MB.
 template <int N> static int chunk_for() {
     int per_sm = 0, dev = 0, sms = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_plane_inv<N>, Cfg<N>::THREADS, Cfg<N>::SMEM) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_plane_inv<N, false>, Cfg<N>::THREADS, Cfg<N>::SMEM) !=
         cudaSuccess) {
         cudaGetLastError();
         per_sm = 1;
@@ -254,14 +289,62 @@ cudaError_t collide_set_attributes(int N) {
     return cudaErrorInvalidValue;
 }
 
+// BZ_DATA_REAL: the Hermitian part of the input (sym_input) feeds h and the pair passes; the
+// chunks run over term pairs [p0 / 2, p1 / 2) with the pair table A, the Nyquist sums X are
+// reduced beside V, and Q is symmetrised after the last chunk.
+template <int N>
+static bz_status run_chunks_real(Plan &pl, int p0, int p1, cudaStream_t st, int *launches) {
+    constexpr int PPC = Cfg<N>::PPC;
+    const int n3 = N * N * N, ns = 3 * N * N;
+    if ((p0 | p1) & 1) return BZ_ERR_ARG;
+    const int u0 = p0 / 2, u1 = p1 / 2;
+    const int chunk = pl.chunk;
+    tm_begin(pl, st);
+    bz_status s = sym_input(pl, pl.src ? pl.src : (const void *)pl.fin, pl.src ? pl.src_dtype : BZ_C64, st);
+    if (s != BZ_OK) return s;
+    k_plane_inv<N, false><<<dim3(N / PPC, 1), Cfg<N>::THREADS, Cfg<N>::SMEM, st>>>(pl.fsym, pl.tw, pl.S, 0, 0);
+    k_pencil<N, 0><<<dim3((N * N + 127) / 128, 1), 128, 0, st>>>(pl.S, nullptr, pl.h);
+    BZ_CUDA_TRY(cudaMemsetAsync(pl.acc, 0, (size_t)n3 * sizeof(double2), st));
+    BZ_CUDA_TRY(cudaMemsetAsync(pl.acc_s, 0, (size_t)ns * sizeof(double2), st));
+    tm_end(pl, st, TK_OTHER);
+    int nl = 3;
+    for (int c0 = u0; c0 < u1; c0 += chunk) {
+        const int T = (u1 - c0) < chunk ? (u1 - c0) : chunk;
+        tm_begin(pl, st);
+        k_plane_inv<N, true><<<dim3(N / PPC, T), Cfg<N>::THREADS, Cfg<N>::SMEM, st>>>(pl.fsym, pl.tw, pl.S, c0, 1);
+        tm_end(pl, st, TK_PLANE_INV);
+        tm_begin(pl, st);
+        k_pencil<N, 2><<<dim3((N * N + 127) / 128, T), 128, 0, st>>>(pl.S, pl.h, nullptr);
+        tm_end(pl, st, TK_PENCIL);
+        tm_begin(pl, st);
+        k_plane_fwd<N, true><<<dim3(N / PPC, T), Cfg<N>::THREADS, Cfg<N>::SMEM, st>>>(pl.S, pl.apair, c0, pl.cpair,
+                                                                                   pl.S_s);
+        tm_end(pl, st, TK_PLANE_FWD);
+        tm_begin(pl, st);
+        k_reduce<<<(n3 + 255) / 256, 256, 0, st>>>(pl.S, T, n3, pl.acc);
+        k_reduce<<<(ns + 255) / 256, 256, 0, st>>>(pl.S_s, T, ns, pl.acc_s);
+        tm_end(pl, st, TK_REDUCE);
+        nl += 5;
+    }
+    tm_begin(pl, st);
+    s = sym_output(pl, st);
+    if (s != BZ_OK) return s;
+    tm_end(pl, st, TK_OTHER);
+    ++nl;
+    BZ_CUDA_TRY(cudaGetLastError());
+    if (launches) *launches += nl;
+    return BZ_OK;
+}
+
 template <int N>
 static bz_status run_chunks(Plan &pl, int p0, int p1, cudaStream_t st, int *launches) {
     constexpr int PPC = Cfg<N>::PPC;
     const int n3 = N * N * N;
     const dim3 plane_grid1(N / PPC, 1);
+    if (pl.real) return run_chunks_real<N>(pl, p0, p1, st, launches);
     // h = IFFT(fhat): planes without twiddles into S[0], then an inverse-only pencil pass
     tm_begin(pl, st);
-    k_plane_inv<N><<<plane_grid1, Cfg<N>::THREADS, Cfg<N>::SMEM, st>>>(pl.fin, pl.tw, pl.S, 0, 0);
+    k_plane_inv<N, false><<<plane_grid1, Cfg<N>::THREADS, Cfg<N>::SMEM, st>>>(pl.fin, pl.tw, pl.S, 0, 0);
     k_pencil<N, 0><<<dim3((N * N + 127) / 128, 1), 128, 0, st>>>(pl.S, nullptr, pl.h);
     BZ_CUDA_TRY(cudaMemsetAsync(pl.acc, 0, (size_t)n3 * sizeof(double2), st));
     tm_end(pl, st, TK_OTHER);
@@ -269,13 +352,13 @@ static bz_status run_chunks(Plan &pl, int p0, int p1, cudaStream_t st, int *laun
     for (int c0 = p0; c0 < p1; c0 += pl.chunk) {
         const int T = (p1 - c0) < pl.chunk ? (p1 - c0) : pl.chunk;
         tm_begin(pl, st);
-        k_plane_inv<N><<<dim3(N / PPC, T), Cfg<N>::THREADS, Cfg<N>::SMEM, st>>>(pl.fin, pl.tw, pl.S, c0, 1);
+        k_plane_inv<N, false><<<dim3(N / PPC, T), Cfg<N>::THREADS, Cfg<N>::SMEM, st>>>(pl.fin, pl.tw, pl.S, c0, 1);
         tm_end(pl, st, TK_PLANE_INV);
         tm_begin(pl, st);
         k_pencil<N, 1><<<dim3((N * N + 127) / 128, T), 128, 0, st>>>(pl.S, pl.h, nullptr);
         tm_end(pl, st, TK_PENCIL);
         tm_begin(pl, st);
-        k_plane_fwd<N><<<dim3(N / PPC, T), Cfg<N>::THREADS, Cfg<N>::SMEM, st>>>(pl.S, pl.alpha, c0);
+        k_plane_fwd<N, false><<<dim3(N / PPC, T), Cfg<N>::THREADS, Cfg<N>::SMEM, st>>>(pl.S, pl.alpha, c0);
         tm_end(pl, st, TK_PLANE_FWD);
         tm_begin(pl, st);
         k_reduce<<<(n3 + 255) / 256, 256, 0, st>>>(pl.S, T, n3, pl.acc);

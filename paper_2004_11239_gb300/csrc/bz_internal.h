@@ -78,6 +78,8 @@ struct Plan {
     float2 *cpair = nullptr;        // [P / 2][3][N][N] C = conj B(-k), B = (alpha_2q + i alpha_2q+1) / 2, on the
                                     // Nyquist planes (families k1 = -N/2, k2 = -N/2, k3 = -N/2), 0 elsewhere
     float2 *part_s = nullptr;       // [fused_G][3][N][N] per-item sums X on the Nyquist planes
+    float2 *S_s = nullptr;          // chunked pipeline: [chunk][3][N][N] the chunk's Nyquist sums
+    double2 *acc_s = nullptr;       // chunked pipeline: [3][N][N] FP64 sum of X
     float2 *fsym = nullptr;         // [N^3] Hermitian part of fhat, Nyquist planes zero (FP32)
     double2 *fsym64 = nullptr;      // [N^3] the same in FP64 (source of h)
     int *dev_err = nullptr;         // device flag: a bounded wait of the fused kernel gave up
@@ -151,6 +153,8 @@ bz_status build_pair_table(Plan &pl);
 bz_status sym_input(Plan &pl, const void *f, int dtype, cudaStream_t st);
 // pl.acc <- Q from the nblk item sums of pl.part (V) and pl.part_s (X): one kernel
 bz_status reduce_sym(Plan &pl, int nblk, cudaStream_t st);
+// chunked pipeline: pl.acc (V, FP64) <- Q in place, with pl.acc_s (X)
+bz_status sym_output(Plan &pl, cudaStream_t st);
 
 // bz_pair3.cu (BZ_DATA_REAL, N = 32, FP64 h): resident clusters and launch of k_pair3
 cudaError_t pair3_setup(int *G);

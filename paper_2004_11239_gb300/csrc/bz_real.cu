@@ -118,6 +118,32 @@ __global__ void __launch_bounds__(256) k_reduce_sym(const float2 *__restrict__ p
     }
 }
 
+// In place: acc(k) <- V(k) + conj V(-k) off S, V(k) + conj X(-k) on S (xs: the FP64 sums X in
+// the family layout).  Off S the thread of the smaller index of each pair {k, -k} writes both
+// entries; k = 0 is its own mirror.
+__global__ void k_sym_out(double2 *__restrict__ acc, const double2 *__restrict__ xs, int N) {
+    const int n3 = N * N * N;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n3) return;
+    const int i1 = k / (N * N), i2 = (k / N) % N, i3 = k % N;
+    const int m1 = (N - i1) % N, m2 = (N - i2) % N, m3 = (N - i3) % N;
+    const double2 a = acc[k];
+    if (nyquist(i1, i2, i3, N)) {
+        const double2 x = xs[family_index(m1, m2, m3, N)];
+        acc[k] = make_double2(a.x + x.x, a.y - x.y);
+        return;
+    }
+    const size_t m = ((size_t)m1 * N + m2) * N + m3;
+    if ((size_t)k > m) return;
+    if ((size_t)k == m) {
+        acc[k] = make_double2(2.0 * a.x, 0.0);
+        return;
+    }
+    const double2 b = acc[m];
+    acc[k] = make_double2(a.x + b.x, a.y - b.y);
+    acc[m] = make_double2(b.x + a.x, b.y - a.y);
+}
+
 // A_q(k) = (alpha_2q(k) - i alpha_2q+1(k)) / 2 for every k.
 __global__ void k_pair_table(const float2 *__restrict__ alpha, int N, int pairs, float2 *__restrict__ ap) {
     const size_t n3 = (size_t)N * N * N;
@@ -172,6 +198,17 @@ bz_status sym_input(Plan &pl, const void *f, int dtype, cudaStream_t st) {
 bz_status reduce_sym(Plan &pl, int nblk, cudaStream_t st) {
     const int n3 = (int)modes(pl);
     k_reduce_sym<<<(n3 + 31) / 32, 256, 0, st>>>(pl.part, pl.part_s, nblk, pl.N, pl.acc);
+    BZ_CUDA_TRY(cudaGetLastError());
+    return BZ_OK;
+}
+
+}  // namespace bz
+
+namespace bz {
+
+bz_status sym_output(Plan &pl, cudaStream_t st) {
+    const int n3 = (int)modes(pl);
+    k_sym_out<<<(n3 + 255) / 256, 256, 0, st>>>(pl.acc, pl.acc_s, pl.N);
     BZ_CUDA_TRY(cudaGetLastError());
     return BZ_OK;
 }

@@ -68,9 +68,9 @@ def test_precision_checks_without_gpu(libpath):
         d.data, d.ctas_per_sm, d.h_precision = data, ctas, hp
         assert bz.lib.bz_plan_create_ex(ctypes.byref(h), ctypes.byref(d)) == want
         assert h.value is None
-    # the real-data form: 3D FP32 circular fused (N <= 32), M even
+    # the real-data form: 3D FP32 circular, M even; the fused pipeline only where N divides 32
     for N, M, prec, pipe, data, want in [(32, 12, 0, 0, 2, 1), (32, 12, bz.BZ_PREC_BF16X3, 0, 1, 7), (32, 9, 0, 0, 1, 7),
-                                         (48, 12, 0, 0, 1, 7), (16, 12, 0, bz.BZ_PIPE_CHUNKED, 1, 7)]:
+                                         (48, 12, 0, bz.BZ_PIPE_FUSED, 1, 7), (24, 12, 0, bz.BZ_PIPE_FUSED, 1, 7)]:
         d = bz.bz_plan_desc()
         d.N, d.L, d.R, d.gamma, d.s, d.N_rho, d.M = N, 10.0, 9.0, 0.0, 0.5, 2, M
         d.precision, d.pipeline, d.data = prec, pipe, data

@@ -105,14 +105,13 @@ def test_real_term_ranges_fp32_input_and_refusals(bz):
         with pytest.raises(bz.BzError):
             call()
     plan.close()
-    for kw in (dict(precision=bz.BZ_PREC_BF16X3), dict(pipeline=bz.BZ_PIPE_CHUNKED), dict(conv=bz.BZ_CONV_PADDED)):
+    for kw in (dict(precision=bz.BZ_PREC_BF16X3), dict(conv=bz.BZ_CONV_PADDED)):
         with pytest.raises(bz.BzError):
             _real_plan(bz, 32 if "precision" in kw else N, L, R, 0.0, 0.5, 2, 12, **kw)
     with pytest.raises(bz.BzError):                              # M odd: pairs would straddle radial nodes
         _real_plan(bz, N, L, R, 0.0, 0.5, 2, 9)
-    for n in (24, 48):                                           # N must divide a warp's 32 lanes
-        with pytest.raises(bz.BzError):
-            _real_plan(bz, n, L, R, 0.0, 0.5, 1, 12)
+    with pytest.raises(bz.BzError):                              # the fused pair kernel needs N | 32
+        _real_plan(bz, 24, L, R, 0.0, 0.5, 1, 12, pipeline=bz.BZ_PIPE_FUSED)
 
 
 def test_real_rk4_matches_oracle(bz):
@@ -218,4 +217,49 @@ def test_real_batch_matches_oracle_and_is_batch_invariant(bz, N, ctas):
         assert err <= TOL
     assert np.array_equal(got[1], f[1]) and np.array_equal(got[3], f[3])   # inactive slots untouched
     batch.close()
+    plan.close()
+
+
+@pytest.mark.parametrize("N,pipe", [(24, 0), (32, 2), (48, 0)])
+def test_real_chunked_matches_oracle(bz, N, pipe):
+    """The chunked pipeline's pair form (N = 24, 48, or on request): whole collides of a few
+    terms against the oracle's real-data reading, an RK4 change, and term ranges."""
+    L = 10.0
+    R = bi.R_from_L(L)
+    fhat = bi.random_mixture(N, L, seed=N + 7)
+    plan = _real_plan(bz, N, L, R, -1.0, 0.5, 2, 12, pipeline=pipe)
+    assert bz.bz_plan_pipeline(plan)["kernel"] == "chunked"
+    op = spectral.OraclePlan(N, L, R, -1.0, kernels.Kernel("family", 0.5), 2, 12)
+    got = _collide(bz, plan, fhat)
+    err = _rel(got, spectral.collide_real(op, fhat))
+    print(f"real chunked N={N} P=24: rel_Linf={err:.2e}")
+    assert err <= TOL
+    parts = _collide(bz, plan, fhat, 0, 10) + _collide(bz, plan, fhat, 10, 24)
+    assert _rel(parts, got) <= 2 * TOL
+    if N <= 32:
+        f = torch.from_numpy(fhat.copy()).cuda()
+        bz.bz_step_rk(plan, f, 0.0, 0.05, 1)
+        torch.cuda.synchronize()
+        ref = spectral.rk4_real(op, fhat, 0.05, 1)
+        e = _rel(f.cpu().numpy() - fhat, ref - fhat)
+        print(f"real chunked N={N} RK4: rel_Linf of the change = {e:.2e}")
+        assert e <= TOL
+    plan.close()
+
+
+def test_real_chunked_n64_sampled_terms(bz):
+    """N = 64, N_rho = M = 64 (the single-collide workload) on the chunked pair form: sampled
+    term ranges against the oracle's real-data reading, relative to their summands."""
+    N, L = 64, 10.0
+    R = bi.R_from_L(L)
+    fhat = bi.bigaussian_noise_c3(N, L)
+    plan = _real_plan(bz, N, L, R, -1.0, 0.5, 64, 64)
+    for p0, p1 in [(0, 2), (2046, 2050), (4094, 4096)]:
+        got = _collide(bz, plan, fhat, p0, p1)
+        op = spectral.OraclePlan(N, L, R, -1.0, kernels.Kernel("family", 0.5), 64, 64, terms=np.arange(p0, p1))
+        ref = spectral.collide_real(op, fhat, p0, p1)
+        scale = _summand_scale(op, fhat, p0, p1)
+        err = float(np.max(np.abs(got - ref))) / scale
+        print(f"real chunked N=64 terms [{p0},{p1}): err/summand scale={err:.2e}, rel_Linf={_rel(got, ref):.2e}")
+        assert err <= TOL
     plan.close()
