@@ -117,8 +117,9 @@ enum { BZ_H_AUTO = 0, BZ_H_FP64 = 1, BZ_H_FP32 = 2 };
  *                    per collide.  On the Nyquist planes, where alpha_p(-k) != conj alpha_p(k), a
  *                    second sum with a 3 N^2 table per pair completes every mode, so for a real f
  *                    without Nyquist content the result is eq. realQ itself.  Half the transforms,
- *                    exchanges and (nearly) table bytes per term.  3D, FP32, circular, fused
- *                    pipeline, N = 8, 16 or 32, M even; bz_collide_terms takes even term bounds;
+ *                    exchanges and (nearly) table bytes per term.  3D, FP32, circular, M even;
+ *                    the fused pipeline for N = 8, 16, 32, the chunked one for N = 24, 48, 64
+ *                    (BZ_PIPE_FUSED with those: BZ_ERR_UNSUPPORTED); bz_collide_terms takes even term bounds;
  *                    batches need h in FP64 (the default); bz_collide_noalloc returns
  *                    BZ_ERR_UNSUPPORTED. */
 enum { BZ_DATA_COMPLEX = 0, BZ_DATA_REAL = 1 };
