@@ -263,3 +263,19 @@ def test_real_chunked_n64_sampled_terms(bz):
         print(f"real chunked N=64 terms [{p0},{p1}): err/summand scale={err:.2e}, rel_Linf={_rel(got, ref):.2e}")
         assert err <= TOL
     plan.close()
+
+
+@pytest.mark.parametrize("N,cluster", [(16, 1), (16, 2), (32, 4), (32, 8)])
+def test_real_fused_every_cluster_size(bz, N, cluster):
+    """k_fused's pair form at each compiled cluster size (plan creation times them all)."""
+    L = 10.0
+    R = bi.R_from_L(L)
+    fhat = bi.random_mixture(N, L, seed=N + cluster)
+    plan = _real_plan(bz, N, L, R, 0.0, 0.5, 2, 12, cluster=cluster, ctas_per_sm=2 if N == 32 else 0)
+    info = bz.bz_plan_pipeline(plan)
+    assert info["kernel"] == "k_fused" and info["cluster"] == cluster
+    got = _collide(bz, plan, fhat)
+    err = _rel(got, spectral.collide_real(spectral.OraclePlan(N, L, R, 0.0, kernels.Kernel("family", 0.5), 2, 12), fhat))
+    print(f"real k_fused N={N} C={cluster}: rel_Linf={err:.2e}")
+    assert err <= TOL
+    plan.close()
