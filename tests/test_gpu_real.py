@@ -279,3 +279,18 @@ def test_real_fused_every_cluster_size(bz, N, cluster):
     print(f"real k_fused N={N} C={cluster}: rel_Linf={err:.2e}")
     assert err <= TOL
     plan.close()
+
+
+def test_real_fused_with_fp32_h(bz):
+    """h formed in FP32 inside k_fused's item prologue from the symmetrised input (BZ_H_FP32)."""
+    N, L = 16, 10.0
+    R = bi.R_from_L(L)
+    fhat = bi.random_mixture(N, L, seed=61)
+    plan = _real_plan(bz, N, L, R, 0.0, 0.5, 2, 12, h_precision=bz.BZ_H_FP32)
+    got = _collide(bz, plan, fhat)
+    err = _rel(got, spectral.collide_real(spectral.OraclePlan(N, L, R, 0.0, kernels.Kernel("family", 0.5), 2, 12), fhat))
+    print(f"real N={N} FP32 h: rel_Linf={err:.2e}")
+    assert err <= TOL
+    with pytest.raises(bz.BzError):                              # batches need h in FP64
+        bz.bz_batch_create(plan, 2, 0)
+    plan.close()
