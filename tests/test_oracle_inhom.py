@@ -45,3 +45,16 @@ def test_strang_on_uniform_f_is_rk4_per_cell():
     got = inhom.strang(plan, f0, Lx, 0.1, 2)
     ref = spectral.rk4(plan, g, 0.1, 2)
     assert np.max(np.abs(got - ref[None])) < 1e-13 * np.max(np.abs(ref))
+
+
+def test_strang_is_second_order():
+    """Halving dt divides the splitting error by about four (Strang: streaming dt/2, collision
+    dt, streaming dt/2), measured against a run with dt/8."""
+    N, L, nx, Lx, T = 8, 6.0, 4, 3.0, 0.4
+    R = bi.R_from_L(L)
+    plan = spectral.OraclePlan(N, L, R, 0.0, kernels.Kernel("family", 0.5), 2, 12)
+    f0 = bi.inhom_cells(N, L, nx, Lx, eps=0.3)
+    ref = inhom.strang(plan, f0, Lx, T / 16, 16)
+    e = [np.max(np.abs(inhom.strang(plan, f0, Lx, T / n, n) - ref)) for n in (2, 4)]
+    print(f"Strang errors at dt = {T / 2}, {T / 4}: {e[0]:.2e}, {e[1]:.2e} (ratio {e[0] / e[1]:.2f})")
+    assert 3.0 < e[0] / e[1] < 5.5
