@@ -126,15 +126,8 @@ def collide_real(plan: OraclePlan, fhat: np.ndarray, p0: int = 0, p1: int | None
 
 
 def rk4_real(plan: OraclePlan, fhat: np.ndarray, dt: float, nsteps: int) -> np.ndarray:
-    """Classical RK4 (Sec. 5.2) on d fhat/dt = collide_real(fhat)."""
-    f = np.asarray(fhat, dtype=np.complex128).copy()
-    for _ in range(nsteps):
-        k1 = collide_real(plan, f)
-        k2 = collide_real(plan, f + 0.5 * dt * k1)
-        k3 = collide_real(plan, f + 0.5 * dt * k2)
-        k4 = collide_real(plan, f + dt * k3)
-        f = f + dt / 6.0 * (k1 + 2 * k2 + 2 * k3 + k4)
-    return f
+    """Classical RK4 (Sec. 5.2) on d fhat/dt = collide_real(fhat) (`rk4_steps`)."""
+    return rk4_steps(lambda f: collide_real(plan, f), fhat, dt, nsteps)
 
 
 def _embed(x: np.ndarray, N2: int) -> np.ndarray:
@@ -251,13 +244,20 @@ def grid_v2(N: int, L: float) -> np.ndarray:
     return V1 ** 2 + V2 ** 2 + V3 ** 2
 
 
-def rk4(plan: OraclePlan, fhat: np.ndarray, dt: float, nsteps: int) -> np.ndarray:
-    """Classical fourth-order Runge-Kutta on d fhat/dt = Qhat(fhat) (Sec. 5.2)."""
+def rk4_steps(rhs, fhat: np.ndarray, dt: float, nsteps: int) -> np.ndarray:
+    """Classical fourth-order Runge-Kutta (Sec. 5.2) on d fhat/dt = rhs(fhat): per step the four
+    stage slopes k1 = rhs(f), k2 = rhs(f + dt k1 / 2), k3 = rhs(f + dt k2 / 2), k4 = rhs(f + dt k3),
+    then f + dt (k1 + 2 k2 + 2 k3 + k4) / 6.  The one stage formula every oracle RK4 uses."""
     f = np.asarray(fhat, dtype=np.complex128).copy()
     for _ in range(nsteps):
-        k1 = collide(plan, f)
-        k2 = collide(plan, f + 0.5 * dt * k1)
-        k3 = collide(plan, f + 0.5 * dt * k2)
-        k4 = collide(plan, f + dt * k3)
+        k1 = rhs(f)
+        k2 = rhs(f + 0.5 * dt * k1)
+        k3 = rhs(f + 0.5 * dt * k2)
+        k4 = rhs(f + dt * k3)
         f = f + dt / 6.0 * (k1 + 2 * k2 + 2 * k3 + k4)
     return f
+
+
+def rk4(plan: OraclePlan, fhat: np.ndarray, dt: float, nsteps: int) -> np.ndarray:
+    """Classical RK4 (Sec. 5.2) on d fhat/dt = Qhat(fhat) (`rk4_steps`)."""
+    return rk4_steps(lambda f: collide(plan, f), fhat, dt, nsteps)

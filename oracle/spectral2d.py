@@ -24,7 +24,7 @@ import numpy as np
 from . import quadrature
 from .ftable import EPS_DEFAULT, ftable2d
 from .kernels import Kernel2D
-from .spectral import dft_matrix, signed
+from .spectral import dft_matrix, rk4_steps, signed
 
 
 def dft2(x: np.ndarray, sign: int) -> np.ndarray:
@@ -112,12 +112,5 @@ def bkw2d_Q(v2: np.ndarray, K: float, lam: float = 0.125) -> np.ndarray:
 
 
 def rk4_2d(plan: OraclePlan2D, fhat: np.ndarray, dt: float, nsteps: int) -> np.ndarray:
-    """Classical fourth-order Runge-Kutta on d fhat/dt = Qhat(fhat)."""
-    f = np.asarray(fhat, dtype=np.complex128).copy()
-    for _ in range(nsteps):
-        k1 = collide2d(plan, f)
-        k2 = collide2d(plan, f + 0.5 * dt * k1)
-        k3 = collide2d(plan, f + 0.5 * dt * k2)
-        k4 = collide2d(plan, f + dt * k3)
-        f = f + dt / 6.0 * (k1 + 2 * k2 + 2 * k3 + k4)
-    return f
+    """Classical RK4 (Sec. 5.2) on d fhat/dt = collide2d(fhat) (`spectral.rk4_steps`)."""
+    return rk4_steps(lambda f: collide2d(plan, f), fhat, dt, nsteps)

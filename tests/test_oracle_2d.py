@@ -119,3 +119,16 @@ def test_bkw2d_closed_forms_are_consistent():
         h = 1e-5
         fd = (s2.bkw2d_f(v2, bi.bkw2d_K(t + h)) - s2.bkw2d_f(v2, bi.bkw2d_K(t - h))) / (2 * h)
         assert np.allclose(fd, s2.bkw2d_Q(v2, bi.bkw2d_K(t)), rtol=1e-6, atol=1e-10)
+
+
+def test_rk4_2d_is_fourth_order():
+    """The 2D RK4 (Sec. 5.2): halving dt divides the error by about 16 (N = 8, b2)."""
+    R = 6.0
+    L = bi.L_from_R(R)
+    plan = s2.OraclePlan2D(8, L, R, 0.0, kernels.Kernel2D("b2"), 4, 8)
+    K = bi.bkw2d_K(0.0)
+    f0 = bi.bkw2d_fhat_samples(8, L, K)
+    Tend = 2.0
+    ref = s2.rk4_2d(plan, f0, Tend / 256, 256)
+    e = [np.max(np.abs(s2.rk4_2d(plan, f0, Tend / n, n) - ref)) for n in (8, 16, 32)]
+    assert 14 < e[0] / e[1] < 20 and 14 < e[1] / e[2] < 20, e

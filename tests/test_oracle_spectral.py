@@ -144,3 +144,33 @@ def test_rk4_is_fourth_order():
     ref = spectral.rk4(plan, f0, Tend / 256, 256)
     e = [np.max(np.abs(spectral.rk4(plan, f0, Tend / n, n) - ref)) for n in (8, 16, 32)]
     assert 14 < e[0] / e[1] < 20 and 14 < e[1] / e[2] < 20
+
+
+def test_rk4_steps_one_step_is_the_fourth_order_taylor_polynomial():
+    """One classical RK4 step (Sec. 5.2) on the linear system y' = A y multiplies y by
+    1 + Z + Z^2/2 + Z^3/6 + Z^4/24 exactly (Z = dt A): a wrong stage weight or a stage taken at
+    the wrong point changes a coefficient of this polynomial."""
+    rng = np.random.default_rng(5)
+    A = rng.standard_normal((4, 4)) + 1j * rng.standard_normal((4, 4))
+    y0 = rng.standard_normal(4) + 1j * rng.standard_normal(4)
+    dt = 0.3
+    Z = dt * A
+    I = np.eye(4)
+    poly = I + Z + Z @ Z / 2 + Z @ Z @ Z / 6 + Z @ Z @ Z @ Z / 24
+    got = spectral.rk4_steps(lambda y: A @ y, y0, dt, 1)
+    assert np.allclose(got, poly @ y0, rtol=0, atol=1e-13 * np.abs(poly @ y0).max())
+    # nsteps steps apply the polynomial nsteps times
+    got3 = spectral.rk4_steps(lambda y: A @ y, y0, dt, 3)
+    assert np.allclose(got3, poly @ poly @ poly @ y0, rtol=0, atol=1e-12 * np.abs(got3).max())
+
+
+def test_rk4_real_is_fourth_order():
+    """The real-data RK4 (Sec. 5.2 on the real-data reading, `rk4_real`): halving dt divides
+    the error by about 16."""
+    L = 6.0
+    plan = spectral.OraclePlan(8, L, bi.R_from_L(L), 0.0, kernels.Kernel("family", 0.5), 3, 12)
+    f0 = bi.random_mixture(8, L, seed=1, box=1.0)
+    Tend = 1.0
+    ref = spectral.rk4_real(plan, f0, Tend / 256, 256)
+    e = [np.max(np.abs(spectral.rk4_real(plan, f0, Tend / n, n) - ref)) for n in (8, 16, 32)]
+    assert 14 < e[0] / e[1] < 20 and 14 < e[1] / e[2] < 20, e
