@@ -241,21 +241,28 @@ const char *bz_status_str(bz_status s);
  * whose device memory is reserved up front by its own pool allocator, a latency-critical
  * time loop that cannot pay the device synchronisation of cudaMalloc/cudaFree, a host
  * that forbids a library to grow its footprint after start-up).
- * Same result as bz_collide (within the FP32 pipeline's rounding; the term chunking
- * differs), but every scratch buffer lives in one file-scope device array of
+ * It computes the operator bz_collide computes on the same plan: h = IFFT(fhat) is formed
+ * the same way (in FP64 on the fused pipeline unless the plan asks for BZ_H_FP32, in FP32 on
+ * the chunked one), the terms run through the chunked FP32 kernels and are summed in FP64;
+ * results agree within the FP32 pipeline's rounding (the term chunking and summation order
+ * differ).  Every scratch buffer lives in one file-scope device array of
  * BZ_NOALLOC_SCRATCH_BYTES that each GPU loading libbz holds until the process exits;
  * nothing is allocated or freed.  The plan must have been created beforehand on the
  * current device.
- *   - Size limit: the array holds the FP32 input copy, h, the FP64 accumulator and at least
- *     one term of scratch, i.e. 40 N^3 bytes (rounded up to 256-byte blocks); N = 64 does not
- *     fit and returns BZ_ERR_ARG without touching Qhat.  N <= 48 fits.
- *   - The first call on each device looks up the array's device address (cudaGetSymbolAddress)
- *     with that device current; make that first call before any stream capture begins.
+ *   - Size limit: the array holds the FP32 input copy and h (8 N^3 bytes each), the FP64
+ *     accumulator (16 N^3), the FP64 h pass's scratch where h is formed in FP64 (16 N^3) and at
+ *     least one term of 8 N^3 (each rounded up to 256-byte blocks).  N <= 48 fits (N = 48: five
+ *     terms per chunk); N = 64 does not and returns BZ_ERR_ARG without touching Qhat.
+ *   - Each call looks up the array's device address (cudaGetSymbolAddress) with the current
+ *     device; the first lookup on a device may load the module there, so make the first
+ *     call on each device before any stream capture begins.
  *   - All calls share the one array and it keeps the previous call's contents (the
  *     accumulator is cleared on the stream at the start of every call).  Calls whose work
  *     overlaps on the GPU (other streams, other host threads) race on the array: serialise them.
  * Errors: BZ_ERR_ARG for NULL or aliased arrays, a bad dtype, a plan of another device or a
- * plan too large for the array; BZ_ERR_CUDA if the address lookup or a launch fails. */
+ * plan too large for the array; BZ_ERR_UNSUPPORTED for padded, 2D, real-data (BZ_DATA_REAL)
+ * and split-BF16 (BZ_PREC_BF16X3) plans, which bz_collide serves; BZ_ERR_CUDA if the address
+ * lookup or a launch fails. */
 #define BZ_NOALLOC_SCRATCH_BYTES (8u << 20)
 bz_status bz_collide_noalloc(const bz_plan *plan, const void *fhat, void *Qhat, int dtype,
                              void *stream);

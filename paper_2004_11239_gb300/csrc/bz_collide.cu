@@ -10,7 +10,6 @@
 // inverse-only pencil pass.  Inverse transforms are unnormalised; alpha carries N^-3.
 #include <algorithm>
 #include <cstdio>
-#include <mutex>
 
 #include "bz_fft.cuh"
 #include "bz_internal.h"
@@ -453,7 +452,9 @@ bz_status write_output(Plan &pl, void *Qhat, int dtype, cudaStream_t st, int *la
 // scratch (FP32 input copy, h, the FP64 accumulator and the term chunk) lives in one
 // file-scope device array of kNoallocBytes, which every GPU that loads libbz holds
 // until the process exits.  The caller passes the plan (built beforehand) and the
-// input and output arrays; nothing is allocated or freed during the call.
+// input and output arrays; nothing is allocated or freed during the call.  h is formed as
+// bz_collide forms it on the same plan (FP64 on the fused pipeline unless the plan asks for
+// FP32 h, FP32 on the chunked one), so both compute the same operator.
 // =======================================================================================
 namespace bz {
 namespace {
@@ -461,44 +462,45 @@ namespace {
 constexpr size_t kNoallocBytes = (size_t)8 << 20;   // 8 MiB per device
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_noalloc_mu;
-unsigned char *g_noalloc_ptr[kMaxDevices] = {nullptr};
-
-// Device address of the scratch array on the current device.  The host-side symbol is
-// only a stand-in, so the address is looked up once per device (with that device
-// current) and cached.
-bz_status noalloc_scratch(int dev, unsigned char **out) {
-    if (dev < 0 || dev >= kMaxDevices) return BZ_ERR_UNSUPPORTED;
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return BZ_ERR_CUDA;
-        g_noalloc_ptr[dev] = (unsigned char *)p;
-    }
-    *out = g_noalloc_ptr[dev];
+// Device address of the scratch array on the current device.  In host code the symbol is
+// only a stand-in, so the address is looked up with the device current, on every call: the
+// lookup allocates nothing, and a fresh address after cudaDeviceReset is picked up.  The first
+// lookup on a device may load the module there.
+bz_status noalloc_scratch(unsigned char **out) {
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return BZ_ERR_CUDA;
+    *out = (unsigned char *)p;
     return BZ_OK;
 }
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
+// Scratch layout (256-byte blocks): fin (8 N^3 bytes), h (8 N^3), acc (16 N^3), the FP64 h
+// pass's scratch where the plan forms h in FP64 (16 N^3), then T terms of 8 N^3.
 template <int N>
 bz_status run_noalloc(const Plan &pl, const void *fhat, void *Qhat, int dtype, unsigned char *base,
-                      int T, cudaStream_t st) {
+                      bool h64, int T, cudaStream_t st) {
     constexpr int PPC = Cfg<N>::PPC;
     const int n3 = N * N * N;
     const size_t field = (size_t)n3 * sizeof(float2);
     float2 *fin = (float2 *)base;
     float2 *h = (float2 *)(base + align256(field));
     double2 *acc = (double2 *)(base + 2 * align256(field));
-    float2 *S = (float2 *)(base + 2 * align256(field) + align256(2 * field));
+    double2 *scr64 = (double2 *)(base + 2 * align256(field) + align256(2 * field));
+    float2 *S = (float2 *)(base + 2 * align256(field) + (h64 ? 2 : 1) * align256(2 * field));
     if (dtype == BZ_C64) {
         BZ_CUDA_TRY(cudaMemcpyAsync(fin, fhat, field, cudaMemcpyDeviceToDevice, st));
     } else {
         k_c128_to_c64<<<(n3 + 255) / 256, 256, 0, st>>>((const double2 *)fhat, fin, n3);
     }
-    k_plane_inv<N><<<dim3(N / PPC, 1), Cfg<N>::THREADS, Cfg<N>::SMEM, st>>>(fin, pl.tw, S, 0, 0);
-    k_pencil<N, 0><<<dim3((N * N + 127) / 128, 1), 128, 0, st>>>(S, nullptr, h);
+    if (h64) {
+        // as bz_collide on this plan: h from the caller's coefficients in FP64, stored FP32
+        const bz_status s = h64_launch(N, fhat, dtype, nullptr, nullptr, 1, scr64, h, st);
+        if (s != BZ_OK) return s;
+    } else {
+        k_plane_inv<N><<<dim3(N / PPC, 1), Cfg<N>::THREADS, Cfg<N>::SMEM, st>>>(fin, pl.tw, S, 0, 0);
+        k_pencil<N, 0><<<dim3((N * N + 127) / 128, 1), 128, 0, st>>>(S, nullptr, h);
+    }
     BZ_CUDA_TRY(cudaMemsetAsync(acc, 0, (size_t)n3 * sizeof(double2), st));   // left over from the last call
     for (int c0 = 0; c0 < pl.P; c0 += T) {
         const int Tc = (pl.P - c0) < T ? (pl.P - c0) : T;
@@ -529,25 +531,28 @@ extern "C" bz_status bz_collide_noalloc(const bz_plan *plan, const void *fhat, v
     if (dtype != BZ_C64 && dtype != BZ_C128) return BZ_ERR_ARG;
     const Plan &pl = *plan_internal(plan);
     if (pl.Nin || pl.dim == 2 || pl.real) return BZ_ERR_UNSUPPORTED;   // padded, 2D and real-data plans: bz_collide
+    if (pl.precision != BZ_PREC_FP32) return BZ_ERR_UNSUPPORTED;        // split-BF16 plans: bz_collide
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return BZ_ERR_CUDA;
     if (dev != pl.device) return BZ_ERR_ARG;
+    // h as bz_collide forms it on this plan: FP64 on the fused pipeline with FP64 h, else FP32
+    const bool h64 = pl.use_fused && pl.h_fp64;
     const size_t n3 = (size_t)pl.N * pl.N * pl.N;
     const size_t field = n3 * sizeof(float2);
-    const size_t fixed = 2 * align256(field) + align256(2 * field);   // fin, h, acc
+    const size_t fixed = 2 * align256(field) + (h64 ? 2 : 1) * align256(2 * field);   // fin, h, acc (, scr64)
     if (fixed + field > kNoallocBytes) return BZ_ERR_ARG;               // not even one term fits
     const int T = (int)std::min<size_t>((kNoallocBytes - fixed) / field, (size_t)pl.P);
     unsigned char *base = nullptr;
-    bz_status s = noalloc_scratch(dev, &base);
+    bz_status s = noalloc_scratch(&base);
     if (s != BZ_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
     switch (pl.N) {
-        case 8: return run_noalloc<8>(pl, fhat, Qhat, dtype, base, T, st);
-        case 16: return run_noalloc<16>(pl, fhat, Qhat, dtype, base, T, st);
-        case 24: return run_noalloc<24>(pl, fhat, Qhat, dtype, base, T, st);
-        case 32: return run_noalloc<32>(pl, fhat, Qhat, dtype, base, T, st);
-        case 48: return run_noalloc<48>(pl, fhat, Qhat, dtype, base, T, st);
-        case 64: return run_noalloc<64>(pl, fhat, Qhat, dtype, base, T, st);
+        case 8: return run_noalloc<8>(pl, fhat, Qhat, dtype, base, h64, T, st);
+        case 16: return run_noalloc<16>(pl, fhat, Qhat, dtype, base, h64, T, st);
+        case 24: return run_noalloc<24>(pl, fhat, Qhat, dtype, base, h64, T, st);
+        case 32: return run_noalloc<32>(pl, fhat, Qhat, dtype, base, h64, T, st);
+        case 48: return run_noalloc<48>(pl, fhat, Qhat, dtype, base, h64, T, st);
+        case 64: return run_noalloc<64>(pl, fhat, Qhat, dtype, base, h64, T, st);
     }
     return BZ_ERR_ARG;
 }
