@@ -40,12 +40,13 @@ def dft_matrix(N: int, sign: int) -> np.ndarray:
 
 
 def dft3(x: np.ndarray, sign: int) -> np.ndarray:
-    """Unnormalised 3D DFT y[j] = sum_k x[k] exp(sign 2 pi i k.j / N), axis by axis."""
+    """Unnormalised 3D DFT y[j] = sum_k x[k] exp(sign 2 pi i k.j / N), axis by axis: the DFT
+    matrix W applied along axis 1, then axis 2, then axis 3 (each a matrix product)."""
     N = x.shape[0]
     W = dft_matrix(N, sign)
-    y = np.einsum("ab,bcd->acd", W, x)
-    y = np.einsum("cb,abd->acd", W, y)
-    y = np.einsum("db,acb->acd", W, y)
+    y = (W @ x.reshape(N, N * N)).reshape(N, N, N)           # axis 1: y[a,c,d] = sum_b W[a,b] x[b,c,d]
+    y = np.matmul(W[None], y)                                 # axis 2: y[a,c,d] = sum_b W[c,b] y[a,b,d]
+    y = (y.reshape(N * N, N) @ W.T).reshape(N, N, N)          # axis 3: y[a,c,d] = sum_b y[a,c,b] W[d,b]
     return y
 
 
@@ -94,6 +95,31 @@ def collide(plan: OraclePlan, fhat: np.ndarray, p0: int = 0, p1: int | None = No
         g = dft3(fhat * plan.beta(p), +1)
         U = dft3(h * g, -1) / N ** 3
         Q += plan.alpha(p) * U
+    return Q
+
+
+def collide_at(plan: OraclePlan, fhat: np.ndarray, kidx, F_at: np.ndarray, p0: int = 0,
+               p1: int | None = None) -> np.ndarray:
+    """Qhat of eq. realQ over the terms p0 <= p < p1 of `plan` (all by default), at the modes
+    kidx[S, 3] (array indices, FFT-natural order) only, with F_at[S, p1 - p0] =
+    F(k_s, r_p, qhat_p) supplied by the caller (for example `ftable.fentries`), so a full-size
+    operator can be checked at a few modes without the whole F table.  Per term the same steps
+    as `collide`: g_p = IDFT(beta_p f) on the whole grid, then the forward DFT of h g_p / N^3
+    evaluated at the requested modes only."""
+    N = plan.N
+    p1 = plan.P if p1 is None else p1
+    fhat = np.asarray(fhat, dtype=np.complex128)
+    kidx = np.asarray(kidx).reshape(-1, 3)
+    v = np.arange(N)
+    E = [np.exp(-2j * math.pi * np.outer(kidx[:, d], v) / N) for d in range(3)]     # [S, N] per axis
+    h = dft3(fhat, +1)
+    Q = np.zeros(len(kidx), dtype=np.complex128)
+    for p in range(p0, p1):
+        u = h * dft3(fhat * plan.beta(p), +1)
+        t = (E[0] @ u.reshape(N, N * N)).reshape(-1, N, N)         # sum over v1
+        t = np.einsum("sb,sbc->sc", E[1], t)                        # sum over v2
+        U = np.einsum("sc,sc->s", E[2], t) / N ** 3                 # sum over v3
+        Q += plan.c[p] * F_at[:, p - p0] * U
     return Q
 
 

@@ -174,3 +174,30 @@ def test_rk4_real_is_fourth_order():
     ref = spectral.rk4_real(plan, f0, Tend / 256, 256)
     e = [np.max(np.abs(spectral.rk4_real(plan, f0, Tend / n, n) - ref)) for n in (8, 16, 32)]
     assert 14 < e[0] / e[1] < 20 and 14 < e[1] / e[2] < 20, e
+
+
+def test_collide_at_equals_collide_at_those_modes():
+    """`collide_at` (all terms, a few output modes, F supplied per mode) equals `collide` at the
+    same modes, for the complex operator and the real-data band; the modes include both ends of
+    every axis."""
+    from oracle import ftable
+    L = 6.0
+    N = 8
+    plan = spectral.OraclePlan(N, L, bi.R_from_L(L), -1.0, kernels.Kernel("family", 0.5), 3, 12)
+    f = bi.random_mixture(N, L, seed=9, box=1.5)
+    u = bi.SplitMix64(4).uniform(3 * 20)
+    kidx = np.concatenate([np.array([[0, 0, 0], [N - 1, N // 2, 1], [N // 2, N - 1, N // 2]]),
+                           (u.reshape(20, 3) * N).astype(int)])
+    ks = spectral.signed(N)[kidx]
+    P = plan.P
+    F_at = ftable.fentries(N, L, np.repeat(ks, P, axis=0), np.tile(plan.r, len(ks)),
+                           np.tile(plan.q, (len(ks), 1)), plan.kernel).reshape(len(ks), P)
+    for g in (f, spectral.real_band(f)):
+        full = spectral.collide(plan, g)
+        got = spectral.collide_at(plan, g, kidx, F_at)
+        want = full[kidx[:, 0], kidx[:, 1], kidx[:, 2]]
+        assert np.max(np.abs(got - want)) < 1e-12 * np.max(np.abs(full))
+    # a term range with the matching columns of F
+    part = spectral.collide(plan, f, 5, 17)
+    got = spectral.collide_at(plan, f, kidx, F_at[:, 5:17], 5, 17)
+    assert np.max(np.abs(got - part[kidx[:, 0], kidx[:, 1], kidx[:, 2]])) < 1e-12 * np.max(np.abs(part))
