@@ -80,16 +80,18 @@ def _fhat(w, L):
 
 
 def _flops_per_term(N, dim=3):
-    """Algorithmic FP32 flops of one term: 2 d-dimensional FFTs (5 n log2 n, n = N^d), the
-    twiddle, product and weight multiplies (6 flops each per mode) and the accumulation (2)."""
+    """Algorithmic FP32 flops of one term (the per-unit count of the method's cost): two
+    d-dimensional FFTs of n = N^d points at 5 n log2 n each, and 26 pointwise flops per mode
+    (forming and applying the separable twiddle, 12; the product with h, 6; the alpha weight, 6;
+    the accumulation, 2).  Split per chunked kernel as each one executes them."""
     n = N ** dim
     if dim == 2:
-        return {"fused": 20 * n * math.log2(N) + 20 * n, "reduce": 2 * n}
-    return {"plane_inv": 10 * n * math.log2(N) + 6 * n,
+        return {"fused": 20 * n * math.log2(N) + 26 * n, "reduce": 2 * n}
+    return {"plane_inv": 10 * n * math.log2(N) + 12 * n,
             "pencil": 10 * n * math.log2(N) + 6 * n,
             "plane_fwd": 10 * n * math.log2(N) + 6 * n,
             "reduce": 2 * n,
-            "fused": 30 * n * math.log2(N) + 20 * n}
+            "fused": 30 * n * math.log2(N) + 26 * n}
 
 
 def _bytes_per_term(N, dim=3):
@@ -120,11 +122,12 @@ def _sources_hash(files):
     return h.hexdigest()[:16]
 
 
-def _profiled_traffic(kernel, workload):
-    """DRAM bytes per launch from the committed ncu summary, if the kernel sources still match."""
-    if kernel not in _PROFILES or workload != "rk4_n32":
+def _profiled_traffic(key):
+    """DRAM bytes per launch from the committed ncu summary of `key` (the kernel on its
+    workload), if the kernel sources still match the fingerprint recorded with it."""
+    if key not in _PROFILES:
         return None
-    name, files = _PROFILES[kernel]
+    name, files = _PROFILES[key]
     prof = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(prof):
         return None
@@ -138,12 +141,14 @@ def _profiled_traffic(kernel, workload):
     return float(vals["traffic_bytes_per_launch"])
 
 
-def _peaks():
-    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(p):
-        d = json.load(open(p))
-        return d, "measured"
-    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+def _alu_peak(peaks):
+    """FP32 FMA peak of the current device: SMs (queried) x 128 FP32 lanes x 2 flops x the
+    measured maximum SM clock; returns (TFLOP/s, SM count, how it was derived)."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = peaks.get("sm_max_mhz", 2070.0)
+    return (sms * 128 * 2 * mhz * 1e6 / 1e12, sms,
+            f"derived: {sms} SMs (device query) x 128 FP32 lanes x 2 x sm_max_mhz {mhz:.0f}")
 
 
 class ClockSampler:
@@ -224,61 +229,273 @@ def _dist():
     return ws, rank, local
 
 
-def cpu_oracle_sample(w, L, R, n_terms=16, reps=1):
-    """Times the FP64 oracle on `n_terms` terms of one collide; returns seconds per full collide."""
+# ---------------------------------------------------------------------------------------
+# The FP64 oracle on the host cores: one spawned process per core, each holding the oracle
+# plan (F table) of one contiguous term range; a collide sends f to every process and adds
+# their partial sums.  Used by the cpu_baseline leg, the reference arm and the measured error.
+# ---------------------------------------------------------------------------------------
+
+def _host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def _oracle_worker(conn, spec, p0, p1):
+    """Serves one term range: ("plan",) builds the F table of [p0, p1); ("collide", f, real)
+    returns (partial Q over the range, seconds); ("at", f, kidx, real) returns the partial Q at
+    the modes kidx (F computed at those modes only); ("stop",) ends."""
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"                      # one core per process
     import numpy as np
-    from oracle import kernels, spectral
-    N, P = w["N"], w["N_rho"] * w["M"]
-    sel = np.linspace(0, P - 1, n_terms).astype(int)
-    if w.get("dim", 3) == 2:
-        from oracle import spectral2d
-        name = {3: "b1", 4: "b2", 5: "b3", 6: "b4"}[w["kernel"]]
-        plan = spectral2d.OraclePlan2D(N, L, R, w["gamma"], kernels.Kernel2D(name), w["N_rho"], w["M"])
-        f = _fhat(w, L)
+    from oracle import ftable, kernels, spectral, spectral2d
+    dim2 = spec.get("dim", 3) == 2
+    kern = kernels.Kernel2D(spec["kernel2d"]) if dim2 else kernels.Kernel("family", spec["s"])
+    plan = lite = None
+    while True:
+        msg = conn.recv()
+        if msg[0] == "stop":
+            break
+        if msg[0] == "plan":
+            t0 = time.perf_counter()
+            if dim2:
+                plan = spectral2d.OraclePlan2D(spec["N"], spec["L"], spec["R"], spec["gamma"], kern, spec["N_rho"],
+                                               spec["M"])
+            else:
+                plan = spectral.OraclePlan(spec["N"], spec["L"], spec["R"], spec["gamma"], kern, spec["N_rho"],
+                                           spec["M"], terms=np.arange(p0, p1))
+            conn.send(time.perf_counter() - t0)
+        elif msg[0] == "collide":
+            f, real = msg[1], msg[2]
+            t0 = time.perf_counter()
+            if dim2:
+                q = spectral2d.collide2d(plan, f, p0, p1)
+            else:
+                q = (spectral.collide_real if real else spectral.collide)(plan, f, p0, p1)
+            conn.send((q, time.perf_counter() - t0))
+        elif msg[0] == "at":
+            f, kidx, real = msg[1], msg[2], msg[3]
+            if lite is None:
+                lite = spectral.OraclePlan(spec["N"], spec["L"], spec["R"], spec["gamma"], kern, spec["N_rho"],
+                                           spec["M"], with_table=False)
+            ks = spectral.signed(spec["N"])[kidx]
+            n = p1 - p0
+            F_at = ftable.fentries(spec["N"], spec["L"], np.repeat(ks, n, axis=0), np.tile(lite.r[p0:p1], len(ks)),
+                                   np.tile(lite.q[p0:p1], (len(ks), 1)), kern).reshape(len(ks), n)
+            g = spectral.real_band(f) if real else f
+            conn.send(spectral.collide_at(lite, g, kidx, F_at, p0, p1))
+
+
+class OracleCores:
+    """The oracle spread over processes, one term range each (spawned: no fork after CUDA)."""
+
+    def __init__(self, spec, ranges):
+        import multiprocessing as mp
+        ctx = mp.get_context("spawn")
+        self.ranges = [(a, b) for a, b in ranges if b > a]
+        self.conns, self.procs = [], []
+        for a, b in self.ranges:
+            parent, child = ctx.Pipe()
+            proc = ctx.Process(target=_oracle_worker, args=(child, spec, a, b), daemon=True)
+            proc.start()
+            self.conns.append(parent)
+            self.procs.append(proc)
+
+    @property
+    def terms(self):
+        return sum(b - a for a, b in self.ranges)
+
+    def build(self):
+        for c in self.conns:
+            c.send(("plan",))
+        return max(c.recv() for c in self.conns)
+
+    def collide(self, f, real):
+        """(sum of the partial Q over the ranges, wall seconds of the parallel region)."""
         t0 = time.perf_counter()
-        h = spectral2d.dft2(f, +1)
-        for p in sel:
-            _ = plan.alpha(p) * spectral2d.dft2(h * spectral2d.dft2(f * plan.beta(p), +1), -1) / N ** 2
-        return (time.perf_counter() - t0) * P / n_terms
-    plan = spectral.OraclePlan(N, L, R, w["gamma"], kernels.Kernel("family", w["s"]), w["N_rho"],
-                               w["M"], terms=sel)
-    f = _fhat(w, L)
-    best = float("inf")
-    for _ in range(reps):
+        for c in self.conns:
+            c.send(("collide", f, real))
+        parts = [c.recv() for c in self.conns]
+        return sum(q for q, _ in parts), time.perf_counter() - t0
+
+    def at(self, f, kidx, real):
+        for c in self.conns:
+            c.send(("at", f, kidx, real))
+        return sum(c.recv() for c in self.conns)
+
+    def close(self):
+        for c in self.conns:
+            try:
+                c.send(("stop",))
+            except OSError:
+                pass
+        for p in self.procs:
+            p.join(timeout=10)
+
+
+def _split(p0, p1, parts):
+    """Contiguous near-equal ranges covering [p0, p1)."""
+    n = p1 - p0
+    cuts = [p0 + (n * i) // parts for i in range(parts + 1)]
+    return list(zip(cuts[:-1], cuts[1:]))
+
+
+def _oracle_spec(w, L, R):
+    spec = {"N": w["N"], "L": L, "R": R, "gamma": w["gamma"], "s": w["s"], "N_rho": w["N_rho"], "M": w["M"],
+            "dim": w.get("dim", 3)}
+    if spec["dim"] == 2:
+        spec["kernel2d"] = {3: "b1", 4: "b2", 5: "b3", 6: "b4"}[w["kernel"]]
+    return spec
+
+
+def cpu_baseline_cores(w, L, R, f, real, target_s=15.0):
+    """The FP64 oracle on every host core on a bounded sample: each process builds the F table
+    of a few consecutive terms (a one-time plan cost, not timed) and runs the operator over them
+    until about target_s of CPU work is done in all; evals/s = (terms per second over all
+    processes) / P."""
+    cores = _host_cores()
+    P = w["N_rho"] * w["M"]
+    per = max(1, min(P // cores, 2))
+    starts = [int(x) for x in (P - per) * (0.5 + __import__("numpy").arange(cores)) / cores]
+    oc = OracleCores(_oracle_spec(w, L, R), [(a, a + per) for a in starts])
+    try:
+        oc.build()
+        _, t1 = oc.collide(f, real)                  # one pass: the rate estimate
+        reps = max(1, int(target_s / cores / max(t1, 1e-3)))
         t0 = time.perf_counter()
-        h = spectral.dft3(f, +1)
-        for p in sel:
-            g = spectral.dft3(f * plan.beta(p), +1)
-            U = spectral.dft3(h * g, -1) / N ** 3
-            _ = plan.alpha(p) * U
-        best = min(best, time.perf_counter() - t0)
-    return best * P / n_terms
+        for _ in range(reps):
+            oc.collide(f, real)
+        wall = time.perf_counter() - t0
+    finally:
+        oc.close()
+    rate = oc.terms * reps / wall                   # terms per second, all processes
+    return {"value": rate / P, "unit": "evals/s", "cores": cores, "kind": "oracle",
+            "sample": f"{per} terms per process x {cores} processes (one per host core), {reps} passes of the "
+                      f"operator over them ({oc.terms} of {P} terms of one N={w['N']} collide), terms per second "
+                      f"/ P; the F-table build (a one-time plan cost) is excluded"}
+
+
+def sampled_modes(q_gpu, n_top=24, n_rand=24, seed=12):
+    """Modes at which the oracle checks a collide: the n_top largest |Qhat| and n_rand seeded
+    uniform ones (array indices [S, 3])."""
+    import numpy as np
+    import bz_inputs as bi
+    N = q_gpu.shape[0]
+    top = np.argsort(np.abs(q_gpu).ravel())[::-1][:n_top]
+    u = bi.SplitMix64(seed).uniform(n_rand)
+    rnd = (u * N ** 3).astype(np.int64)
+    flat = np.unique(np.concatenate([top, rnd]))
+    return np.stack(np.unravel_index(flat, q_gpu.shape), axis=1)
+
+
+def error_vs_oracle(w, L, R, f, q_gpu, p0=0, p1=None, real=False, also_realq=False):
+    """Relative L-infinity error of a GPU collide (terms [p0, p1)) against the FP64 oracle at the
+    sampled modes: max_s |Q_gpu(k_s) - Q_oracle(k_s)| / max_k |Q_gpu(k)|, the oracle spread over
+    the host cores.  real: against the real-data reading; also_realq: also against eq. realQ on
+    the unmodified input."""
+    import numpy as np
+    P = w["N_rho"] * w["M"]
+    p1 = P if p1 is None else p1
+    kidx = sampled_modes(q_gpu)
+    t0 = time.perf_counter()
+    oc = OracleCores(_oracle_spec(w, L, R), _split(p0, p1, min(_host_cores(), p1 - p0)))
+    try:
+        ref = oc.at(f, kidx, real)
+        ref2 = oc.at(f, kidx, False) if (real and also_realq) else None
+    finally:
+        oc.close()
+    norm = float(np.max(np.abs(q_gpu)))
+    got = q_gpu[kidx[:, 0], kidx[:, 1], kidx[:, 2]]
+    out = {"rel_linf": float(np.max(np.abs(got - ref)) / norm), "modes": int(len(kidx)), "terms": [p0, p1],
+           "reference": "real-data reading (Hermitian, Nyquist-free part of f)" if real else "eq. realQ",
+           "oracle_s": time.perf_counter() - t0, "cores": _host_cores()}
+    if ref2 is not None:
+        out["rel_linf_vs_eq_realQ"] = float(np.max(np.abs(got - ref2)) / norm)
+    return out
 
 
 def run_reference(args, w):
+    """The FP64 oracle on the host cores, on this arm's workload, metric and unit: a step is
+    the same unit as the GPU arm's (an RK4 step = 4 full collides through the oracle's RK4
+    stage formula, or one full collide) when K + W of them fit in about three minutes, else a
+    full collide's terms sampled evenly (extrapolated).  Rank 0 only."""
+    import numpy as np
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
+    from oracle import spectral
     L, R = _geometry(w)
-    cpu_oracle_sample(w, L, R, n_terms=2)       # builds the oracle library, warms up
-    times = []
-    for i in range(args.warmup + args.steps):
-        t = cpu_oracle_sample(w, L, R, n_terms=8)
-        if i >= args.warmup:
-            times.append(t)
-    sec_per_collide = statistics.median(times)
-    value = 1.0 / sec_per_collide
-    sample = f"8 of {w['N_rho'] * w['M']} terms of one N={w['N']} collide per step, extrapolated"
+    f = _fhat(w, L)
+    real = args.data == "real" or (args.data == "auto" and _real_supported(w))
+    cores = _host_cores()
+    P = w["N_rho"] * w["M"]
+    is_rk = w["dt"] is not None
+    budget = 180.0
+    # estimate from one term per core: F-table seconds per term and operator seconds per term
+    starts = [a for a, _ in _split(0, P, cores)]
+    probe = OracleCores(_oracle_spec(w, L, R), [(a, a + 1) for a in starts])
+    try:
+        tf = probe.build()
+        _, tc = probe.collide(f, real)
+    finally:
+        probe.close()
+    collide_s = tc * P / cores                       # wall of one full collide on every core
+    steps = args.steps + args.warmup
+    if is_rk and steps * 4 * collide_s + tf * P / cores < budget:
+        mode, terms = "rk4", P
+    elif steps * collide_s + tf * P / cores < budget:
+        mode, terms = "collide", P
+    else:
+        mode = "sample"
+        terms = max(cores, min(P, int(budget / steps / max(tc, 1e-6) * cores / 2)))
+    ranges = _split(0, P, cores) if terms == P else [(a, a + max(1, terms // cores)) for a in starts]
+    oc = OracleCores(_oracle_spec(w, L, R), ranges)
+    try:
+        oc.build()
+        frac = P / oc.terms
+
+        def rhs(g):
+            q, _ = oc.collide(g, real)
+            return q
+
+        times = []
+        fcur = f.copy()
+        for i in range(steps):
+            t0 = time.perf_counter()
+            if mode == "rk4":
+                fcur = spectral.rk4_steps(rhs, fcur, w["dt"], 1)
+            else:
+                rhs(fcur)
+            dt_s = time.perf_counter() - t0
+            if i >= args.warmup:
+                times.append(dt_s)
+    finally:
+        oc.close()
+    evals_per_step = 4 if mode == "rk4" else 1
+    sec_per_step = statistics.median(times) * (frac if mode == "sample" else 1.0)
+    value = evals_per_step / sec_per_step
+    sample = {"rk4": f"full RK4 steps (4 full collides of all {P} terms each) on {cores} host cores",
+              "collide": f"one full collide (all {P} terms) per step on {cores} host cores",
+              "sample": f"{oc.terms} of {P} terms of one collide per step on {cores} host cores, "
+                        f"extrapolated to all terms"}[mode]
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "evals/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * sec_per_collide * (4 if w["dt"] else 1),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": args.workload, "desc": w["desc"]},
-            "cpu_baseline": {"value": value, "unit": "evals/s", "cores": 1, "kind": "oracle",
-                             "sample": sample},
+            "ms_per_step": 1e3 * statistics.median(times), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": _config(args, w, real),
+            "collides_per_step": evals_per_step,
+            "cpu_baseline": {"value": value, "unit": "evals/s", "cores": cores, "kind": "oracle",
+                             "sample": sample + "; the F-table build (a one-time plan cost) is excluded"},
             "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
+
+
+def _config(args, w, real):
+    """The workload as both arms name it."""
+    return {"workload": args.workload, "desc": w["desc"], "P": w["N_rho"] * w["M"],
+            "data_form": "real" if real else "complex"}
 
 
 def _real_supported(w):
@@ -343,20 +560,97 @@ def _roofline(args, w, kern, peaks, src, profile_key):
     avg_s = ms_k / 1e3 / max(n_launch, 1)
     fl = _flops_per_term(N, dim).get(dom, 0.0) * terms_per_launch
     by = _bytes_per_term(N, dim).get(dom, 0.0) * terms_per_launch
-    sm_clock = peaks.get("sm_max_mhz", 2070.0)
-    alu_peak = 152 * 128 * 2 * sm_clock * 1e6 / 1e12      # FP32 FMA lanes x 2 flops x clock
+    alu_peak, sms, alu_src = _alu_peak(peaks)
     alu = {"bound": "alu", "achieved": fl / avg_s / 1e12, "peak": alu_peak, "unit": "TFLOP/s"}
     hbm = {"bound": "hbm", "achieved": by / avg_s / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
     for r in (alu, hbm):
         r["frac"] = r["achieved"] / r["peak"]
     roof = max((alu, hbm), key=lambda r: r["frac"])
     other = hbm if roof is alu else alu
-    key = profile_key if dom == "fused" else dom
-    roof.update({"kernel": dom, "traffic": _profiled_traffic(key, args.workload),
-                 "peak_source": f"{src}" if roof is hbm else "derived: 152 SMs x 128 FP32 lanes x 2 x sm_max_mhz",
+    if profile_key == "n64":
+        key = f"n64:{dom}"                 # the chunked kernels at N = 64, P = 4096
+    elif args.workload == "rk4_n32" and dom == "fused":
+        key = profile_key
+    else:
+        key = None
+    roof.update({"kernel": dom, "traffic": _profiled_traffic(key),
+                 "peak_source": f"{src}" if roof is hbm else alu_src, "sm_count": sms,
                  "launches": n_launch, "avg_launch_us": avg_s * 1e6,
                  "also": {k: other[k] for k in ("bound", "achieved", "peak", "unit", "frac")}})
     return roof
+
+
+def run_sharded(args, w):
+    """Under torchrun with N > 1 ranks, the single-collide workloads shard the terms (strong
+    scaling): per step each rank evaluates its term range with bz_collide_terms and one NCCL
+    all-reduce of the N^3 complex128 result completes Qhat on every rank; value = collides per
+    second of the whole job (each collide counted once), max time over ranks."""
+    import torch
+    import torch.distributed as dist
+    ws, rank, local = _dist()
+    dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import paper_2004_11239_gb300 as bz
+    from paper_2004_11239_gb300 import shard
+    L, R = _geometry(w)
+    real = args.data == "real" or (args.data == "auto" and _real_supported(w))
+    plan = bz.bz_plan_create_ex(w["N"], L, R, w["gamma"], w["s"], w["N_rho"], w["M"],
+                                data=bz.BZ_DATA_REAL if real else bz.BZ_DATA_COMPLEX)
+    f_host = _fhat(w, L)
+    f = torch.from_numpy(f_host).to("cuda")
+    q = torch.empty_like(f)
+    p0, p1 = bz.bz_partition_terms(plan.P, plan.data, ws, rank)
+
+    def step():
+        shard.collide_sharded(plan, f, q)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    launches = bz.bz_plan_last_launches(plan)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clk = ClockSampler(local)
+    clk.__enter__()
+    dist.barrier()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(args.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    dist.barrier()
+    clk.__exit__(None, None, None)
+    ms = max_over_ranks(e0.elapsed_time(e1))
+    value = args.steps / (ms / 1e3)
+    # end to end: the input copied from pinned host memory to every rank, the result read back
+    h_in = torch.from_numpy(f_host).pin_memory()
+    h_out = torch.empty_like(h_in).pin_memory()
+    dist.barrier()
+    torch.cuda.synchronize()
+    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2.record()
+    for _ in range(args.steps):
+        f.copy_(h_in, non_blocking=True)
+        step()
+        h_out.copy_(q, non_blocking=True)
+    e3.record()
+    torch.cuda.synchronize()
+    ms_e2e = max_over_ranks(e2.elapsed_time(e3))
+    nbytes = f.numel() * f.element_size()
+    if rank == 0:
+        cfg = _config(args, w, real)
+        cfg.update({"terms_per_rank": [list(bz.bz_partition_terms(plan.P, plan.data, ws, r)) for r in range(ws)],
+                    "exchange": "one NCCL all-reduce (sum) of the N^3 complex128 result per collide",
+                    "l2": "inputs larger than L2: each rank streams its slice of the pair or alpha table"})
+        print(json.dumps({"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": ws, "steps": args.steps,
+                          "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                          "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                          "config": cfg, "clocks": clk.summary(), "gpu_launches": launches * args.steps,
+                          "e2e": {"value": args.steps / (ms_e2e / 1e3), "unit": "evals/s",
+                                  "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}}))
+    plan.close()
+    dist.destroy_process_group()
+    return 0
 
 
 def run_ours(args, w):
@@ -420,7 +714,8 @@ def run_ours(args, w):
 
     peaks, src = _peaks()
     kname = pipe.get("kernel", "k_fused")
-    roof = _roofline(args, w, kern, peaks, src, "pair3" if kname == "k_pair3" else ("fused_real" if real else "fused"))
+    roof = _roofline(args, w, kern, peaks, src, "n64" if (args.workload == "single_n64" and real) else
+                     ("pair3" if kname == "k_pair3" else ("fused_real" if real else "fused")))
     roof["kernel_name"] = kname
     if real:
         roof["executed"] = ("term pairs share every pair of 3D transforms: about half the counted FFT "
@@ -451,31 +746,41 @@ def run_ours(args, w):
         if pc is not plan:
             pc.close()
 
+    # parity of one headline collide against the FP64 oracle (host cores), after the timed regions
+    parity = None
+    if rank == 0 and not args.no_cpu_baseline and dim == 3:
+        f0 = torch.from_numpy(f_host).to("cuda")
+        bz.bz_collide(plan, f0, q, st)
+        torch.cuda.synchronize()
+        parity = error_vs_oracle(w, L, R, f_host, q.cpu().numpy().astype(np.complex128), real=real,
+                                 also_realq=real)
+        parity["collide"] = "one full collide of the workload's input through bz_collide"
+
+    n64 = None
+    if args.workload == "rk4_n32" and not args.no_n64:
+        n64 = _measure_n64(args, bz, peaks, src, barrier, rank == 0 and not args.no_cpu_baseline)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        P = w["N_rho"] * w["M"]
-        per_term = cpu_oracle_sample(w, L, R, n_terms=2) / P
-        n_terms = int(max(4, min(P, 15.0 / max(per_term, 1e-6))))   # about 15 s of oracle work
-        sec = cpu_oracle_sample(w, L, R, n_terms=n_terms)
-        cpu = {"value": 1.0 / sec, "unit": "evals/s", "cores": 1, "kind": "oracle",
-               "sample": f"{n_terms} of {P} terms of one collide (FP64 oracle, one thread), "
-                         "extrapolated to all terms; F-table build excluded"}
+        cpu = cpu_baseline_cores(w, L, R, f_host, real)
 
     streamed = plan.alpha_bytes - (plan.P * N ** 3 * 8 if real else 0)
     form_desc = ("real: f is real, fhat's Hermitian part with the Nyquist planes (index -N/2) dropped "
-                 "(BZ_DATA_REAL; parity with eq. realQ on this input 6e-6 at full size)" if real else
+                 "(BZ_DATA_REAL; `parity` gives its measured distance from eq. realQ on this input)" if real else
                  "complex: eq. realQ on fhat as given (BZ_DATA_COMPLEX)")
+    config = _config(args, w, real)
+    config.update({"data_form_desc": form_desc, "pipeline": pipe, "collides_per_step": evals_per_step,
+                   "l2": "inputs larger than L2: the %s of %d MB streams every collide"
+                         % ("pair table" if real else "alpha table", streamed >> 20)})
     line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": args.workload, "desc": w["desc"], "P": w["N_rho"] * w["M"],
-                       "data_form": form_desc, "pipeline": pipe,
-                       "collides_per_step": evals_per_step,
-                       "l2": "inputs larger than L2: the %s of %d MB streams every collide"
-                             % ("pair table" if real else "alpha table", streamed >> 20)},
+            "config": config,
             "clocks": clocks, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
             "roofline": roof, "kernels_ms": {k: v[1] for k, v in kern.items()},
-            "cpu_baseline": cpu}
+            "parity": parity, "cpu_baseline": cpu}
+    if n64 is not None:
+        line["n64"] = n64
     if other is not None:
         line["other_form"] = other
     if mixed is not None:
@@ -487,6 +792,43 @@ def run_ours(args, w):
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+N64 = dict(N=64, N_rho=64, M=64, gamma=-1.0, s=0.5, R=None, L=10.0, dt=None, data="c3",
+           desc="single collide, N=64, N_rho=64, M=64 (P=4096), gamma=-1, s=0.5, L=10, bi-Gaussian "
+                "(T=2, 0.5, 0.5) plus 1% seeded noise; real-data form on the chunked pipeline")
+
+
+def _measure_n64(args, bz, peaks, src, barrier, with_parity):
+    """The single-instance heavy collide (N = 64, P = 4096, gamma = -1): evals/s over K collides,
+    the dominant chunked kernel's roofline (per-kernel CUDA events over K more collides), and the
+    relative L-infinity error against the FP64 oracle on one full collide at sampled modes."""
+    import numpy as np
+    import torch
+    w = N64
+    L, R = _geometry(w)
+    t0 = time.perf_counter()
+    plan = bz.bz_plan_create_ex(64, L, R, w["gamma"], w["s"], w["N_rho"], w["M"], data=bz.BZ_DATA_REAL)
+    plan_s = time.perf_counter() - t0
+    f_host = _fhat(w, L)
+    f = torch.from_numpy(f_host).to("cuda")
+    q = torch.empty_like(f)
+    st = torch.cuda.current_stream()
+    a = argparse.Namespace(**vars(args))
+    a.steps = max(5, min(args.steps, 50))
+    value, ms, kern, launches, _ = _time_plan(a, w, bz, plan, f, q, st, barrier)
+    roof = _roofline(a, w, kern, peaks, src, "n64")
+    out = {"desc": w["desc"], "value": value, "unit": "evals/s", "steps": a.steps, "ms_per_collide": ms / a.steps,
+           "gpu_launches": launches * a.steps, "plan_create_s": plan_s, "roofline": roof,
+           "kernels_ms": {k: v[1] / a.steps for k, v in kern.items()}, "pipeline": bz.bz_plan_pipeline(plan),
+           "l2": "inputs larger than L2: the 4.3 GB pair table streams every collide"}
+    if with_parity:
+        bz.bz_collide(plan, f, q, st)
+        torch.cuda.synchronize()
+        out["parity"] = error_vs_oracle(w, L, R, f_host, q.cpu().numpy().astype(np.complex128), real=True)
+        out["parity"]["collide"] = "one full collide (all 4096 terms) through bz_collide"
+    plan.close()
+    return out
 
 
 def _tc_flops_per_term(N):
@@ -549,7 +891,7 @@ def _measure_mixed(args, w, bz, plan32, f_host, L, R, st, peaks, src, barrier):
             "gpu_launches": launches_per_step * args.steps,
             "roofline": {"bound": "tensor", "kernel": "k_mixed", "achieved": tc, "peak": tc_peak,
                          "unit": "TFLOP/s", "frac": tc / tc_peak,
-                         "traffic": _profiled_traffic("mixed", args.workload), "launches": n_launch,
+                         "traffic": _profiled_traffic("mixed" if args.workload == "rk4_n32" else None), "launches": n_launch,
                          "avg_launch_us": avg_s * 1e6,
                          "peak_source": f"{src} bf16 (sustained)" if "bf16_tflops_sustained" in peaks else src,
                          "work": "split-BF16 DFT-GEMM flops: 6 x 2 N^2 x 2N x 3 x 2N per term",
@@ -612,12 +954,12 @@ def run_batch(args, w):
     # shares each group's alpha table, so the step is bound by the CUDA cores, not by HBM)
     flops = sum(4 * len(r[5]) * r[2].P * _flops_per_term(r[0])["fused"] for r in runs) * args.steps
     peaks, _ = _peaks()
-    alu_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    alu_peak, sms, alu_src = _alu_peak(peaks)
     achieved = flops / (ms / 1e3) / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak,
             "kernel": "whole step (k_fused dominant)", "traffic": None,
-            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x sm_max_mhz",
-            "work": "30 N^3 log2 N + 20 N^3 flops per term, 4 collides per RK4 step"}
+            "peak_source": alu_src, "sm_count": sms,
+            "work": "30 N^3 log2 N + 26 N^3 flops per term, 4 collides per RK4 step"}
     line = {"metric": METRIC, "value": evals / (ms / 1e3), "unit": "evals/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -688,12 +1030,12 @@ def run_inhom(args, w):
     nbytes = fd.numel() * fd.element_size()
     flops = 4 * nx * plan.P * _flops_per_term(N)["fused"] * args.steps
     peaks, _ = _peaks()
-    alu_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    alu_peak, sms, alu_src = _alu_peak(peaks)
     achieved = flops / (ms / 1e3) / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak,
             "kernel": "whole step (k_fused dominant)", "traffic": None,
-            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x sm_max_mhz",
-            "work": "30 N^3 log2 N + 20 N^3 flops per term, 4 collides per cell per step"}
+            "peak_source": alu_src, "sm_count": sms,
+            "work": "30 N^3 log2 N + 26 N^3 flops per term, 4 collides per cell per step"}
     line = {"metric": METRIC, "value": evals / (ms / 1e3), "unit": "evals/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -790,6 +1132,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="rk4_n32", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-n64", action="store_true",
+                    help="skip the N = 64 single-collide block measured beside the default workload")
     ap.add_argument("--no-mixed", action="store_true",
                     help="skip the split-BF16 tensor-core form (measured beside the FP32 form at N = 32)")
     ap.add_argument("--rates", default=None, help="serve workload: comma-separated arrival rates (req/s)")
@@ -804,6 +1148,13 @@ def main():
                     help="h = IFFT(fhat) precision on the fused path: 0 auto (FP64), 1 FP64, 2 FP32")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
+    if args.impl == "reference" and args.workload in ("batch_4096", "serve"):
+        # the oracle computes one collide at a time: its rate on one instance is the reference
+        ws, rank, _ = _dist()
+        if rank == 0:
+            print(json.dumps({"impl": "reference", "unavailable": "the FP64 oracle has no batched or served "
+                              "form; its per-collide rate is the reference of --workload rk4_n32"}))
+        return 0
     if args.workload == "batch_4096":
         return run_batch(args, w)
     if args.workload == "serve":
@@ -812,6 +1163,8 @@ def main():
         return run_reference(args, w)
     if args.workload == "inhom_n16":
         return run_inhom(args, w)
+    if _dist()[0] > 1 and w["dt"] is None and w.get("dim", 3) == 3:
+        return run_sharded(args, w)
     return run_ours(args, w)
 
 

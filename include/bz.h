@@ -197,6 +197,17 @@ bz_status bz_plan_terms(const bz_plan *plan, double *r, double *w_r, double *qha
 bz_status bz_quadrature(int N_rho, double R, int M, double gamma, double *r, double *w_r, double *qhat,
                         double *w_q, double *c);
 
+/* Host only (no GPU needed).  The terms one rank of a term-sharded collide evaluates.  The sum
+ * over p in eq. realQ (Sec. 4) is a sum of independent terms, so `world` ranks can each
+ * evaluate a contiguous range [*p0, *p1) with bz_collide_terms and add their N^3 results with
+ * one all-reduce (sum); the ranges of ranks 0 .. world-1 are near-equal, in rank order, and
+ * cover [0, P) exactly once.  data = BZ_DATA_REAL splits the P/2 term pairs so that both
+ * terms of a pair (2q, 2q+1) stay on one rank (the bounds are even, as bz_collide_terms needs
+ * for a real-data plan); a rank may get an empty range (*p0 == *p1) when world > P (or P/2).
+ * Errors: BZ_ERR_ARG for NULL outputs, P < 0, world < 1, rank outside [0, world), an unknown
+ * data form or an odd P with BZ_DATA_REAL. */
+bz_status bz_partition_terms(int P, int data, int world, int rank, int *p0, int *p1);
+
 /* Host only.  The angular kernel's normalisation c (g = sin(theta) b(cos theta), lambda = 1/6)
  * and the part-I moments A = (int g (1-cos), int g (1-cos)^2, int g sin^2) over [0, eps]
  * (Sec. 4.1; eps <= 0 selects pi/1000). */

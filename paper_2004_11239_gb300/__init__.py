@@ -21,7 +21,7 @@ __all__ = [
     "bz_collide", "bz_collide_terms", "bz_step_rk", "bz_moments", "bz_ftable_entries",
     "bz_plan_alpha", "bz_plan_last_launches", "bz_plan_device_errors", "bz_status_str", "library_path", "lib",
     "bz_plan_set_timing", "bz_plan_timing", "bz_collide_noalloc", "bz_plan_pipeline",
-    "bz_quadrature", "bz_kernel_constants",
+    "bz_quadrature", "bz_kernel_constants", "bz_partition_terms",
     "bz_batch_create", "bz_batch_destroy", "bz_batch_set_gamma", "bz_batch_collide", "bz_batch_step_rk",
     "bz_batch_last_launches", "bz_server_create", "bz_submit", "bz_poll", "bz_server_stats",
     "bz_transport_x", "bz_inhom_step", "bz_plan_kernel",
@@ -91,6 +91,7 @@ def _load():
         "bz_plan_pipeline": [vp, ip, ip, ip, ctypes.POINTER(ctypes.c_float)],
         "bz_quadrature": [c_int, c_double, c_int, c_double, dp, dp, dp, dp, dp],
         "bz_kernel_constants": [c_int, c_double, c_double, dp, dp],
+        "bz_partition_terms": [c_int, c_int, c_int, c_int, ip, ip],
         "bz_collide": [vp, vp, vp, c_int, vp],
         "bz_collide_terms": [vp, c_int, c_int, vp, vp, c_int, vp],
         "bz_step_rk": [vp, vp, c_int, dp, c_double, c_int, vp, vp],
@@ -173,11 +174,12 @@ def _dev(t, n3: int):
 class Plan:
     """Owning handle of a bz_plan (destroyed with the object or by close())."""
 
-    def __init__(self, handle: ctypes.c_void_p, N: int, L: float, dim: int = 3):
+    def __init__(self, handle: ctypes.c_void_p, N: int, L: float, dim: int = 3, data: int = BZ_DATA_COMPLEX):
         self.handle = handle
         self.N = N
         self.L = L
         self.dim = dim
+        self.data = data
         P = ctypes.c_int()
         ab = ctypes.c_size_t()
         wb = ctypes.c_size_t()
@@ -234,7 +236,7 @@ def bz_plan_create_ex(N: int, L: float, R: float, gamma: float, s: float, N_rho:
         d.sphere_w = w.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     h = ctypes.c_void_p()
     _check(lib.bz_plan_create_ex(ctypes.byref(h), ctypes.byref(d)), "bz_plan_create_ex")
-    return Plan(h, N, L, dim)
+    return Plan(h, N, L, dim, data)
 
 
 def bz_plan_destroy(plan: Plan):
@@ -253,6 +255,13 @@ def bz_plan_pipeline(plan: Plan):
            "bz_plan_pipeline")
     return {"pipeline": "fused" if p.value == BZ_PIPE_FUSED else "chunked", "cluster": c.value,
             "clusters": g.value, "tuned_ms": t.value, "kernel": lib.bz_plan_kernel(plan.handle).decode()}
+
+
+def bz_partition_terms(P: int, data: int, world: int, rank: int):
+    """Host-only: the term range (p0, p1) of `rank` in a collide sharded over `world` ranks."""
+    a, b = ctypes.c_int(), ctypes.c_int()
+    _check(lib.bz_partition_terms(P, data, world, rank, ctypes.byref(a), ctypes.byref(b)), "bz_partition_terms")
+    return a.value, b.value
 
 
 def bz_quadrature(N_rho: int, R: float, M: int, gamma: float):

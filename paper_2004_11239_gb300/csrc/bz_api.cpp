@@ -393,6 +393,20 @@ bz_status bz_plan_device_errors(bz_plan *plan, int *count) {
     return BZ_OK;
 }
 
+bz_status bz_partition_terms(int P, int data, int world, int rank, int *p0, int *p1) {
+    if (!p0 || !p1 || P < 0 || world < 1 || rank < 0 || rank >= world) return BZ_ERR_ARG;
+    if (data != BZ_DATA_COMPLEX && data != BZ_DATA_REAL) return BZ_ERR_ARG;
+    // contiguous near-equal ranges in rank order; BZ_DATA_REAL splits the P / 2 term pairs so
+    // that both terms of a pair (2q, 2q + 1) stay on one rank
+    const long u = data == BZ_DATA_REAL ? P / 2 : P;
+    if (data == BZ_DATA_REAL && (P & 1)) return BZ_ERR_ARG;
+    const long a = u * rank / world, b = u * (rank + 1) / world;
+    const int scale = data == BZ_DATA_REAL ? 2 : 1;
+    *p0 = (int)(a * scale);
+    *p1 = (int)(b * scale);
+    return BZ_OK;
+}
+
 bz_status bz_quadrature(int N_rho, double R, int M, double gamma, double *r, double *w_r, double *qhat,
                         double *w_q, double *c) {
     if (N_rho < 1 || M < 1 || !(R > 0) || !std::isfinite(gamma)) return BZ_ERR_ARG;
