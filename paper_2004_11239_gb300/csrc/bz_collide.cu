@@ -21,7 +21,9 @@ template <int N> struct Cfg {
     static constexpr int PPC = N <= 8 ? 8 : (N <= 16 ? 16 : (N <= 32 ? 8 : (N <= 48 ? 4 : 2)));
     static constexpr int LD = N + 1;                                              // padded row
     static constexpr int THREADS = PPC * N;
-    static constexpr size_t SMEM = (size_t)PPC * N * LD * sizeof(float2);
+    static constexpr size_t SMEM = ((size_t)PPC * N * LD + 6 * N) * sizeof(float2);   // planes + a pair's twiddles
+    // resident CTAs per SM the register budget is held to (shared memory allows as many)
+    static constexpr int MINB = N == 64 ? 3 : (N == 48 ? 2 : 1);
 };
 
 // ---------------------------------------------------------------------------------------
@@ -30,35 +32,40 @@ template <int N> struct Cfg {
 // PAIR (BZ_DATA_REAL): unit t is the term pair (2u, 2u + 1), u = p0 + t, and the twiddle is
 // beta_2u + i beta_2u+1 (both terms' [3][N] vectors, contiguous).
 template <int N, bool PAIR = false>
-__global__ void __launch_bounds__(Cfg<N>::THREADS)
+__global__ void __launch_bounds__(Cfg<N>::THREADS, Cfg<N>::MINB)
 k_plane_inv(const float2 *__restrict__ fin, const float2 *__restrict__ tw, float2 *__restrict__ S,
             int p0, int use_tw) {
-    constexpr int PPC = Cfg<N>::PPC, LD = Cfg<N>::LD;
+    constexpr int PPC = Cfg<N>::PPC, LD = Cfg<N>::LD, NT = (PAIR ? 6 : 3) * N;
     extern __shared__ float2 sm[];
+    float2 *stw = sm + PPC * N * LD;                  // the term's twiddle vectors
     const int lane = threadIdx.x % N, pid = threadIdx.x / N;
     const int k1 = blockIdx.x * PPC + pid;
     const int t = blockIdx.y;
     float2 *s = sm + pid * N * LD;
     const float2 *f = fin + (size_t)k1 * N * N;
-    const float2 *twp = tw + (size_t)(p0 + t) * (PAIR ? 6 : 3) * N;
-    float2 t13 = make_float2(1.f, 0.f), t13b = make_float2(0.f, 0.f);
-    if (use_tw) t13 = cmul(twp[k1], twp[2 * N + lane]);
-    if (PAIR && use_tw) t13b = cmul(twp[3 * N + k1], twp[5 * N + lane]);
-    #pragma unroll 4
-    for (int i = 0; i < N; ++i) {
-        float2 v = f[i * N + lane];
-        if (use_tw) {
-            if constexpr (PAIR) {
-                const float2 u = cmul(t13, twp[N + i]), w = cmul(t13b, twp[4 * N + i]);
-                v = cmul(v, make_float2(u.x - w.y, u.y + w.x));
-            } else {
-                v = cmul(v, cmul(t13, twp[N + i]));
-            }
-        }
-        s[i * LD + lane] = v;
-    }
-    __syncthreads();
+    const float2 *twp = tw + (size_t)(p0 + t) * NT;
     float2 x[N];
+    #pragma unroll
+    for (int i = 0; i < N; ++i) x[i] = f[i * N + lane];   // every load of the plane in flight at once
+    if (use_tw) {
+        for (int i = threadIdx.x; i < NT; i += Cfg<N>::THREADS) stw[i] = twp[i];
+        __syncthreads();
+        const float2 t13 = cmul(stw[k1], stw[2 * N + lane]);
+        if constexpr (PAIR) {
+            const float2 t13b = cmul(stw[3 * N + k1], stw[5 * N + lane]);
+            #pragma unroll
+            for (int i = 0; i < N; ++i) {
+                const float2 u = cmul(t13, stw[N + i]), w = cmul(t13b, stw[4 * N + i]);
+                x[i] = cmul(x[i], make_float2(u.x - w.y, u.y + w.x));
+            }
+        } else {
+            #pragma unroll
+            for (int i = 0; i < N; ++i) x[i] = cmul(x[i], cmul(t13, stw[N + i]));
+        }
+    }
+    #pragma unroll
+    for (int i = 0; i < N; ++i) s[i * LD + lane] = x[i];
+    __syncthreads();
     #pragma unroll
     for (int j = 0; j < N; ++j) x[j] = s[lane * LD + j];
     fft_inplace<N, +1>(x);                       // axis 3: k3 -> j3
@@ -116,7 +123,7 @@ k_pencil(float2 *__restrict__ S, const float2 *__restrict__ h, float2 *__restric
 // PAIR (BZ_DATA_REAL): alpha is the pair table A, and the chunk's Nyquist sums X = C Z go to
 // Ss[t][3][N][N] (family layout; every entry written, zero where C is zero).
 template <int N, bool PAIR = false>
-__global__ void __launch_bounds__(Cfg<N>::THREADS)
+__global__ void __launch_bounds__(Cfg<N>::THREADS, Cfg<N>::MINB)
 k_plane_fwd(float2 *__restrict__ S, const float2 *__restrict__ alpha, int p0, const float2 *__restrict__ cpair = nullptr,
             float2 *__restrict__ Ss = nullptr) {
     constexpr int PPC = Cfg<N>::PPC, LD = Cfg<N>::LD;
@@ -126,6 +133,7 @@ k_plane_fwd(float2 *__restrict__ S, const float2 *__restrict__ alpha, int p0, co
     const int t = blockIdx.y;
     float2 *s = sm + pid * N * LD;
     float2 *pl = S + (size_t)t * N * N * N + (size_t)k1 * N * N;
+    const float2 *al = alpha + (size_t)(p0 + t) * N * N * N + (size_t)k1 * N * N;
     float2 x[N];
     #pragma unroll
     for (int i = 0; i < N; ++i) x[i] = pl[i * N + lane];     // column j3 = lane, over j2
@@ -139,9 +147,10 @@ k_plane_fwd(float2 *__restrict__ S, const float2 *__restrict__ alpha, int p0, co
     #pragma unroll
     for (int j = 0; j < N; ++j) s[lane * LD + j] = x[j];
     __syncthreads();
-    const float2 *al = alpha + (size_t)(p0 + t) * N * N * N + (size_t)k1 * N * N;
-    #pragma unroll 4
-    for (int i = 0; i < N; ++i) pl[i * N + lane] = cmul(s[i * LD + lane], al[i * N + lane]);
+    #pragma unroll
+    for (int i = 0; i < N; ++i) x[i] = al[i * N + lane];    // every weight load in flight at once
+    #pragma unroll
+    for (int i = 0; i < N; ++i) pl[i * N + lane] = cmul(s[i * LD + lane], x[i]);
     if constexpr (PAIR) {
         const float2 *cq = cpair + (size_t)(p0 + t) * 3 * N * N;
         float2 *xs = Ss + (size_t)t * 3 * N * N;
@@ -157,26 +166,58 @@ k_plane_fwd(float2 *__restrict__ S, const float2 *__restrict__ alpha, int p0, co
 
 // ---------------------------------------------------------------------------------------
 // reduce: acc[k] += sum_t S[t][k], Kahan-compensated in FP32 over the chunk's terms (in
-// term order), then added to the FP64 accumulator.
+// term order), then added to the FP64 accumulator.  Each thread takes two adjacent modes
+// (16-byte loads) and issues the loads of up to kRedBatch terms before it adds them, so the
+// chunk's loads are in flight together.  A second array (S2, n2 modes, acc2) may follow the
+// first in the same launch: thread pairs past n3 / 2 take it.
 // ---------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256)
-k_reduce(const float2 *__restrict__ S, int T, int n3, double2 *__restrict__ acc) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n3) return;
-    float sr = 0.f, si = 0.f, cr = 0.f, ci = 0.f;
-    for (int t = 0; t < T; ++t) {
-        float2 v = S[(size_t)t * n3 + k];
-        float yr = v.x - cr, yi = v.y - ci;
-        float tr = sr + yr, ti = si + yi;
-        cr = (tr - sr) - yr;
-        ci = (ti - si) - yi;
-        sr = tr;
-        si = ti;
+constexpr int kRedBatch = 8;
+
+struct Kahan4 {
+    float s[4] = {0.f, 0.f, 0.f, 0.f}, c[4] = {0.f, 0.f, 0.f, 0.f};
+    __device__ __forceinline__ void add(float4 v) {
+        const float x[4] = {v.x, v.y, v.z, v.w};
+        #pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float y = x[i] - c[i], t = s[i] + y;
+            c[i] = (t - s[i]) - y;
+            s[i] = t;
+        }
     }
-    double2 a = acc[k];
-    a.x += (double)sr - (double)cr;
-    a.y += (double)si - (double)ci;
-    acc[k] = a;
+};
+
+__global__ void __launch_bounds__(256)
+k_reduce(const float2 *__restrict__ S, int T, int n3, double2 *__restrict__ acc,
+         const float2 *__restrict__ S2 = nullptr, int n2 = 0, double2 *__restrict__ acc2 = nullptr) {
+    int k2 = blockIdx.x * blockDim.x + threadIdx.x;          // mode pair index
+    const float4 *src = (const float4 *)S;
+    int n = n3;
+    double2 *dst = acc;
+    if (k2 >= n3 / 2) {
+        k2 -= n3 / 2;
+        if (!S2 || k2 >= n2 / 2) return;
+        src = (const float4 *)S2;
+        n = n2;
+        dst = acc2;
+    }
+    const size_t stride = (size_t)n / 2;                     // float4 per term
+    Kahan4 sum;
+    for (int t0 = 0; t0 < T; t0 += kRedBatch) {
+        float4 v[kRedBatch];
+        #pragma unroll
+        for (int i = 0; i < kRedBatch; ++i)
+            if (t0 + i < T) v[i] = src[(size_t)(t0 + i) * stride + k2];
+        #pragma unroll
+        for (int i = 0; i < kRedBatch; ++i)
+            if (t0 + i < T) sum.add(v[i]);
+    }
+    double2 a = dst[2 * k2], b = dst[2 * k2 + 1];
+    a.x += (double)sum.s[0] - (double)sum.c[0];
+    a.y += (double)sum.s[1] - (double)sum.c[1];
+    b.x += (double)sum.s[2] - (double)sum.c[2];
+    b.y += (double)sum.s[3] - (double)sum.c[3];
+    dst[2 * k2] = a;
+    dst[2 * k2 + 1] = b;
 }
 
 __global__ void k_c128_to_c64(const double2 *__restrict__ in, float2 *__restrict__ out, int n) {
@@ -247,8 +288,10 @@ template <int N> static cudaError_t set_attrs() {
     return cudaSuccess;
 }
 
-// Terms per chunk: as many as one wave of plane CTAs holds (resident CTAs / CTAs per term),
-// capped by an L2-sized scratch of 32 MB.
+// Terms per chunk: two waves of plane CTAs (resident CTAs / CTAs per term, twice), so that
+// the second wave's loads overlap the first wave's arithmetic, capped by a scratch of 64 MB
+// that stays in L2 (measured at N = 64, P = 1024, real data: 2.56 ms per collide with one
+// wave of 14 pairs, 2.18 ms with two).
 template <int N> static int chunk_for() {
     int per_sm = 0, dev = 0, sms = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_plane_inv<N, false>, Cfg<N>::THREADS, Cfg<N>::SMEM) !=
@@ -258,8 +301,8 @@ template <int N> static int chunk_for() {
     }
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int wave = per_sm * sms / (N / Cfg<N>::PPC);
-    const int l2 = (int)(((size_t)32 << 20) / ((size_t)N * N * N * sizeof(float2)));
+    const int wave = 2 * per_sm * sms / (N / Cfg<N>::PPC);
+    const int l2 = (int)(((size_t)64 << 20) / ((size_t)N * N * N * sizeof(float2)));
     const int c = wave < l2 ? wave : l2;
     return c > 0 ? c : 1;
 }
@@ -320,10 +363,9 @@ static bz_status run_chunks_real(Plan &pl, int p0, int p1, cudaStream_t st, int 
                                                                                    pl.S_s);
         tm_end(pl, st, TK_PLANE_FWD);
         tm_begin(pl, st);
-        k_reduce<<<(n3 + 255) / 256, 256, 0, st>>>(pl.S, T, n3, pl.acc);
-        k_reduce<<<(ns + 255) / 256, 256, 0, st>>>(pl.S_s, T, ns, pl.acc_s);
+        k_reduce<<<(n3 / 2 + ns / 2 + 255) / 256, 256, 0, st>>>(pl.S, T, n3, pl.acc, pl.S_s, ns, pl.acc_s);
         tm_end(pl, st, TK_REDUCE);
-        nl += 5;
+        nl += 4;
     }
     tm_begin(pl, st);
     s = sym_output(pl, st);
@@ -360,7 +402,7 @@ static bz_status run_chunks(Plan &pl, int p0, int p1, cudaStream_t st, int *laun
         k_plane_fwd<N, false><<<dim3(N / PPC, T), Cfg<N>::THREADS, Cfg<N>::SMEM, st>>>(pl.S, pl.alpha, c0);
         tm_end(pl, st, TK_PLANE_FWD);
         tm_begin(pl, st);
-        k_reduce<<<(n3 + 255) / 256, 256, 0, st>>>(pl.S, T, n3, pl.acc);
+        k_reduce<<<(n3 / 2 + 255) / 256, 256, 0, st>>>(pl.S, T, n3, pl.acc);
         tm_end(pl, st, TK_REDUCE);
         nl += 4;
     }
@@ -507,7 +549,7 @@ bz_status run_noalloc(const Plan &pl, const void *fhat, void *Qhat, int dtype, u
         k_plane_inv<N><<<dim3(N / PPC, Tc), Cfg<N>::THREADS, Cfg<N>::SMEM, st>>>(fin, pl.tw, S, c0, 1);
         k_pencil<N, 1><<<dim3((N * N + 127) / 128, Tc), 128, 0, st>>>(S, h, nullptr);
         k_plane_fwd<N><<<dim3(N / PPC, Tc), Cfg<N>::THREADS, Cfg<N>::SMEM, st>>>(S, pl.alpha, c0);
-        k_reduce<<<(n3 + 255) / 256, 256, 0, st>>>(S, Tc, n3, acc);
+        k_reduce<<<(n3 / 2 + 255) / 256, 256, 0, st>>>(S, Tc, n3, acc);
     }
     if (dtype == BZ_C128) {
         BZ_CUDA_TRY(cudaMemcpyAsync(Qhat, acc, (size_t)n3 * sizeof(double2), cudaMemcpyDeviceToDevice, st));
