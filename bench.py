@@ -34,10 +34,10 @@ WORKLOADS = {
     "single_n16": dict(N=16, N_rho=16, M=12, gamma=0.0, s=0.5, R=None, L=10.0, dt=None,
                        data="c1", desc="single collide, N=16, N_rho=16, M=12, gamma=0, s=0.5, "
                                        "L=10, two Maxwellians at +-2 e1"),
-    "serve": dict(N=None, N_rho=None, M=None, gamma=None, s=None, R=None, L=10.0, dt=0.02,
-                  data="mixtures", desc="continuous-batching server: 64 requests, Poisson arrivals at 200/s, "
-                  "N in {16,24,32}, N_rho=N, M in {12,32}, gamma in {0,-1,-2}, s in {0.25,0.5}, RK4 to "
-                  "t=0.2 (dt=0.02, 10 steps), two-Maxwellian data; plans warmed before the trace; 32 terms per work item"),
+    "serve": dict(N=None, N_rho=None, M=None, gamma=None, s=None, R=None, L=10.0, dt=0.02, t_end=2.0,
+                  data="mixtures", desc="continuous-batching server: %d requests, Poisson arrivals at 200/s, "
+                  "N in {16,24,32,48,64}, N_rho=N, M in {12,32}, gamma in {0,-1,-2}, s in {0.25,0.5}, RK4 to "
+                  "t=2 (dt=0.02, 100 steps), seeded two-Maxwellian data; plans warmed before the trace"),
     "single_2d_n64": dict(N=64, N_rho=64, M=32, gamma=0.0, s=0.0, R=6.0, dt=None, data="bkw2d", dim=2,
                           kernel=6, desc="single 2D collide in the Table 1 setting: N=64, N_rho=64, M=32 circle "
                                          "points, kernel b4, R=6, L=(3+sqrt2)R/4, BKW samples at t=0"),
@@ -139,6 +139,14 @@ def _profiled_traffic(key):
     if vals.get("kernel_sources_sha256_16") != _sources_hash(files):
         return None
     return float(vals["traffic_bytes_per_launch"])
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
 def _alu_peak(peaks):
@@ -1052,8 +1060,20 @@ def run_inhom(args, w):
     return 0
 
 
+def _serve_trace(n_req, seed=77):
+    """The serving workload's requests: N from {16, 24, 32, 48, 64}, N_rho = N, M from {12, 32},
+    gamma from {0, -1, -2}, s from {0.25, 0.5}, seeded two-Maxwellian initial data."""
+    import bz_inputs as bi
+    u = bi.SplitMix64(seed).uniform(4 * n_req)
+    Ns, Ms, gs, ss = [16, 24, 32, 48, 64], [12, 32], [0.0, -1.0, -2.0], [0.25, 0.5]
+    return [dict(N=Ns[int(u[4 * i] * 5)], M=Ms[int(u[4 * i + 1] * 2)], gamma=gs[int(u[4 * i + 2] * 3)],
+                 s=ss[int(u[4 * i + 3] * 2)], seed=1000 + i) for i in range(n_req)]
+
+
 def run_serve(args, w):
-    """Seeded Poisson trace through bz_submit / bz_poll; latency percentiles and throughput."""
+    """A seeded Poisson trace through bz_submit / bz_poll: latency percentiles and throughput, for
+    the FP32 server (real-data form where M is even) and the mixed-precision one (split-BF16 at
+    N = 32, complex data; FP32 elsewhere).  Plans are warmed before each trace."""
     import numpy as np
     import torch
     import bz_inputs as bi
@@ -1061,19 +1081,21 @@ def run_serve(args, w):
     torch.cuda.set_device(0)
     L = w["L"]
     R = bi.R_from_L(L)
-    n_req, rate = 64, 200.0
-    u = bi.SplitMix64(77).uniform(4 * n_req)
-    arrivals = bi.poisson_arrivals(n_req, rate, seed=78)
-    Ns, Ms, gs, ss = [16, 24, 32], [12, 32], [0.0, -1.0, -2.0], [0.25, 0.5]
-    reqs = []
-    for i in range(n_req):
-        N = Ns[int(u[4 * i] * 3)]
-        reqs.append(dict(N=N, M=Ms[int(u[4 * i + 1] * 2)], gamma=gs[int(u[4 * i + 2] * 3)],
-                         s=ss[int(u[4 * i + 3] * 2)], f=bi.random_mixture(N, L, seed=1000 + i)))
+    n_req, rate = args.serve_requests, 200.0
+    trace = _serve_trace(n_req)
+    f0 = {r["seed"]: bi.random_mixture(r["N"], L, seed=r["seed"]) for r in trace}
+    t_end = w["t_end"]
     server = bz.bz_server_create(200 << 30, max_batch=32, terms_per_item=32)
 
-    def submit(r, t_end):
-        return bz.bz_submit(server, r["f"], r["N"], L, R, r["gamma"], r["s"], r["N"], r["M"], 0.0, t_end, w["dt"])
+    def form(r, mixed):
+        if mixed and r["N"] == 32:
+            return bz.BZ_DATA_COMPLEX, bz.BZ_PREC_BF16X3
+        return bz.BZ_DATA_REAL, bz.BZ_PREC_FP32          # M in {12, 32}: the real-data form applies
+
+    def submit(r, t_end_, mixed):
+        data, prec = form(r, mixed)
+        return bz.bz_submit(server, f0[r["seed"]], r["N"], L, R, r["gamma"], r["s"], r["N"], r["M"], 0.0, t_end_,
+                            w["dt"], data=data, precision=prec)
 
     def wait(tickets):
         out = {}
@@ -1086,40 +1108,54 @@ def run_serve(args, w):
             time.sleep(0.0005)
         return out
 
-    # warm every (N, M, s) group once: plan tables, batches, graphs
-    keys = {}
-    for r in reqs:
-        keys.setdefault((r["N"], r["M"], r["s"]), r)
-    wait([(submit(r, w["dt"]), r["N"]) for r in keys.values()])
-    rates = [rate] if args.rates is None else [float(x) for x in args.rates.split(",")]
-    sweep = []
-    for rt in rates:
-        arr = bi.poisson_arrivals(n_req, rt, seed=78)
+    def key(r, mixed):
+        data, prec = form(r, mixed)
+        batched = r["N"] <= 32 and (data == bz.BZ_DATA_COMPLEX or 32 % r["N"] == 0)
+        return (r["N"], r["M"], r["s"], data, prec, None if batched else r["gamma"])
+
+    passes = []
+    for mixed in (False, True):
+        keys = {}
+        for r in trace:
+            keys.setdefault(key(r, mixed), r)
+        tw = time.perf_counter()
+        wait([(submit(r, w["dt"], mixed), r["N"]) for r in keys.values()])     # plans, batches, graphs
+        warm_s = time.perf_counter() - tw
+        arr = bi.poisson_arrivals(n_req, rate, seed=78)
         t0 = time.perf_counter()
         tickets = []
         with ClockSampler(0) as clk:
-            for r, ta in zip(reqs, arr):
+            for r, ta in zip(trace, arr):
                 delay = t0 + ta - time.perf_counter()
                 if delay > 0:
                     time.sleep(delay)
-                tickets.append((submit(r, 0.2), r["N"]))
+                tickets.append((submit(r, t_end, mixed), r["N"]))
             res = wait(tickets)
         wall = time.perf_counter() - t0
         lat = np.array([res[t][0].latency_s for t, _ in tickets])
         que = np.array([res[t][0].queue_s for t, _ in tickets])
-        sweep.append({"rate": rt, "requests_per_s": n_req / wall, "wall_s": wall,
-                      "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99)),
-                      "queue_p50_s": float(np.percentile(que, 50)), "queue_p99_s": float(np.percentile(que, 99)),
-                      "all_ok": all(res[t][0].status == 0 for t, _ in tickets), "clocks": clk.summary()})
+        steps = sum(res[t][0].steps for t, _ in tickets)
+        by_n = {}
+        for (t, N) in tickets:
+            by_n.setdefault(N, []).append(res[t][0].latency_s)
+        passes.append({"precision": "bf16x3 at N=32, fp32 elsewhere" if mixed else "fp32",
+                       "requests_per_s": n_req / wall, "q_evals_per_s": 4 * steps / wall, "wall_s": wall,
+                       "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99)),
+                       "queue_p50_s": float(np.percentile(que, 50)), "queue_p99_s": float(np.percentile(que, 99)),
+                       "latency_p50_by_N_s": {str(k): float(np.percentile(v, 50)) for k, v in sorted(by_n.items())},
+                       "all_ok": all(res[t][0].status == 0 for t, _ in tickets), "plans": len(keys),
+                       "warm_s": warm_s, "clocks": clk.summary()})
+        if args.no_mixed:
+            break
     server.close()
-    head = sweep[-1]
+    head = passes[0]
     line = {"metric": "served requests/s", "value": head["requests_per_s"], "unit": "requests/s", "n_gpus": 1,
-            "steps": n_req, "warmup": len(keys), "ms_per_step": 1e3 * head["wall_s"] / n_req,
+            "steps": n_req, "warmup": head["plans"], "ms_per_step": 1e3 * head["wall_s"] / n_req,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": args.workload, "desc": w["desc"], "groups": len(keys), "rate": head["rate"]},
+            "config": {"workload": args.workload, "desc": w["desc"] % n_req, "rate": rate},
             "latency_s": {"p50": head["latency_p50_s"], "p99": head["latency_p99_s"]},
             "queue_s": {"p50": head["queue_p50_s"], "p99": head["queue_p99_s"]},
-            "q_evals_per_s": 4 * 10 * n_req / head["wall_s"], "sweep": sweep}
+            "q_evals_per_s": head["q_evals_per_s"], "passes": passes}
     print(json.dumps(line))
     return 0
 
@@ -1136,7 +1172,7 @@ def main():
                     help="skip the N = 64 single-collide block measured beside the default workload")
     ap.add_argument("--no-mixed", action="store_true",
                     help="skip the split-BF16 tensor-core form (measured beside the FP32 form at N = 32)")
-    ap.add_argument("--rates", default=None, help="serve workload: comma-separated arrival rates (req/s)")
+    ap.add_argument("--serve-requests", type=int, default=256, help="serve workload: requests in the trace")
     ap.add_argument("--data", default="auto", choices=["auto", "real", "complex"],
                     help="data form of the headline plan: auto = real where the plan supports it "
                          "(3D, N in {8, 16, 32}, M even; the workloads' f are real), else complex")

@@ -278,6 +278,33 @@ const char *bz_status_str(bz_status s);
 bz_status bz_collide_noalloc(const bz_plan *plan, const void *fhat, void *Qhat, int dtype,
                              void *stream);
 
+/* Non-finite results.  Every kernel that writes a result to the caller (the Qhat of bz_collide,
+ * bz_collide_terms and batches, the fhat of bz_step_rk and batch RK steps) raises a device flag
+ * of the plan when a value it writes is NaN or Inf.  This call waits for the device, returns
+ * BZ_ERR_NONFINITE (and *nonfinite = 1) if the flag was raised since the last check, clears it,
+ * and returns BZ_OK (*nonfinite = 0) otherwise; nonfinite may be NULL.  bz_moments returns
+ * BZ_ERR_NONFINITE itself when a moment is NaN or Inf.  No counterpart in the paper. */
+bz_status bz_plan_check_finite(bz_plan *plan, int *nonfinite);
+
+/* Checkpoint and resume of an RK4 solve (Sec. 5.2).  The state between bz_step_rk calls is the
+ * coefficient array and t.  bz_checkpoint_write waits for `stream`, copies fhat (device, dtype)
+ * to the host and writes it as complex128 to `path` (through a temporary file renamed over it),
+ * with t, every parameter of the plan's operator and its pipeline choices (pipeline, CTAs per
+ * cluster, pair kernel, terms per chunk).  bz_checkpoint_plan_desc fills *desc (sphere_xyz and
+ * sphere_w NULL: a plan built on a user sphere rule needs the same arrays again) and *t (may be
+ * NULL) from the file, so that bz_plan_create_ex rebuilds a plan that makes the same choices.
+ * bz_checkpoint_read checks that the file's operator equals the plan's (BZ_ERR_ARG otherwise),
+ * writes the coefficients to fhat (device, dtype) and *t (may be NULL), and waits for `stream`.
+ * With BZ_C128 state, steps taken after a resume on such a plan give the same bits as an
+ * uninterrupted run (the RK state is FP64 and every sum has a fixed order); BZ_C64 state is
+ * rounded to FP32 at every call boundary.  Errors: BZ_ERR_ARG for NULL arguments, a bad dtype,
+ * a file that cannot be written or read or is not a checkpoint; BZ_ERR_CUDA.  No counterpart in
+ * the paper. */
+bz_status bz_checkpoint_write(const bz_plan *plan, const void *fhat, int dtype, double t, const char *path,
+                              void *stream);
+bz_status bz_checkpoint_plan_desc(const char *path, bz_plan_desc *desc, double *t);
+bz_status bz_checkpoint_read(const bz_plan *plan, const char *path, void *fhat, int dtype, double *t, void *stream);
+
 /* ---------------------------------------------------------------------------------------
  * Batches: many independent instances of one plan geometry (same N, L, R, kernel, N_rho, M
  * and F table; gamma per instance), standing in for the cells of a spatially
@@ -331,12 +358,15 @@ bz_status bz_inhom_step(bz_batch *batch, int nx, double Lx, void *fcells, int dt
 
 /* ---------------------------------------------------------------------------------------
  * Serving: a worker thread runs homogeneous relaxation solves (RK4 on d fhat/dt = Q) for
- * submitted requests with continuous batching.  Each iteration admits queued requests in
- * arrival order while the HBM budget and group slots allow, advances every active request
- * by one RK4 step (requests with equal geometry and dt share one batched call, N <= 32;
- * larger N step through their own plan; each group on its own stream), and retires the
- * finished ones.  State stays on the device from admission to completion.  A request's
- * result does not depend on the other requests in flight.
+ * submitted requests with continuous batching.  Requests with equal geometry, data form,
+ * precision and dt form a group with its own plan, stream and completion event; groups on the
+ * fused pipeline (N <= 32; N | 32 for BZ_DATA_REAL) step all their requests with one batched
+ * call, the others step each request through the group's plan.  The worker admits queued
+ * requests in arrival order while the HBM budget and group slots allow; a group whose step has
+ * completed (polled with cudaEventQuery: no group waits for another) advances its requests by
+ * one RK4 step, retires the finished ones and launches its next step, which requests admitted
+ * meanwhile join.  State stays on the device from admission to completion.  A request's result
+ * does not depend on the other requests in flight.
  * --------------------------------------------------------------------------------------- */
 typedef struct bz_server bz_server;
 
@@ -345,10 +375,14 @@ typedef struct {
     const void *fhat0; int dtype;   /* host array of N^3 initial coefficients; copied by bz_submit */
     double t0, t_end, dt;           /* round((t_end - t0) / dt) RK4 steps of size dt              */
     double max_queue_s;             /* > 0: fail with BZ_ERR_TIMEOUT if not admitted in time      */
+    int data;                       /* BZ_DATA_COMPLEX (0) or BZ_DATA_REAL (M even)               */
+    int precision;                  /* BZ_PREC_FP32 (0) or BZ_PREC_BF16X3 (N = 32, complex data)  */
 } bz_request;
 
 typedef struct {
-    int status;          /* BZ_OK, or the error that ended the request                       */
+    int status;          /* BZ_OK, or the error that ended the request (BZ_ERR_NONFINITE: the
+                            result held NaN or Inf; BZ_ERR_TIMEOUT: not admitted within
+                            max_queue_s; BZ_ERR_OOM: larger than the whole budget)               */
     int steps;           /* RK4 steps taken                                                   */
     double t;            /* t0 + steps * dt                                                   */
     double latency_s;    /* submit to completion                                              */
@@ -358,12 +392,16 @@ typedef struct {
 /* hbm_budget_bytes bounds the device memory of plans, batches and request state; max_batch
  * is the slot capacity of each batched group; terms_per_item <= 0 autotunes per group. */
 bz_status bz_server_create(bz_server **out, size_t hbm_budget_bytes, int max_batch, int terms_per_item);
-/* Queues a request (never blocks on the device).  *ticket identifies it for bz_poll. */
+/* Queues a request (never blocks on the device).  *ticket identifies it for bz_poll.
+ * Errors: BZ_ERR_ARG for an invalid request; BZ_ERR_UNSUPPORTED for BZ_DATA_REAL with M odd or
+ * BZ_PREC_BF16X3 other than at N = 32 with complex data. */
 bz_status bz_submit(bz_server *server, const bz_request *req, uint64_t *ticket);
 /* Non-blocking.  BZ_ERR_BUSY while queued or running; otherwise fills *out, copies the
  * final coefficients to fhat_out (host, dtype; may be NULL) when out->status == BZ_OK,
  * forgets the ticket and returns BZ_OK.  BZ_ERR_ARG for an unknown ticket. */
 bz_status bz_poll(bz_server *server, uint64_t ticket, bz_result *out, void *fhat_out, int dtype);
+/* completed: requests retired; steps: RK4 steps completed, summed over requests; hbm_used:
+ * bytes charged to the budget; queued / active: requests waiting / admitted.  Any may be NULL. */
 bz_status bz_server_stats(bz_server *server, long *completed, long *steps, size_t *hbm_used, int *queued,
                           int *active);
 /* Stops the worker after its current iteration and frees everything. */
@@ -392,6 +430,14 @@ int bz_plan_last_launches(const bz_plan *plan);
  * results of that launch are invalid), else 0.  Waits for the device.  No counterpart in
  * the paper. */
 bz_status bz_plan_device_errors(bz_plan *plan, int *count);
+
+/* Exercises that path without a fault: one kernel on `stream` waits, through the same bounded
+ * wait as the tensor-core kernels, on a shared-memory barrier that nothing completes, for at
+ * most `cycles` SM clocks (1 .. 2^31); it then gives up, raises the plan's wait flag (which
+ * bz_plan_device_errors reports from then on) and returns, with nothing left in flight.
+ * Errors: BZ_ERR_ARG for a NULL plan or cycles outside the range; BZ_ERR_CUDA.  No counterpart
+ * in the paper. */
+bz_status bz_plan_wait_selftest(bz_plan *plan, long long cycles, void *stream);
 
 #ifdef __cplusplus
 }

@@ -21,7 +21,9 @@ __all__ = [
     "bz_collide", "bz_collide_terms", "bz_step_rk", "bz_moments", "bz_ftable_entries",
     "bz_plan_alpha", "bz_plan_last_launches", "bz_plan_device_errors", "bz_status_str", "library_path", "lib",
     "bz_plan_set_timing", "bz_plan_timing", "bz_collide_noalloc", "bz_plan_pipeline",
-    "bz_quadrature", "bz_kernel_constants", "bz_partition_terms",
+    "bz_quadrature", "bz_kernel_constants", "bz_partition_terms", "bz_plan_check_finite",
+    "bz_plan_wait_selftest", "bz_checkpoint_write", "bz_checkpoint_plan_desc", "bz_checkpoint_read",
+    "bz_plan_create_from_desc",
     "bz_batch_create", "bz_batch_destroy", "bz_batch_set_gamma", "bz_batch_collide", "bz_batch_step_rk",
     "bz_batch_last_launches", "bz_server_create", "bz_submit", "bz_poll", "bz_server_stats",
     "bz_transport_x", "bz_inhom_step", "bz_plan_kernel",
@@ -48,7 +50,8 @@ class bz_request(ctypes.Structure):
                 ("gamma", ctypes.c_double), ("s", ctypes.c_double), ("N_rho", ctypes.c_int),
                 ("M", ctypes.c_int), ("kernel", ctypes.c_int), ("fhat0", ctypes.c_void_p),
                 ("dtype", ctypes.c_int), ("t0", ctypes.c_double), ("t_end", ctypes.c_double),
-                ("dt", ctypes.c_double), ("max_queue_s", ctypes.c_double)]
+                ("dt", ctypes.c_double), ("max_queue_s", ctypes.c_double), ("data", ctypes.c_int),
+                ("precision", ctypes.c_int)]
 
 
 class bz_result(ctypes.Structure):
@@ -92,6 +95,11 @@ def _load():
         "bz_quadrature": [c_int, c_double, c_int, c_double, dp, dp, dp, dp, dp],
         "bz_kernel_constants": [c_int, c_double, c_double, dp, dp],
         "bz_partition_terms": [c_int, c_int, c_int, c_int, ip, ip],
+        "bz_plan_check_finite": [vp, ip],
+        "bz_plan_wait_selftest": [vp, ctypes.c_longlong, vp],
+        "bz_checkpoint_write": [vp, vp, c_int, c_double, ctypes.c_char_p, vp],
+        "bz_checkpoint_plan_desc": [ctypes.c_char_p, ctypes.POINTER(bz_plan_desc), dp],
+        "bz_checkpoint_read": [vp, ctypes.c_char_p, vp, c_int, dp, vp],
         "bz_collide": [vp, vp, vp, c_int, vp],
         "bz_collide_terms": [vp, c_int, c_int, vp, vp, c_int, vp],
         "bz_step_rk": [vp, vp, c_int, dp, c_double, c_int, vp, vp],
@@ -363,6 +371,47 @@ def bz_plan_device_errors(plan: Plan) -> int:
     return c.value
 
 
+def bz_plan_check_finite(plan: Plan) -> int:
+    """1 if a result written since the last check held NaN or Inf (the flag is cleared), else 0."""
+    c = ctypes.c_int()
+    code = lib.bz_plan_check_finite(plan.handle, ctypes.byref(c))
+    if code not in (0, 5):
+        _check(code, "bz_plan_check_finite")
+    return c.value
+
+
+def bz_plan_wait_selftest(plan: Plan, cycles: int, stream=None):
+    _check(lib.bz_plan_wait_selftest(plan.handle, int(cycles), _stream(stream)), "bz_plan_wait_selftest")
+
+
+def bz_checkpoint_write(plan: Plan, fhat, t: float, path: str, stream=None):
+    _check(lib.bz_checkpoint_write(plan.handle, _dev(fhat, plan.n3), _dtype(fhat), float(t), path.encode(),
+                                   _stream(stream)), "bz_checkpoint_write")
+
+
+def bz_checkpoint_plan_desc(path: str):
+    """(bz_plan_desc, t) recorded in a checkpoint file."""
+    d = bz_plan_desc()
+    t = ctypes.c_double()
+    _check(lib.bz_checkpoint_plan_desc(path.encode(), ctypes.byref(d), ctypes.byref(t)), "bz_checkpoint_plan_desc")
+    return d, t.value
+
+
+def bz_plan_create_from_desc(d: bz_plan_desc) -> Plan:
+    """A plan from a filled bz_plan_desc (for example from bz_checkpoint_plan_desc)."""
+    h = ctypes.c_void_p()
+    _check(lib.bz_plan_create_ex(ctypes.byref(h), ctypes.byref(d)), "bz_plan_create_ex")
+    return Plan(h, d.N, d.L, d.dim if d.dim else 3, d.data)
+
+
+def bz_checkpoint_read(plan: Plan, path: str, fhat, stream=None) -> float:
+    """Loads the checkpoint's coefficients into fhat (device tensor); returns its t."""
+    t = ctypes.c_double()
+    _check(lib.bz_checkpoint_read(plan.handle, path.encode(), _dev(fhat, plan.n3), _dtype(fhat), ctypes.byref(t),
+                                  _stream(stream)), "bz_checkpoint_read")
+    return t.value
+
+
 BZ_K_PLANE_INV, BZ_K_PENCIL, BZ_K_PLANE_FWD, BZ_K_REDUCE, BZ_K_OTHER = range(5)
 KERNEL_KINDS = {"plane_inv": 0, "pencil": 1, "plane_fwd": 2, "reduce": 3, "other": 4, "fused": 5}
 
@@ -490,14 +539,16 @@ def bz_server_create(hbm_budget_bytes: int, max_batch: int = 64, terms_per_item:
 
 
 def bz_submit(server: Server, fhat0, N: int, L: float, R: float, gamma: float, s: float, N_rho: int, M: int,
-              t0: float, t_end: float, dt: float, kernel: int = BZ_KERNEL_FAMILY, max_queue_s: float = 0.0) -> int:
+              t0: float, t_end: float, dt: float, kernel: int = BZ_KERNEL_FAMILY, max_queue_s: float = 0.0,
+              data: int = BZ_DATA_COMPLEX, precision: int = BZ_PREC_FP32) -> int:
     """fhat0: host numpy array of N^3 complex128 (or complex64) coefficients; returns the ticket."""
     import numpy as np
     a = np.ascontiguousarray(fhat0)
     dt_code = BZ_C128 if a.dtype == np.complex128 else BZ_C64
     if a.dtype not in (np.complex128, np.complex64) or a.size != N ** 3:
         raise ValueError("fhat0 must hold N^3 complex64/complex128 values")
-    r = bz_request(N, L, R, gamma, s, N_rho, M, kernel, a.ctypes.data, dt_code, t0, t_end, dt, max_queue_s)
+    r = bz_request(N, L, R, gamma, s, N_rho, M, kernel, a.ctypes.data, dt_code, t0, t_end, dt, max_queue_s,
+                   data, precision)
     t = ctypes.c_uint64()
     _check(lib.bz_submit(server.handle, ctypes.byref(r), ctypes.byref(t)), "bz_submit")
     return t.value

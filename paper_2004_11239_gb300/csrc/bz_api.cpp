@@ -193,7 +193,7 @@ bz_status create(bz_plan **out, const bz_plan_desc *d) {
         (s = dmalloc(&pl.acc, n3 * sizeof(double2))) != BZ_OK ||
         (s = dmalloc(&pl.rk, 2 * n3 * sizeof(double2))) != BZ_OK ||
         (s = dmalloc(&pl.mom, 8 * sizeof(double))) != BZ_OK ||
-        (s = dmalloc(&pl.dev_err, sizeof(int))) != BZ_OK) {
+        (s = dmalloc(&pl.dev_err, 2 * sizeof(int))) != BZ_OK) {
         free_plan(pl);
         delete h;
         return s;
@@ -201,7 +201,7 @@ bz_status create(bz_plan **out, const bz_plan_desc *d) {
     pl.ws_bytes = (size_t)chunk * field + 2 * field + 3 * n3 * sizeof(double2);
     std::vector<float2> tw = make_twiddles(pl);
     if (cudaMemcpy(pl.tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemset(pl.dev_err, 0, sizeof(int)) != cudaSuccess ||
+        cudaMemset(pl.dev_err, 0, 2 * sizeof(int)) != cudaSuccess ||
         (pl.precision == BZ_PREC_BF16X3 && bz::mixed_upload(&pl.wimg) != BZ_OK) ||
         (dim == 3 && bz::collide_set_attributes(N) != cudaSuccess)) {
         free_plan(pl);
@@ -391,6 +391,20 @@ bz_status bz_plan_device_errors(bz_plan *plan, int *count) {
     if (cudaMemcpy(&v, plan->p.dev_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return BZ_ERR_CUDA;
     *count = v != 0;
     return BZ_OK;
+}
+
+bz_status bz_plan_wait_selftest(bz_plan *plan, long long cycles, void *stream) {
+    if (!plan || cycles < 1 || cycles > (1LL << 31)) return BZ_ERR_ARG;
+    return bz::wait_selftest(plan->p, cycles, (cudaStream_t)stream);
+}
+
+bz_status bz_plan_check_finite(bz_plan *plan, int *nonfinite) {
+    if (!plan) return BZ_ERR_ARG;
+    int v = 0;
+    if (cudaMemcpy(&v, plan->p.dev_err + 1, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return BZ_ERR_CUDA;
+    if (v && cudaMemset(plan->p.dev_err + 1, 0, sizeof(int)) != cudaSuccess) return BZ_ERR_CUDA;
+    if (nonfinite) *nonfinite = v != 0;
+    return v ? BZ_ERR_NONFINITE : BZ_OK;
 }
 
 bz_status bz_partition_terms(int P, int data, int world, int rank, int *p0, int *p1) {

@@ -82,15 +82,21 @@ __device__ __forceinline__ double2 sum_blocks(const float2 *part, int slot, int 
 }
 
 __global__ void k_batch_out(const float2 *part, int nblk, const int *slots, const int *count_dev, int n3,
-                            void *Qhat, int dtype) {
+                            void *Qhat, int dtype, int *flag) {
     const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int b = (int)(e / n3), k = (int)(e % n3);
     if (b >= *count_dev) return;
     const int slot = slots[b];
     double2 q = sum_blocks(part, slot, nblk, n3, k);
     const size_t idx = (size_t)slot * n3 + k;
-    if (dtype == BZ_C128) ((double2 *)Qhat)[idx] = q;
-    else ((float2 *)Qhat)[idx] = make_float2((float)q.x, (float)q.y);
+    if (dtype == BZ_C128) {
+        ((double2 *)Qhat)[idx] = q;
+        note_finite(q, flag);
+    } else {
+        const float2 w = make_float2((float)q.x, (float)q.y);
+        ((float2 *)Qhat)[idx] = w;
+        note_finite(w, flag);
+    }
 }
 
 __global__ void k_batch_rk_init(const void *fhat, int dtype, const int *slots, const int *count_dev, int n3,
@@ -168,7 +174,7 @@ __device__ __forceinline__ bool real_q(const float2 *part, const float2 *part_s,
 }
 
 __global__ void k_batch_out_real(const float2 *part, const float2 *part_s, int nblk, const int *slots,
-                                 const int *count_dev, int N, void *Qhat, int dtype) {
+                                 const int *count_dev, int N, void *Qhat, int dtype, int *flag) {
     const int n3 = N * N * N;
     const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int b = (int)(e / n3), k = (int)(e % n3);
@@ -179,8 +185,14 @@ __global__ void k_batch_out_real(const float2 *part, const float2 *part_s, int n
     if (!real_q(part, part_s, slot, nblk, N, k, qk, qm, mm)) return;
     const size_t base = (size_t)slot * n3;
     auto put = [&](size_t i, double2 q) {
-        if (dtype == BZ_C128) ((double2 *)Qhat)[base + i] = q;
-        else ((float2 *)Qhat)[base + i] = make_float2((float)q.x, (float)q.y);
+        if (dtype == BZ_C128) {
+            ((double2 *)Qhat)[base + i] = q;
+            note_finite(q, flag);
+        } else {
+            const float2 w = make_float2((float)q.x, (float)q.y);
+            ((float2 *)Qhat)[base + i] = w;
+            note_finite(w, flag);
+        }
     };
     put((size_t)k, qk);
     if (mm >= 0) put((size_t)mm, qm);
@@ -225,13 +237,19 @@ __global__ void k_batch_rk_stage_real(const float2 *part, const float2 *part_s, 
 }
 
 __global__ void k_batch_rk_out(const double2 *f0, const int *slots, const int *count_dev, int n3, void *fhat,
-                               int dtype) {
+                               int dtype, int *flag) {
     const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int b = (int)(e / n3), k = (int)(e % n3);
     if (b >= *count_dev) return;
     const size_t idx = (size_t)slots[b] * n3 + k;
-    if (dtype == BZ_C128) ((double2 *)fhat)[idx] = f0[idx];
-    else ((float2 *)fhat)[idx] = make_float2((float)f0[idx].x, (float)f0[idx].y);
+    if (dtype == BZ_C128) {
+        ((double2 *)fhat)[idx] = f0[idx];
+        note_finite(f0[idx], flag);
+    } else {
+        const float2 w = make_float2((float)f0[idx].x, (float)f0[idx].y);
+        ((float2 *)fhat)[idx] = w;
+        note_finite(w, flag);
+    }
 }
 
 ItemArgs item_args(const bz_batch &B) {
@@ -435,9 +453,10 @@ bz_status bz_batch_collide(bz_batch *batch, int count, const int *slots, const v
     if (s != BZ_OK) return s;
     if (B.pl->real)
         k_batch_out_real<<<grid_for(B), 256, 0, st>>>(B.part, B.part_s, B.nblk, B.slots_dev, B.count_dev, B.pl->N,
-                                                     Qhat, dtype);
+                                                     Qhat, dtype, nonfinite_flag(*B.pl));
     else
-        k_batch_out<<<grid_for(B), 256, 0, st>>>(B.part, B.nblk, B.slots_dev, B.count_dev, n3, Qhat, dtype);
+        k_batch_out<<<grid_for(B), 256, 0, st>>>(B.part, B.nblk, B.slots_dev, B.count_dev, n3, Qhat, dtype,
+                                                nonfinite_flag(*B.pl));
     BZ_CUDA_TRY(cudaGetLastError());
     B.last_launches = (B.pl->real ? 2 : 3) + (B.pl->h_fp64 ? h64_launches(B.pl->N) : 0);
     return BZ_OK;
@@ -485,7 +504,7 @@ bz_status bz_batch_step_rk(bz_batch *batch, int count, const int *slots, void *f
     }
     k_batch_rk_init<<<grid_for(B), 256, 0, st>>>(fhat, dtype, B.slots_dev, B.count_dev, n3, B.f0, B.fin, B.fin64);
     for (int step = 0; step < nsteps; ++step) BZ_CUDA_TRY(cudaGraphLaunch(it->second, st));
-    k_batch_rk_out<<<grid_for(B), 256, 0, st>>>(B.f0, B.slots_dev, B.count_dev, n3, fhat, dtype);
+    k_batch_rk_out<<<grid_for(B), 256, 0, st>>>(B.f0, B.slots_dev, B.count_dev, n3, fhat, dtype, nonfinite_flag(*B.pl));
     BZ_CUDA_TRY(cudaGetLastError());
     B.last_launches = 2 + 4 * (2 + (B.pl->h_fp64 ? h64_launches(B.pl->N) : 0)) * nsteps;
     return BZ_OK;

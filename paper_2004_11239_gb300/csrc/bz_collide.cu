@@ -230,6 +230,21 @@ __global__ void k_acc_to_c64(const double2 *__restrict__ in, float2 *__restrict_
     if (i < n) out[i] = make_float2((float)in[i].x, (float)in[i].y);
 }
 
+// The plan's result to the caller's array in its dtype, raising the non-finite flag.
+__global__ void k_acc_out(const double2 *__restrict__ in, void *__restrict__ out, int dtype, int n, int *flag) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double2 v = in[i];
+    if (dtype == BZ_C128) {
+        ((double2 *)out)[i] = v;
+        note_finite(v, flag);
+    } else {
+        const float2 w = make_float2((float)v.x, (float)v.y);
+        ((float2 *)out)[i] = w;
+        note_finite(w, flag);
+    }
+}
+
 // Padded plans (BZ_CONV_PADDED): the caller's Nin-grid lives inside the N = 2 Nin grid at the
 // same signed modes.  Embed: one thread per N-grid mode, zero outside the caller's range.
 __global__ void k_embed(const void *__restrict__ f, int dtype, int Nin, int N, float2 *__restrict__ out,
@@ -256,7 +271,8 @@ __global__ void k_embed(const void *__restrict__ f, int dtype, int Nin, int N, f
 }
 
 // Extract: one thread per caller mode, from the FP64 accumulator of the N grid.
-__global__ void k_extract(const double2 *__restrict__ acc, int Nin, int N, void *__restrict__ Q, int dtype) {
+__global__ void k_extract(const double2 *__restrict__ acc, int Nin, int N, void *__restrict__ Q, int dtype,
+                          int *flag) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= Nin * Nin * Nin) return;
     int s[3] = {i / (Nin * Nin), (i / Nin) % Nin, i % Nin};
@@ -267,8 +283,14 @@ __global__ void k_extract(const double2 *__restrict__ acc, int Nin, int N, void 
         src = src * N + (size_t)((k + N) % N);
     }
     const double2 v = acc[src];
-    if (dtype == BZ_C128) ((double2 *)Q)[i] = v;
-    else ((float2 *)Q)[i] = make_float2((float)v.x, (float)v.y);
+    if (dtype == BZ_C128) {
+        ((double2 *)Q)[i] = v;
+        note_finite(v, flag);
+    } else {
+        const float2 w = make_float2((float)v.x, (float)v.y);
+        ((float2 *)Q)[i] = w;
+        note_finite(w, flag);
+    }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -464,20 +486,15 @@ bz_status write_output(Plan &pl, void *Qhat, int dtype, cudaStream_t st, int *la
     if (pl.Nin) {
         if (dtype != BZ_C64 && dtype != BZ_C128) return BZ_ERR_ARG;
         const int m3 = pl.Nin * pl.Nin * pl.Nin;
-        k_extract<<<(m3 + 255) / 256, 256, 0, st>>>(pl.acc, pl.Nin, pl.N, Qhat, dtype);
+        k_extract<<<(m3 + 255) / 256, 256, 0, st>>>(pl.acc, pl.Nin, pl.N, Qhat, dtype, nonfinite_flag(pl));
         BZ_CUDA_TRY(cudaGetLastError());
         if (launches) *launches += 1;
         return BZ_OK;
     }
-    if (dtype == BZ_C128) {
-        BZ_CUDA_TRY(cudaMemcpyAsync(Qhat, pl.acc, (size_t)n3 * sizeof(double2), cudaMemcpyDeviceToDevice, st));
-    } else if (dtype == BZ_C64) {
-        k_acc_to_c64<<<(n3 + 255) / 256, 256, 0, st>>>(pl.acc, (float2 *)Qhat, n3);
-        BZ_CUDA_TRY(cudaGetLastError());
-        if (launches) *launches += 1;
-    } else {
-        return BZ_ERR_ARG;
-    }
+    if (dtype != BZ_C64 && dtype != BZ_C128) return BZ_ERR_ARG;
+    k_acc_out<<<(n3 + 255) / 256, 256, 0, st>>>(pl.acc, Qhat, dtype, n3, nonfinite_flag(pl));
+    BZ_CUDA_TRY(cudaGetLastError());
+    if (launches) *launches += 1;
     return BZ_OK;
 }
 

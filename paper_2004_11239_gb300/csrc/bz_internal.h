@@ -82,11 +82,23 @@ struct Plan {
     double2 *acc_s = nullptr;       // chunked pipeline: [3][N][N] FP64 sum of X
     float2 *fsym = nullptr;         // [N^3] Hermitian part of fhat, Nyquist planes zero (FP32)
     double2 *fsym64 = nullptr;      // [N^3] the same in FP64 (source of h)
-    int *dev_err = nullptr;         // device flag: a bounded wait of the fused kernel gave up
+    int *dev_err = nullptr;         // device flags: [0] a bounded wait of a kernel gave up,
+                                    // [1] a result written since the last check held NaN or Inf
     size_t ws_bytes = 0;
     int last_launches = 0;
     Timing tm;
 };
+
+// Raises the non-finite flag (Plan::dev_err[1]) if the value written is NaN or Inf.
+#ifdef __CUDACC__
+__device__ __forceinline__ void note_finite(double2 v, int *flag) {
+    if (flag && !(isfinite(v.x) && isfinite(v.y))) atomicOr(flag, 1);
+}
+__device__ __forceinline__ void note_finite(float2 v, int *flag) {
+    if (flag && !(isfinite(v.x) && isfinite(v.y))) atomicOr(flag, 1);
+}
+#endif
+inline int *nonfinite_flag(const Plan &pl) { return pl.dev_err ? pl.dev_err + 1 : nullptr; }
 
 // Fourier modes of one field: N^3 (3D) or N^2 (2D).
 inline size_t modes(const Plan &pl) { return (size_t)pl.N * pl.N * (pl.dim == 2 ? 1 : pl.N); }
@@ -164,6 +176,8 @@ bz_status launch_pair3(const Plan &pl, const ItemArgs &a, cudaStream_t st);
 cudaError_t mixed_setup(int N, int *G);
 bz_status mixed_upload(uint4 **wimg);
 bz_status launch_mixed(const Plan &pl, const ItemArgs &a, cudaStream_t st);
+// one bounded wait that nothing completes, giving up after `limit` clocks (bz_plan_wait_selftest)
+bz_status wait_selftest(const Plan &pl, long long limit, cudaStream_t st);
 cudaError_t collide_set_attributes(int N);
 void reduce_parts(const float2 *part, int nblk, int n, double2 *acc, cudaStream_t st);
 int chunk_terms_for(int N);          // after collide_set_attributes(N)

@@ -90,14 +90,17 @@ __device__ __forceinline__ uint32_t mbar_try(uint32_t mbar, uint32_t parity) {
                  : "=r"(ok) : "r"(mbar), "r"(parity) : "memory");
     return ok;
 }
-// Wait for the phase of the given parity, for at most about one second of SM clock; on
-// time-out the device flag is raised, `dead` is set so that later waits return at once, and
-// the pipeline carries on (every CTA still reaches every barrier; the results are invalid).
-__device__ __forceinline__ void mbar_wait(uint32_t mbar, uint32_t parity, int *err, bool &dead) {
+// Wait for the phase of the given parity, for at most `limit` SM clocks (by default about one
+// second); on time-out the device flag is raised, `dead` is set so that later waits return at
+// once, and the pipeline carries on (every CTA still reaches every barrier; the results are
+// invalid).
+constexpr long long kWaitLimit = 1LL << 31;
+__device__ __forceinline__ void mbar_wait(uint32_t mbar, uint32_t parity, int *err, bool &dead,
+                                          long long limit = kWaitLimit) {
     if (dead) return;
     const long long t0 = clock64();
     while (!mbar_try(mbar, parity))
-        if (clock64() - t0 > (1LL << 31)) {
+        if (clock64() - t0 > limit) {
             dead = true;
             if (err) atomicOr(err, 1);
             return;
@@ -478,6 +481,29 @@ static cudaLaunchConfig_t mixed_config(int G, cudaStream_t st, cudaLaunchAttribu
 // one CTA per SM for a kernel that allocates tensor memory, but two CTAs fit (2 x 256 of the
 // 512 columns; shared memory admits no third): the grid takes the cluster count of the FP32
 // kernel with the same cluster shape and two CTAs per SM when that is larger.
+// One wait that nothing completes, through the bounded wait of the tensor-core kernels: one
+// thread initialises an mbarrier that expects one arrival, no thread arrives, and the wait
+// gives up after `limit` clocks, raising *err.  Nothing is in flight when it returns.
+__global__ void k_wait_selftest(int *err, long long limit) {
+    __shared__ __align__(8) unsigned long long mbar;
+    const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&mbar);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        bool dead = false;
+        mbar_wait(mb, 0, err, dead, limit);
+    }
+}
+
+bz_status wait_selftest(const Plan &pl, long long limit, cudaStream_t st) {
+    k_wait_selftest<<<1, 32, 0, st>>>(pl.dev_err, limit);
+    BZ_CUDA_TRY(cudaGetLastError());
+    return BZ_OK;
+}
+
 cudaError_t mixed_setup(int N, int *G) {
     *G = 0;
     if (N != XN) return cudaErrorInvalidValue;

@@ -3,6 +3,8 @@
 // RK4: the step state f0 and the running combination fsum = f0 + dt/6 (k1 + 2k2 + 2k3 + k4)
 // are FP64; each stage's collide input is rounded to FP32 (pl.fin) and each stage
 // derivative k_s arrives in the FP64 accumulator of the collide pipeline.
+#include <cmath>
+
 #include "bz_internal.h"
 
 namespace bz {
@@ -47,11 +49,17 @@ __global__ void k_rk_stage(const double2 *__restrict__ k, double2 *__restrict__ 
     if (fin64) fin64[i] = y;
 }
 
-__global__ void k_rk_out(const double2 *f0, void *fhat, int dtype, int n) {
+__global__ void k_rk_out(const double2 *f0, void *fhat, int dtype, int n, int *flag) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    if (dtype == BZ_C128) ((double2 *)fhat)[i] = f0[i];
-    else ((float2 *)fhat)[i] = make_float2((float)f0[i].x, (float)f0[i].y);
+    if (dtype == BZ_C128) {
+        ((double2 *)fhat)[i] = f0[i];
+        note_finite(f0[i], flag);
+    } else {
+        const float2 w = make_float2((float)f0[i].x, (float)f0[i].y);
+        ((float2 *)fhat)[i] = w;
+        note_finite(w, flag);
+    }
 }
 
 // Moments of f_N over [-L, L]^3.  Only the modes on the three axes contribute:
@@ -108,7 +116,7 @@ bz_status rk4_steps(Plan &pl, void *fhat, int dtype, double dt, int nsteps, cuda
             ++nl;
         }
     }
-    k_rk_out<<<gs, bs, 0, st>>>(f0, fhat, dtype, n);
+    k_rk_out<<<gs, bs, 0, st>>>(f0, fhat, dtype, n, nonfinite_flag(pl));
     ++nl;
     BZ_CUDA_TRY(cudaGetLastError());
     if (launches) *launches += nl;
@@ -120,6 +128,8 @@ bz_status moments(Plan &pl, const void *fhat, int dtype, double out[5], cudaStre
     BZ_CUDA_TRY(cudaGetLastError());
     BZ_CUDA_TRY(cudaMemcpyAsync(out, pl.mom, 5 * sizeof(double), cudaMemcpyDeviceToHost, st));
     BZ_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int q = 0; q < 5; ++q)
+        if (!std::isfinite(out[q])) return BZ_ERR_NONFINITE;
     return BZ_OK;
 }
 

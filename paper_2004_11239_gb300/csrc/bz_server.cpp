@@ -1,18 +1,23 @@
 // Serving loop: continuous batching of homogeneous relaxation solves (RK4 on the collision
-// operator) of mixed N and (gamma, s).
+// operator) of mixed N, (gamma, s), data form and precision.
 //
-// A worker thread owns the device work.  Each iteration it
-//   1. admits queued requests in arrival order while the HBM budget and group slots allow
-//      (a request whose own footprint exceeds the whole budget fails with BZ_ERR_OOM; one
-//      queued longer than its max_queue_s fails with BZ_ERR_TIMEOUT),
-//   2. advances every active request by one RK4 step: requests with the same plan geometry
-//      and dt form a group; N <= 32 groups step all their active slots with one batched
-//      call (bz_batch_step_rk), larger N step each request through its own plan; every
-//      group runs on its own stream, so groups overlap on the device,
-//   3. retires requests whose last step is done (result copied to host) and frees their
-//      slots; idle plans and batches stay cached until the budget needs their memory.
-// State stays on the device from admission to completion.  Results do not depend on the
-// other requests in flight (batched results are per-instance invariant).
+// A worker thread owns the device work.  Requests with the same plan geometry, data form,
+// precision and dt form a group with its own plan, stream and completion event; N <= 32 groups
+// (fused pipeline) step all their active slots with one batched call (bz_batch_step_rk), the
+// others step each request through the group's plan.  The worker loops over the groups:
+//   - admission, in arrival order, while the HBM budget and group slots allow (a request whose
+//     own footprint exceeds the whole budget fails with BZ_ERR_OOM; one queued longer than its
+//     max_queue_s fails with BZ_ERR_TIMEOUT); a request admitted to a group whose step is in
+//     flight joins its next step,
+//   - a group whose event has completed (cudaEventQuery, never a blocking wait on another
+//     group) retires that step: each participant advances one RK4 step, finished requests copy
+//     their result to the host (BZ_ERR_NONFINITE if it holds NaN or Inf, BZ_ERR_CUDA if the
+//     step failed) and free their slots,
+//   - an idle group with active requests launches its next step and records its event.
+// Groups therefore run ahead independently and overlap on the device.  State stays on the
+// device from admission to completion; results do not depend on the other requests in flight
+// (batched results are per-instance invariant).  Idle plans and batches stay cached until the
+// budget needs their memory.
 #include <chrono>
 #include <condition_variable>
 #include <cmath>
@@ -39,11 +44,11 @@ namespace {
 using Clock = std::chrono::steady_clock;
 
 struct Key {
-    int N, N_rho, M, kernel;
+    int N, N_rho, M, kernel, data, precision;
     double L, R, s, dt, gamma_plan;   // gamma_plan is 0 for batched groups (gamma per slot)
     bool operator<(const Key &o) const {
-        return std::tie(N, N_rho, M, kernel, L, R, s, dt, gamma_plan) <
-               std::tie(o.N, o.N_rho, o.M, o.kernel, o.L, o.R, o.s, o.dt, o.gamma_plan);
+        return std::tie(N, N_rho, M, kernel, data, precision, L, R, s, dt, gamma_plan) <
+               std::tie(o.N, o.N_rho, o.M, o.kernel, o.data, o.precision, o.L, o.R, o.s, o.dt, o.gamma_plan);
     }
 };
 
@@ -63,15 +68,20 @@ struct Request {
 struct Group {
     Key key{};
     bz_plan *plan = nullptr;
-    bz_batch *batch = nullptr;         // N <= 32
+    bz_batch *batch = nullptr;         // batched groups (fused pipeline)
     double2 *state = nullptr;          // [capacity][N^3] c128 (batched groups)
     int capacity = 0;
     std::vector<Request *> slots;      // per slot (nullptr = free)
+    std::vector<Request *> singles;    // unbatched groups: the active requests
     cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;        // recorded after each step's launches
+    bool inflight = false;
+    int launch_status = BZ_OK;         // status of the in-flight step's launches
+    std::vector<Request *> running;    // participants of the in-flight step
     size_t bytes = 0;
     Clock::time_point last_used;
     int active() const {
-        int n = 0;
+        int n = (int)singles.size();
         for (auto *r : slots) n += r != nullptr;
         return n;
     }
@@ -89,7 +99,6 @@ struct bz_server {
     std::deque<Request *> queue;
     std::map<uint64_t, std::unique_ptr<Request>> all;
     std::map<Key, std::unique_ptr<Group>> groups;
-    std::vector<Request *> active_single;
     uint64_t next_id = 1;
     bool stop = false;
     std::thread worker;
@@ -100,23 +109,29 @@ struct bz_server {
 
 namespace {
 
-bool batched(int N) { return N <= 32; }
+// Groups whose plan runs the fused pipeline step their slots as one batch.
+bool batched(const bz_request &r) {
+    if (r.N > 32) return false;
+    return r.data != BZ_DATA_REAL || 32 % r.N == 0;    // the real-data form is fused for N | 32
+}
 
 size_t plan_bytes(const bz_request &r) {
     const size_t n3 = (size_t)r.N * r.N * r.N;
     const size_t P = (size_t)r.N_rho * r.M;
-    return P * n3 * 8 + P * 3 * r.N * 8 + (size_t)(32u << 20) + 6 * n3 * 16;
+    size_t b = P * n3 * 8 + P * 3 * r.N * 8 + (size_t)(64u << 20) + 6 * n3 * 16;
+    if (r.data == BZ_DATA_REAL) b += (P / 2) * (n3 * 8 + (size_t)3 * r.N * r.N * 8) + 2 * n3 * 16;
+    return b;
 }
 
 size_t batch_bytes(const bz_request &r, int capacity) {
     const size_t n3 = (size_t)r.N * r.N * r.N;
     const size_t P = (size_t)r.N_rho * r.M;
     const size_t nblk_max = (P + 15) / 16;
-    return (size_t)capacity * n3 * (8 + 8 * nblk_max + 32 + 16);
+    return (size_t)capacity * n3 * (8 + 8 * nblk_max + 32 + 16 + (r.data == BZ_DATA_REAL ? 8 : 0));
 }
 
 Key key_of(const bz_request &r) {
-    Key k{r.N, r.N_rho, r.M, r.kernel, r.L, r.R, r.s, r.dt, batched(r.N) ? 0.0 : r.gamma};
+    Key k{r.N, r.N_rho, r.M, r.kernel, r.data, r.precision, r.L, r.R, r.s, r.dt, batched(r) ? 0.0 : r.gamma};
     return k;
 }
 
@@ -124,6 +139,7 @@ void destroy_group(bz_server *S, Group *g) {
     if (g->batch) bz_batch_destroy(g->batch);
     if (g->plan) bz_plan_destroy(g->plan);
     cudaFree(g->state);
+    if (g->done) cudaEventDestroy(g->done);
     if (g->stream) cudaStreamDestroy(g->stream);
     S->used -= g->bytes;
 }
@@ -147,7 +163,7 @@ Group *get_group(bz_server *S, const bz_request &r, int *err) {
     Key k = key_of(r);
     auto it = S->groups.find(k);
     if (it != S->groups.end()) return it->second.get();
-    const int cap = batched(r.N) ? S->max_batch : 0;
+    const int cap = batched(r) ? S->max_batch : 0;
     const size_t need = plan_bytes(r) + (cap ? batch_bytes(r, cap) : 0);
     if (need > S->budget) { *err = BZ_ERR_OOM; return nullptr; }
     if (!make_room(S, need)) { *err = BZ_ERR_BUSY; return nullptr; }
@@ -156,10 +172,13 @@ Group *get_group(bz_server *S, const bz_request &r, int *err) {
     bz_plan_desc d;
     std::memset(&d, 0, sizeof(d));
     d.N = r.N; d.L = r.L; d.R = r.R; d.gamma = k.gamma_plan; d.s = r.s; d.N_rho = r.N_rho; d.M = r.M;
-    d.kernel = r.kernel; d.precision = BZ_PREC_FP32;
+    d.kernel = r.kernel; d.precision = r.precision; d.data = r.data;
     int st = bz_plan_create_ex(&g->plan, &d);
     if (st != BZ_OK) { *err = st; return nullptr; }
-    if (cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    if (cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&g->done, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        if (g->stream) cudaStreamDestroy(g->stream);
         bz_plan_destroy(g->plan);
         *err = BZ_ERR_CUDA;
         return nullptr;
@@ -172,6 +191,7 @@ Group *get_group(bz_server *S, const bz_request &r, int *err) {
             cudaGetLastError();
             if (g->batch) bz_batch_destroy(g->batch);
             bz_plan_destroy(g->plan);
+            cudaEventDestroy(g->done);
             cudaStreamDestroy(g->stream);
             *err = st;
             return nullptr;
@@ -237,7 +257,7 @@ void admit(bz_server *S) {
                 continue;
             }
             S->used += bytes;
-            S->active_single.push_back(q);
+            g->singles.push_back(q);
         }
         q->group = g;
         q->t_admit = Clock::now();
@@ -246,6 +266,8 @@ void admit(bz_server *S) {
     }
 }
 
+// Retires a request: its result to the host (a finite check on it), its slot or state freed.
+// The group's stream is idle here (its step has completed; at most an admission copy follows).
 void finish(bz_server *S, Request *q, int status) {
     Group *g = q->group;
     const size_t n3 = (size_t)q->req.N * q->req.N * q->req.N;
@@ -255,9 +277,20 @@ void finish(bz_server *S, Request *q, int status) {
         (cudaMemcpyAsync(q->output.data(), src, n3 * sizeof(double2), cudaMemcpyDeviceToHost, g->stream) != cudaSuccess ||
          cudaStreamSynchronize(g->stream) != cudaSuccess))
         status = BZ_ERR_CUDA;
+    if (status == BZ_OK)
+        for (const double2 &v : q->output)
+            if (!(std::isfinite(v.x) && std::isfinite(v.y))) {
+                status = BZ_ERR_NONFINITE;
+                break;
+            }
     if (g->batch) {
         g->slots[q->slot] = nullptr;
     } else {
+        for (size_t i = 0; i < g->singles.size(); ++i)
+            if (g->singles[i] == q) {
+                g->singles.erase(g->singles.begin() + (long)i);
+                break;
+            }
         cudaFree(q->state_single);
         q->state_single = nullptr;
         S->used -= n3 * sizeof(double2);
@@ -268,59 +301,75 @@ void finish(bz_server *S, Request *q, int status) {
     S->completed++;
 }
 
+// Retires the completed step of g (its event has fired or failed).
+void retire_step(bz_server *S, Group *g, cudaError_t ev) {
+    const int st = ev == cudaSuccess ? g->launch_status : BZ_ERR_CUDA;
+    g->inflight = false;
+    std::vector<Request *> run;
+    run.swap(g->running);
+    for (Request *q : run) {
+        if (st != BZ_OK) { finish(S, q, st); continue; }
+        S->steps++;
+        if (++q->steps_done >= q->steps_total) finish(S, q, BZ_OK);
+    }
+}
+
+// Launches one RK4 step of every active request of g on its stream and records its event.
+void launch_step(Group *g) {
+    int st = BZ_OK;
+    g->running.clear();
+    if (g->batch) {
+        std::vector<int> sl;
+        for (int i = 0; i < g->capacity; ++i)
+            if (g->slots[i]) {
+                sl.push_back(i);
+                g->running.push_back(g->slots[i]);
+            }
+        st = bz_batch_step_rk(g->batch, (int)sl.size(), sl.data(), g->state, BZ_C128, g->key.dt, 1, g->stream);
+    } else {
+        for (Request *q : g->singles) {
+            g->running.push_back(q);
+            double t = 0.0;
+            const int s1 = bz_step_rk(g->plan, q->state_single, BZ_C128, &t, q->req.dt, 1, nullptr, g->stream);
+            if (s1 != BZ_OK && st == BZ_OK) st = s1;
+        }
+    }
+    if (cudaEventRecord(g->done, g->stream) != cudaSuccess && st == BZ_OK) st = BZ_ERR_CUDA;
+    g->launch_status = st;
+    g->inflight = true;
+}
+
 void worker_main(bz_server *S) {
     cudaSetDevice(S->device);
     std::unique_lock<std::mutex> lk(S->mu);
     while (!S->stop) {
         admit(S);
-        bool any = !S->active_single.empty();
-        for (auto &kv : S->groups) any = any || (kv.second->batch && kv.second->active() > 0);
-        if (!any) {
-            S->cv.wait_for(lk, std::chrono::milliseconds(2));
-            continue;
-        }
+        bool progressed = false, inflight = false;
         auto t0 = Clock::now();
-        // one RK4 step for every active request; groups on their own streams
-        std::vector<std::pair<Group *, int>> launched;
         for (auto &kv : S->groups) {
             Group *g = kv.second.get();
-            if (!g->batch || g->active() == 0) continue;
-            std::vector<int> sl;
-            for (int i = 0; i < g->capacity; ++i)
-                if (g->slots[i]) sl.push_back(i);
-            int st = bz_batch_step_rk(g->batch, (int)sl.size(), sl.data(), g->state, BZ_C128, g->key.dt, 1, g->stream);
-            launched.push_back({g, st});
-        }
-        std::vector<std::pair<Request *, int>> singles;
-        for (Request *q : S->active_single) {
-            double t = 0.0;
-            int st = bz_step_rk(q->group->plan, q->state_single, BZ_C128, &t, q->req.dt, 1, nullptr, q->group->stream);
-            singles.push_back({q, st});
-        }
-        lk.unlock();
-        for (auto &gs : launched) cudaStreamSynchronize(gs.first->stream);
-        for (auto &qs : singles) cudaStreamSynchronize(qs.first->group->stream);
-        lk.lock();
-        S->steps++;
-        for (auto &gs : launched) {
-            Group *g = gs.first;
-            for (int i = 0; i < g->capacity; ++i) {
-                Request *q = g->slots[i];
-                if (!q) continue;
-                if (gs.second != BZ_OK) { finish(S, q, gs.second); continue; }
-                if (++q->steps_done >= q->steps_total) finish(S, q, BZ_OK);
+            if (g->inflight) {
+                const cudaError_t ev = cudaEventQuery(g->done);
+                if (ev == cudaErrorNotReady) {
+                    inflight = true;
+                    continue;
+                }
+                retire_step(S, g, ev);
+                progressed = true;
+            }
+            if (g->active() > 0) {
+                launch_step(g);
+                inflight = true;
+                progressed = true;
             }
         }
-        std::vector<Request *> still;
-        for (auto &qs : singles) {
-            Request *q = qs.first;
-            if (qs.second != BZ_OK) { finish(S, q, qs.second); continue; }
-            if (++q->steps_done >= q->steps_total) finish(S, q, BZ_OK);
-            else still.push_back(q);
+        if (progressed) {
+            S->busy_s += std::chrono::duration<double>(Clock::now() - t0).count();
+            S->cv.notify_all();
+        } else {
+            // nothing completed: poll again shortly (steps in flight) or wait for a request
+            S->cv.wait_for(lk, inflight ? std::chrono::microseconds(50) : std::chrono::microseconds(2000));
         }
-        S->active_single.swap(still);
-        S->busy_s += std::chrono::duration<double>(Clock::now() - t0).count();
-        S->cv.notify_all();
     }
 }
 
@@ -351,8 +400,13 @@ bz_status bz_submit(bz_server *S, const bz_request *req, uint64_t *ticket) {
     if (!S || !req || !ticket || !req->fhat0) return BZ_ERR_ARG;
     const bz_request &r = *req;
     if (!bz::supported_N(r.N) || r.N_rho < 1 || r.M < 1 || !(r.dt > 0) || !(r.t_end >= r.t0) ||
-        (r.dtype != BZ_C64 && r.dtype != BZ_C128) || r.kernel < BZ_KERNEL_FAMILY || r.kernel > BZ_KERNEL_B8)
+        (r.dtype != BZ_C64 && r.dtype != BZ_C128) || r.kernel < BZ_KERNEL_FAMILY || r.kernel > BZ_KERNEL_B8 ||
+        (r.data != BZ_DATA_COMPLEX && r.data != BZ_DATA_REAL) ||
+        (r.precision != BZ_PREC_FP32 && r.precision != BZ_PREC_BF16X3))
         return BZ_ERR_ARG;
+    if ((r.data == BZ_DATA_REAL && (r.M & 1)) ||
+        (r.precision == BZ_PREC_BF16X3 && (r.N != 32 || r.data != BZ_DATA_COMPLEX)))
+        return BZ_ERR_UNSUPPORTED;
     std::unique_ptr<Request> q(new (std::nothrow) Request());
     if (!q) return BZ_ERR_OOM;
     q->req = r;
@@ -408,8 +462,8 @@ bz_status bz_server_stats(bz_server *S, long *completed, long *steps, size_t *hb
     if (hbm_used) *hbm_used = S->used;
     if (queued) *queued = (int)S->queue.size();
     if (active) {
-        int n = (int)S->active_single.size();
-        for (auto &kv : S->groups) n += kv.second->batch ? kv.second->active() : 0;
+        int n = 0;
+        for (auto &kv : S->groups) n += kv.second->active();
         *active = n;
     }
     return BZ_OK;

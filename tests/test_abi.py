@@ -123,3 +123,17 @@ def test_library_rejects_unknown_sphere_rule(libpath):
         bz.bz_quadrature(4, 6.0, 13, 0.0)
     with pytest.raises(bz.BzError):
         bz.bz_kernel_constants(0, 1.5)
+
+
+def test_checkpoint_file_checks_without_gpu(libpath, tmp_path):
+    import paper_2004_11239_gb300 as bz
+    with pytest.raises(bz.BzError) as e:
+        bz.bz_checkpoint_plan_desc(str(tmp_path / "missing.bzck"))
+    assert e.value.code == 1
+    junk = tmp_path / "junk.bzck"
+    junk.write_bytes(b"not a checkpoint at all" * 10)
+    with pytest.raises(bz.BzError) as e:
+        bz.bz_checkpoint_plan_desc(str(junk))
+    assert e.value.code == 1
+    assert bz.lib.bz_plan_wait_selftest(None, 100, None) == 1
+    assert bz.lib.bz_plan_check_finite(None, None) == 1
