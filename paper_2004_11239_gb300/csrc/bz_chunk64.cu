@@ -1,0 +1,221 @@
+// The two plane passes of the chunked pipeline (Sec. 4, eq. realQ) at N = 64, one plane per CTA.
+//
+// A 64-point transform is split as 64 = 8 x 8 (n = 8 n1 + n2, k = k1 + 8 k2):
+//     X[k1 + 8 k2] = sum_n2 W8^(n2 k2) [ W64^(n2 k1) sum_n1 x[8 n1 + n2] W8^(n1 k1) ],
+// so each of 8 threads takes one n2 (stage 1: an 8-point DFT over n1, then the twiddle
+// W64^(n2 k1)), the 8 x 8 block is transposed through shared memory, and each thread takes one
+// k1 (stage 2: an 8-point DFT over n2).  A thread holds 8 values instead of a whole line, so a
+// 512-thread CTA transforms a 64 x 64 plane with about 64 registers per thread (the generic
+// kernels hold a line of 64 per thread: 168 registers, 12 warps per SM).
+//   rows (contiguous axis): the 8 threads of a row sit in one warp, the transpose needs only
+//     __syncwarp; its shared-memory slots are XOR-swizzled (8 k1 + (n2 ^ k1)) so that neither
+//     the stage-1 stores nor the stage-2 loads conflict;
+//   columns: a warp holds 32 consecutive columns of one n2, every access is a contiguous row
+//     segment; the transpose needs __syncthreads.
+// k_plane_inv64: twiddle (beta_p, or the pair's beta_p + i beta_p') on load from global, inverse
+//   transform along k3 (rows) then k2 (columns), result to S[t][k1][j2][j3].
+// k_plane_fwd64: forward transform along j2 (columns, loaded from S) then j3 (rows), times the
+//   weight alpha_p (or the pair table A), whose 8 values per thread are loaded at the start so
+//   the HBM stream overlaps the transforms; result to S; the pair form also writes the Nyquist
+//   sums X = C Z of the plane (family layout [3][N][N], every entry of this k1 written).
+#include "bz_fft.cuh"
+#include "bz_internal.h"
+
+namespace bz {
+
+namespace {
+
+constexpr int N64 = 64;
+constexpr int RP = 72;                 // row pitch (float2): rows r, r + 1 fall on opposite bank halves
+constexpr int T64 = 512;               // threads per CTA
+constexpr size_t kTileBytes = (size_t)N64 * RP * sizeof(float2);
+constexpr size_t kInvSmem = kTileBytes + (6 * N64 + N64) * sizeof(float2);   // tile, twiddles, W64
+constexpr size_t kFwdSmem = kTileBytes + N64 * sizeof(float2);
+
+// W64^(SIGN j) from the table w[j] = exp(+2 pi i j / 64)
+template <int SIGN> __device__ __forceinline__ float2 w64(const float2 *w, int j) {
+    float2 v = w[j & 63];
+    if (SIGN < 0) v.y = -v.y;
+    return v;
+}
+
+__device__ __forceinline__ void load_w64(float2 *w) {
+    if (threadIdx.x < N64) w[threadIdx.x] = c_tw.v[tw_off<64>() + threadIdx.x];
+}
+
+// Stage 1 of a 64-point transform on the thread's 8 values x[n1] = x(8 n1 + n2): the 8-point
+// DFT over n1 and the twiddle W64^(SIGN n2 k1); x[k1] holds Y[n2][k1] after it.
+template <int SIGN> __device__ __forceinline__ void stage1(float2 (&x)[8], int n2, const float2 *w) {
+    fft_inplace<8, SIGN>(x);
+    #pragma unroll
+    for (int k1 = 1; k1 < 8; ++k1) x[k1] = cmul(x[k1], w64<SIGN>(w, n2 * k1));
+}
+
+// Row pass of the plane held in `tile` (natural order) or, for the first pass of plane_inv, in
+// registers: thread (r, n2) = (tid / 8, tid % 8) holds x[n1] = row r element 8 n1 + n2 on entry
+// and y[k2] = row r element kk + 8 k2 of the transform (kk = n2) on exit.  The row's slots of
+// the tile are overwritten (swizzled scratch).
+template <int SIGN> __device__ __forceinline__ void row_pass(float2 (&x)[8], float2 *tile, int r, int n2,
+                                                             const float2 *w) {
+    stage1<SIGN>(x, n2, w);
+    float2 *row = tile + r * RP;
+    __syncwarp();                                         // the row's natural-order loads are done
+    #pragma unroll
+    for (int k1 = 0; k1 < 8; ++k1) row[8 * k1 + (n2 ^ k1)] = x[k1];
+    __syncwarp();
+    #pragma unroll
+    for (int m = 0; m < 8; ++m) x[m] = row[8 * n2 + (m ^ n2)];   // Y[m][kk], kk = n2
+    fft_inplace<8, SIGN>(x);                              // x[k2] = X[kk + 8 k2]
+}
+
+template <bool PAIR>
+__global__ void __launch_bounds__(T64, 2)
+k_plane_inv64(const float2 *__restrict__ fin, const float2 *__restrict__ tw, float2 *__restrict__ S, int p0,
+              int use_tw) {
+    extern __shared__ float2 sm[];
+    float2 *tile = sm;
+    float2 *stw = sm + N64 * RP;
+    float2 *w = stw + 6 * N64;
+    const int tid = threadIdx.x, k1p = blockIdx.x, t = blockIdx.y;
+    const int r = tid >> 3, n2 = tid & 7;
+    // the plane's row r, elements 8 n1 + n2, straight from global (L2)
+    const float2 *f = fin + ((size_t)k1p * N64 + r) * N64 + n2;
+    float2 x[8];
+    #pragma unroll
+    for (int n1 = 0; n1 < 8; ++n1) x[n1] = f[8 * n1];
+    load_w64(w);
+    if (use_tw) {
+        constexpr int NT = (PAIR ? 6 : 3) * N64;
+        const float2 *twp = tw + (size_t)(p0 + t) * NT;
+        for (int i = tid; i < NT; i += T64) stw[i] = twp[i];
+    }
+    __syncthreads();
+    if (use_tw) {
+        // beta(k1, k2, k3) = b1(k1) b2(k2) b3(k3) per term; the pair form takes b + i b'
+        const float2 a = cmul(stw[k1p], stw[N64 + r]);
+        if constexpr (PAIR) {
+            const float2 b = cmul(stw[3 * N64 + k1p], stw[4 * N64 + r]);
+            #pragma unroll
+            for (int n1 = 0; n1 < 8; ++n1) {
+                const int k3 = 8 * n1 + n2;
+                const float2 u = cmul(a, stw[2 * N64 + k3]), v = cmul(b, stw[5 * N64 + k3]);
+                x[n1] = cmul(x[n1], make_float2(u.x - v.y, u.y + v.x));
+            }
+        } else {
+            #pragma unroll
+            for (int n1 = 0; n1 < 8; ++n1) x[n1] = cmul(x[n1], cmul(a, stw[2 * N64 + 8 * n1 + n2]));
+        }
+    }
+    row_pass<+1>(x, tile, r, n2, w);                      // axis 3: k3 -> j3
+    __syncwarp();                                         // the row's swizzled loads are done
+    #pragma unroll
+    for (int k2 = 0; k2 < 8; ++k2) tile[r * RP + n2 + 8 * k2] = x[k2];
+    __syncthreads();
+    // axis 2: k2 -> j2, column c, thread (c, m2) = (tid % 64, tid / 64)
+    const int c = tid & 63, m2 = tid >> 6;
+    #pragma unroll
+    for (int n1 = 0; n1 < 8; ++n1) x[n1] = tile[(8 * n1 + m2) * RP + c];
+    stage1<+1>(x, m2, w);
+    #pragma unroll
+    for (int k1 = 0; k1 < 8; ++k1) tile[(8 * k1 + m2) * RP + c] = x[k1];   // the rows it read: no hazard
+    __syncthreads();
+    #pragma unroll
+    for (int m = 0; m < 8; ++m) x[m] = tile[(8 * m2 + m) * RP + c];
+    fft_inplace<8, +1>(x);                                // x[k2] = column c at j2 = m2 + 8 k2
+    float2 *out = S + (size_t)t * N64 * N64 * N64 + (size_t)k1p * N64 * N64 + c;
+    #pragma unroll
+    for (int k2 = 0; k2 < 8; ++k2) out[(m2 + 8 * k2) * N64] = x[k2];
+}
+
+template <bool PAIR>
+__global__ void __launch_bounds__(T64, 2)
+k_plane_fwd64(float2 *__restrict__ S, const float2 *__restrict__ alpha, int p0, const float2 *__restrict__ cpair,
+              float2 *__restrict__ Ss) {
+    extern __shared__ float2 sm[];
+    float2 *tile = sm;
+    float2 *w = sm + N64 * RP;
+    const int tid = threadIdx.x, k1p = blockIdx.x, t = blockIdx.y;
+    const int r = tid >> 3, n2 = tid & 7;                 // row-pass roles
+    const int c = tid & 63, m2 = tid >> 6;                // column-pass roles
+    float2 *pl = S + (size_t)t * N64 * N64 * N64 + (size_t)k1p * N64 * N64;
+    // the weights of this thread's 8 outputs (row r, k3 = n2 + 8 k2): from HBM, in flight
+    // during both transforms
+    const float2 *al = alpha + ((size_t)(p0 + t) * N64 * N64 * N64 + (size_t)k1p * N64 * N64 + (size_t)r * N64 + n2);
+    float2 a[8];
+    #pragma unroll
+    for (int k2 = 0; k2 < 8; ++k2) a[k2] = al[8 * k2];
+    float2 x[8];
+    #pragma unroll
+    for (int n1 = 0; n1 < 8; ++n1) x[n1] = pl[(8 * n1 + m2) * N64 + c];
+    load_w64(w);
+    __syncthreads();
+    // axis 2: j2 -> k2 on column c
+    stage1<-1>(x, m2, w);
+    #pragma unroll
+    for (int k1 = 0; k1 < 8; ++k1) tile[(8 * k1 + m2) * RP + c] = x[k1];
+    __syncthreads();
+    #pragma unroll
+    for (int m = 0; m < 8; ++m) x[m] = tile[(8 * m2 + m) * RP + c];
+    fft_inplace<8, -1>(x);                                // x[k2] = column c at k2 = m2 + 8 k2
+    __syncthreads();                                      // every stage-2 load is done
+    #pragma unroll
+    for (int k2 = 0; k2 < 8; ++k2) tile[(m2 + 8 * k2) * RP + c] = x[k2];
+    __syncthreads();
+    // axis 3: j3 -> k3 on row r (= k2)
+    #pragma unroll
+    for (int n1 = 0; n1 < 8; ++n1) x[n1] = tile[r * RP + 8 * n1 + n2];
+    row_pass<-1>(x, tile, r, n2, w);                      // x[k2] = Z(k2 = r, k3 = n2 + 8 k2)
+    float2 *o = pl + (size_t)r * N64 + n2;
+    #pragma unroll
+    for (int k2 = 0; k2 < 8; ++k2) o[8 * k2] = cmul(x[k2], a[k2]);
+    if constexpr (PAIR) {
+        const float2 *cq = cpair + (size_t)(p0 + t) * 3 * N64 * N64;
+        float2 *xs = Ss + (size_t)t * 3 * N64 * N64;
+        if (r == N64 / 2) {                               // family k2 = -N/2: [k1][k3]
+            #pragma unroll
+            for (int k2 = 0; k2 < 8; ++k2) {
+                const int k3 = n2 + 8 * k2;
+                xs[N64 * N64 + k1p * N64 + k3] = cmul(x[k2], cq[N64 * N64 + k1p * N64 + k3]);
+            }
+        }
+        if (n2 == 0)                                      // family k3 = -N/2 (k3 = 32: k2 = 4): [k1][k2]
+            xs[2 * N64 * N64 + k1p * N64 + r] = cmul(x[4], cq[2 * N64 * N64 + k1p * N64 + r]);
+        if (k1p == N64 / 2) {                             // the plane k1 = -N/2: [k2][k3]
+            #pragma unroll
+            for (int k2 = 0; k2 < 8; ++k2) {
+                const int k3 = n2 + 8 * k2;
+                xs[r * N64 + k3] = cmul(x[k2], cq[r * N64 + k3]);
+            }
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t chunk64_set_attributes() {
+    const void *inv[2] = {(const void *)k_plane_inv64<false>, (const void *)k_plane_inv64<true>};
+    const void *fwd[2] = {(const void *)k_plane_fwd64<false>, (const void *)k_plane_fwd64<true>};
+    for (const void *k : inv) {
+        const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kInvSmem);
+        if (e != cudaSuccess) return e;
+    }
+    for (const void *k : fwd) {
+        const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmem);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+void plane_inv64(const float2 *fin, const float2 *tw, float2 *S, int p0, int T, int use_tw, bool pair,
+                 cudaStream_t st) {
+    if (pair) k_plane_inv64<true><<<dim3(N64, T), T64, kInvSmem, st>>>(fin, tw, S, p0, use_tw);
+    else k_plane_inv64<false><<<dim3(N64, T), T64, kInvSmem, st>>>(fin, tw, S, p0, use_tw);
+}
+
+void plane_fwd64(float2 *S, const float2 *alpha, int p0, int T, const float2 *cpair, float2 *Ss, bool pair,
+                 cudaStream_t st) {
+    if (pair) k_plane_fwd64<true><<<dim3(N64, T), T64, kFwdSmem, st>>>(S, alpha, p0, cpair, Ss);
+    else k_plane_fwd64<false><<<dim3(N64, T), T64, kFwdSmem, st>>>(S, alpha, p0, nullptr, nullptr);
+}
+
+}  // namespace bz

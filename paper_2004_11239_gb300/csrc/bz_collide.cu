@@ -301,6 +301,10 @@ int supported_N(int N) {
 }
 
 template <int N> static cudaError_t set_attrs() {
+    if constexpr (N == 64) {
+        const cudaError_t e = chunk64_set_attributes();
+        if (e != cudaSuccess) return e;
+    }
     const void *ks[4] = {(const void *)k_plane_inv<N, false>, (const void *)k_plane_inv<N, true>,
                          (const void *)k_plane_fwd<N, false>, (const void *)k_plane_fwd<N, true>};
     for (const void *k : ks) {
@@ -353,12 +357,26 @@ cudaError_t collide_set_attributes(int N) {
     return cudaErrorInvalidValue;
 }
 
+// Plane passes of a chunk: at N = 64 the radix-8 one-plane-per-CTA kernels, else the generic ones.
+template <int N, bool PAIR>
+static void plane_inv(const float2 *fin, const float2 *tw, float2 *S, int p0, int T, int use_tw, cudaStream_t st) {
+    constexpr int PPC = Cfg<N>::PPC;
+    if constexpr (N == 64) plane_inv64(fin, tw, S, p0, T, use_tw, PAIR, st);
+    else k_plane_inv<N, PAIR><<<dim3(N / PPC, T), Cfg<N>::THREADS, Cfg<N>::SMEM, st>>>(fin, tw, S, p0, use_tw);
+}
+
+template <int N, bool PAIR>
+static void plane_fwd(float2 *S, const float2 *alpha, int p0, int T, const float2 *cpair, float2 *Ss, cudaStream_t st) {
+    constexpr int PPC = Cfg<N>::PPC;
+    if constexpr (N == 64) plane_fwd64(S, alpha, p0, T, cpair, Ss, PAIR, st);
+    else k_plane_fwd<N, PAIR><<<dim3(N / PPC, T), Cfg<N>::THREADS, Cfg<N>::SMEM, st>>>(S, alpha, p0, cpair, Ss);
+}
+
 // BZ_DATA_REAL: the Hermitian part of the input (sym_input) feeds h and the pair passes; the
 // chunks run over term pairs [p0 / 2, p1 / 2) with the pair table A, the Nyquist sums X are
 // reduced beside V, and Q is symmetrised after the last chunk.
 template <int N>
 static bz_status run_chunks_real(Plan &pl, int p0, int p1, cudaStream_t st, int *launches) {
-    constexpr int PPC = Cfg<N>::PPC;
     const int n3 = N * N * N, ns = 3 * N * N;
     if ((p0 | p1) & 1) return BZ_ERR_ARG;
     const int u0 = p0 / 2, u1 = p1 / 2;
@@ -366,7 +384,7 @@ static bz_status run_chunks_real(Plan &pl, int p0, int p1, cudaStream_t st, int 
     tm_begin(pl, st);
     bz_status s = sym_input(pl, pl.src ? pl.src : (const void *)pl.fin, pl.src ? pl.src_dtype : BZ_C64, st);
     if (s != BZ_OK) return s;
-    k_plane_inv<N, false><<<dim3(N / PPC, 1), Cfg<N>::THREADS, Cfg<N>::SMEM, st>>>(pl.fsym, pl.tw, pl.S, 0, 0);
+    plane_inv<N, false>(pl.fsym, pl.tw, pl.S, 0, 1, 0, st);
     k_pencil<N, 0><<<dim3((N * N + 127) / 128, 1), 128, 0, st>>>(pl.S, nullptr, pl.h);
     BZ_CUDA_TRY(cudaMemsetAsync(pl.acc, 0, (size_t)n3 * sizeof(double2), st));
     BZ_CUDA_TRY(cudaMemsetAsync(pl.acc_s, 0, (size_t)ns * sizeof(double2), st));
@@ -375,14 +393,13 @@ static bz_status run_chunks_real(Plan &pl, int p0, int p1, cudaStream_t st, int 
     for (int c0 = u0; c0 < u1; c0 += chunk) {
         const int T = (u1 - c0) < chunk ? (u1 - c0) : chunk;
         tm_begin(pl, st);
-        k_plane_inv<N, true><<<dim3(N / PPC, T), Cfg<N>::THREADS, Cfg<N>::SMEM, st>>>(pl.fsym, pl.tw, pl.S, c0, 1);
+        plane_inv<N, true>(pl.fsym, pl.tw, pl.S, c0, T, 1, st);
         tm_end(pl, st, TK_PLANE_INV);
         tm_begin(pl, st);
         k_pencil<N, 2><<<dim3((N * N + 127) / 128, T), 128, 0, st>>>(pl.S, pl.h, nullptr);
         tm_end(pl, st, TK_PENCIL);
         tm_begin(pl, st);
-        k_plane_fwd<N, true><<<dim3(N / PPC, T), Cfg<N>::THREADS, Cfg<N>::SMEM, st>>>(pl.S, pl.apair, c0, pl.cpair,
-                                                                                   pl.S_s);
+        plane_fwd<N, true>(pl.S, pl.apair, c0, T, pl.cpair, pl.S_s, st);
         tm_end(pl, st, TK_PLANE_FWD);
         tm_begin(pl, st);
         k_reduce<<<(n3 / 2 + ns / 2 + 255) / 256, 256, 0, st>>>(pl.S, T, n3, pl.acc, pl.S_s, ns, pl.acc_s);
@@ -401,13 +418,11 @@ static bz_status run_chunks_real(Plan &pl, int p0, int p1, cudaStream_t st, int 
 
 template <int N>
 static bz_status run_chunks(Plan &pl, int p0, int p1, cudaStream_t st, int *launches) {
-    constexpr int PPC = Cfg<N>::PPC;
     const int n3 = N * N * N;
-    const dim3 plane_grid1(N / PPC, 1);
     if (pl.real) return run_chunks_real<N>(pl, p0, p1, st, launches);
     // h = IFFT(fhat): planes without twiddles into S[0], then an inverse-only pencil pass
     tm_begin(pl, st);
-    k_plane_inv<N, false><<<plane_grid1, Cfg<N>::THREADS, Cfg<N>::SMEM, st>>>(pl.fin, pl.tw, pl.S, 0, 0);
+    plane_inv<N, false>(pl.fin, pl.tw, pl.S, 0, 1, 0, st);
     k_pencil<N, 0><<<dim3((N * N + 127) / 128, 1), 128, 0, st>>>(pl.S, nullptr, pl.h);
     BZ_CUDA_TRY(cudaMemsetAsync(pl.acc, 0, (size_t)n3 * sizeof(double2), st));
     tm_end(pl, st, TK_OTHER);
@@ -415,13 +430,13 @@ static bz_status run_chunks(Plan &pl, int p0, int p1, cudaStream_t st, int *laun
     for (int c0 = p0; c0 < p1; c0 += pl.chunk) {
         const int T = (p1 - c0) < pl.chunk ? (p1 - c0) : pl.chunk;
         tm_begin(pl, st);
-        k_plane_inv<N, false><<<dim3(N / PPC, T), Cfg<N>::THREADS, Cfg<N>::SMEM, st>>>(pl.fin, pl.tw, pl.S, c0, 1);
+        plane_inv<N, false>(pl.fin, pl.tw, pl.S, c0, T, 1, st);
         tm_end(pl, st, TK_PLANE_INV);
         tm_begin(pl, st);
         k_pencil<N, 1><<<dim3((N * N + 127) / 128, T), 128, 0, st>>>(pl.S, pl.h, nullptr);
         tm_end(pl, st, TK_PENCIL);
         tm_begin(pl, st);
-        k_plane_fwd<N, false><<<dim3(N / PPC, T), Cfg<N>::THREADS, Cfg<N>::SMEM, st>>>(pl.S, pl.alpha, c0);
+        plane_fwd<N, false>(pl.S, pl.alpha, c0, T, nullptr, nullptr, st);
         tm_end(pl, st, TK_PLANE_FWD);
         tm_begin(pl, st);
         k_reduce<<<(n3 / 2 + 255) / 256, 256, 0, st>>>(pl.S, T, n3, pl.acc);

@@ -179,6 +179,12 @@ bz_status launch_mixed(const Plan &pl, const ItemArgs &a, cudaStream_t st);
 // one bounded wait that nothing completes, giving up after `limit` clocks (bz_plan_wait_selftest)
 bz_status wait_selftest(const Plan &pl, long long limit, cudaStream_t st);
 cudaError_t collide_set_attributes(int N);
+// bz_chunk64.cu: the plane passes of the chunked pipeline at N = 64 (radix 8 x 8, one plane per CTA)
+cudaError_t chunk64_set_attributes();
+void plane_inv64(const float2 *fin, const float2 *tw, float2 *S, int p0, int T, int use_tw, bool pair,
+                 cudaStream_t st);
+void plane_fwd64(float2 *S, const float2 *alpha, int p0, int T, const float2 *cpair, float2 *Ss, bool pair,
+                 cudaStream_t st);
 void reduce_parts(const float2 *part, int nblk, int n, double2 *acc, cudaStream_t st);
 int chunk_terms_for(int N);          // after collide_set_attributes(N)
 int supported_N(int N);
