@@ -32,6 +32,12 @@ void free_plan(bz::Plan &p) {
     cudaFree(p.rk); cudaFree(p.mom); cudaFree(p.part); cudaFree(p.fin64); cudaFree(p.scr64);
     cudaFree(p.wimg); cudaFree(p.dev_err); cudaFree(p.apair); cudaFree(p.fsym); cudaFree(p.fsym64);
     cudaFree(p.cpair); cudaFree(p.part_s); cudaFree(p.S_s); cudaFree(p.acc_s);
+    cudaFree(p.S2); cudaFree(p.S_s2); cudaFree(p.acc2); cudaFree(p.acc_s2);
+    if (p.ev_fork) cudaEventDestroy(p.ev_fork);
+    if (p.ev_join) cudaEventDestroy(p.ev_join);
+    if (p.st2) cudaStreamDestroy(p.st2);
+    p.S2 = nullptr; p.S_s2 = nullptr; p.acc2 = nullptr; p.acc_s2 = nullptr;
+    p.ev_fork = nullptr; p.ev_join = nullptr; p.st2 = nullptr;
     p.wimg = nullptr; p.dev_err = nullptr; p.apair = nullptr; p.fsym = nullptr; p.fsym64 = nullptr;
     p.cpair = nullptr; p.part_s = nullptr; p.S_s = nullptr; p.acc_s = nullptr;
     p.part = nullptr; p.fin64 = nullptr; p.scr64 = nullptr; p.src = nullptr;
@@ -176,10 +182,13 @@ bz_status create(bz_plan **out, const bz_plan_desc *d) {
     const size_t field = n3 * sizeof(float2);
     int chunk = d->chunk_terms;
     if (dim == 2) chunk = 1;                  // no chunked pipeline in 2D
+    // the chunked pipeline (N > 32, or asked for) runs its chunks on two streams
+    const bool two_streams = dim == 3 && (N > 32 || d->pipeline == BZ_PIPE_CHUNKED);
     if (chunk <= 0) {
-        // one wave of plane CTAs, within an L2-sized scratch
+        // two waves of plane CTAs, within an L2-sized scratch; one wave per stream on two streams
         if (bz::collide_set_attributes(N) != cudaSuccess) { delete h; return BZ_ERR_CUDA; }
         chunk = bz::chunk_terms_for(N);
+        if (two_streams && chunk > 1) chunk /= 2;
     }
     if (chunk > pl.P) chunk = pl.P;
     if (chunk > 65535) chunk = 65535;
@@ -252,6 +261,29 @@ bz_status create(bz_plan **out, const bz_plan_desc *d) {
         free_plan(pl);
         delete h;
         return BZ_ERR_UNSUPPORTED;
+    }
+    if (two_streams && !pl.use_fused) {
+        // second scratch and accumulators; without them the chunks stay on one stream
+        const size_t ns = (size_t)3 * N * N;
+        bool ok = dmalloc(&pl.S2, (size_t)pl.chunk * field) == BZ_OK && dmalloc(&pl.acc2, n3 * sizeof(double2)) == BZ_OK;
+        if (ok && pl.real)
+            ok = dmalloc(&pl.S_s2, (size_t)pl.chunk * ns * sizeof(float2)) == BZ_OK &&
+                 dmalloc(&pl.acc_s2, ns * sizeof(double2)) == BZ_OK;
+        ok = ok && cudaStreamCreateWithFlags(&pl.st2, cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&pl.ev_fork, cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&pl.ev_join, cudaEventDisableTiming) == cudaSuccess;
+        if (ok) {
+            pl.ws_bytes += (size_t)pl.chunk * field + n3 * sizeof(double2) +
+                           (pl.real ? (size_t)pl.chunk * ns * sizeof(float2) + ns * sizeof(double2) : 0);
+        } else {
+            cudaGetLastError();
+            cudaFree(pl.S2); cudaFree(pl.acc2); cudaFree(pl.S_s2); cudaFree(pl.acc_s2);
+            if (pl.ev_fork) cudaEventDestroy(pl.ev_fork);
+            if (pl.ev_join) cudaEventDestroy(pl.ev_join);
+            if (pl.st2) cudaStreamDestroy(pl.st2);
+            pl.S2 = nullptr; pl.acc2 = nullptr; pl.S_s2 = nullptr; pl.acc_s2 = nullptr;
+            pl.ev_fork = nullptr; pl.ev_join = nullptr; pl.st2 = nullptr;
+        }
     }
     *out = h;
     return BZ_OK;

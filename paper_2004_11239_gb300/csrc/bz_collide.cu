@@ -1,7 +1,8 @@
 // The per-term pipeline of eq. realQ (Sec. 4) in FP32 with FP64 accumulation over terms.
 //
 // For each chunk of T terms, four kernels run over a scratch buffer S[T][N^3] sized to
-// stay in L2:
+// stay in L2 (where the plan has a second stream, odd chunks run on it over a second scratch
+// and accumulator, overlapping the even chunks; the two sums are added at the end):
 //   plane_inv  (planes k1):  S = IFFT_{axes 3,2}( beta_p(m) fhat_m )       twiddle + 2 axes
 //   pencil     (lines k1):   S = FFT_1( h . IFFT_1(S) )                     product in registers
 //   plane_fwd  (planes k1):  S = alpha_p . FFT_{axes 3,2}(S)                 weight in the epilogue
@@ -230,6 +231,18 @@ __global__ void k_acc_to_c64(const double2 *__restrict__ in, float2 *__restrict_
     if (i < n) out[i] = make_float2((float)in[i].x, (float)in[i].y);
 }
 
+// a[i] += b[i]: the second stream's accumulator into the first.
+__global__ void k_acc_add(double2 *__restrict__ a, const double2 *__restrict__ b, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        double2 v = a[i];
+        const double2 w = b[i];
+        v.x += w.x;
+        v.y += w.y;
+        a[i] = v;
+    }
+}
+
 // The plan's result to the caller's array in its dtype, raising the non-finite flag.
 __global__ void k_acc_out(const double2 *__restrict__ in, void *__restrict__ out, int dtype, int n, int *flag) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -390,21 +403,40 @@ static bz_status run_chunks_real(Plan &pl, int p0, int p1, cudaStream_t st, int 
     BZ_CUDA_TRY(cudaMemsetAsync(pl.acc_s, 0, (size_t)ns * sizeof(double2), st));
     tm_end(pl, st, TK_OTHER);
     int nl = 3;
-    for (int c0 = u0; c0 < u1; c0 += chunk) {
+    const bool two = pl.st2 && (u1 - u0) > chunk;
+    if (two) {
+        BZ_CUDA_TRY(cudaEventRecord(pl.ev_fork, st));
+        BZ_CUDA_TRY(cudaStreamWaitEvent(pl.st2, pl.ev_fork, 0));
+        BZ_CUDA_TRY(cudaMemsetAsync(pl.acc2, 0, (size_t)n3 * sizeof(double2), pl.st2));
+        BZ_CUDA_TRY(cudaMemsetAsync(pl.acc_s2, 0, (size_t)ns * sizeof(double2), pl.st2));
+    }
+    for (int c0 = u0, i = 0; c0 < u1; c0 += chunk, ++i) {
         const int T = (u1 - c0) < chunk ? (u1 - c0) : chunk;
-        tm_begin(pl, st);
-        plane_inv<N, true>(pl.fsym, pl.tw, pl.S, c0, T, 1, st);
-        tm_end(pl, st, TK_PLANE_INV);
-        tm_begin(pl, st);
-        k_pencil<N, 2><<<dim3((N * N + 127) / 128, T), 128, 0, st>>>(pl.S, pl.h, nullptr);
-        tm_end(pl, st, TK_PENCIL);
-        tm_begin(pl, st);
-        plane_fwd<N, true>(pl.S, pl.apair, c0, T, pl.cpair, pl.S_s, st);
-        tm_end(pl, st, TK_PLANE_FWD);
-        tm_begin(pl, st);
-        k_reduce<<<(n3 / 2 + ns / 2 + 255) / 256, 256, 0, st>>>(pl.S, T, n3, pl.acc, pl.S_s, ns, pl.acc_s);
-        tm_end(pl, st, TK_REDUCE);
+        const bool odd = two && (i & 1);
+        cudaStream_t cs = odd ? pl.st2 : st;
+        float2 *S = odd ? pl.S2 : pl.S, *Ss = odd ? pl.S_s2 : pl.S_s;
+        double2 *acc = odd ? pl.acc2 : pl.acc, *acc_s = odd ? pl.acc_s2 : pl.acc_s;
+        tm_begin(pl, cs);
+        plane_inv<N, true>(pl.fsym, pl.tw, S, c0, T, 1, cs);
+        tm_end(pl, cs, TK_PLANE_INV);
+        tm_begin(pl, cs);
+        k_pencil<N, 2><<<dim3((N * N + 127) / 128, T), 128, 0, cs>>>(S, pl.h, nullptr);
+        tm_end(pl, cs, TK_PENCIL);
+        tm_begin(pl, cs);
+        plane_fwd<N, true>(S, pl.apair, c0, T, pl.cpair, Ss, cs);
+        tm_end(pl, cs, TK_PLANE_FWD);
+        tm_begin(pl, cs);
+        k_reduce<<<(n3 / 2 + ns / 2 + 255) / 256, 256, 0, cs>>>(S, T, n3, acc, Ss, ns, acc_s);
+        tm_end(pl, cs, TK_REDUCE);
         nl += 4;
+    }
+    if (two) {
+        // the second stream's sums join the first's in a fixed order
+        BZ_CUDA_TRY(cudaEventRecord(pl.ev_join, pl.st2));
+        BZ_CUDA_TRY(cudaStreamWaitEvent(st, pl.ev_join, 0));
+        k_acc_add<<<(n3 + 255) / 256, 256, 0, st>>>(pl.acc, pl.acc2, n3);
+        k_acc_add<<<(ns + 255) / 256, 256, 0, st>>>(pl.acc_s, pl.acc_s2, ns);
+        nl += 2;
     }
     tm_begin(pl, st);
     s = sym_output(pl, st);
@@ -427,21 +459,37 @@ static bz_status run_chunks(Plan &pl, int p0, int p1, cudaStream_t st, int *laun
     BZ_CUDA_TRY(cudaMemsetAsync(pl.acc, 0, (size_t)n3 * sizeof(double2), st));
     tm_end(pl, st, TK_OTHER);
     int nl = 2;
-    for (int c0 = p0; c0 < p1; c0 += pl.chunk) {
+    const bool two = pl.st2 && (p1 - p0) > pl.chunk;
+    if (two) {
+        BZ_CUDA_TRY(cudaEventRecord(pl.ev_fork, st));
+        BZ_CUDA_TRY(cudaStreamWaitEvent(pl.st2, pl.ev_fork, 0));
+        BZ_CUDA_TRY(cudaMemsetAsync(pl.acc2, 0, (size_t)n3 * sizeof(double2), pl.st2));
+    }
+    for (int c0 = p0, i = 0; c0 < p1; c0 += pl.chunk, ++i) {
         const int T = (p1 - c0) < pl.chunk ? (p1 - c0) : pl.chunk;
-        tm_begin(pl, st);
-        plane_inv<N, false>(pl.fin, pl.tw, pl.S, c0, T, 1, st);
-        tm_end(pl, st, TK_PLANE_INV);
-        tm_begin(pl, st);
-        k_pencil<N, 1><<<dim3((N * N + 127) / 128, T), 128, 0, st>>>(pl.S, pl.h, nullptr);
-        tm_end(pl, st, TK_PENCIL);
-        tm_begin(pl, st);
-        plane_fwd<N, false>(pl.S, pl.alpha, c0, T, nullptr, nullptr, st);
-        tm_end(pl, st, TK_PLANE_FWD);
-        tm_begin(pl, st);
-        k_reduce<<<(n3 / 2 + 255) / 256, 256, 0, st>>>(pl.S, T, n3, pl.acc);
-        tm_end(pl, st, TK_REDUCE);
+        const bool odd = two && (i & 1);
+        cudaStream_t cs = odd ? pl.st2 : st;
+        float2 *S = odd ? pl.S2 : pl.S;
+        double2 *acc = odd ? pl.acc2 : pl.acc;
+        tm_begin(pl, cs);
+        plane_inv<N, false>(pl.fin, pl.tw, S, c0, T, 1, cs);
+        tm_end(pl, cs, TK_PLANE_INV);
+        tm_begin(pl, cs);
+        k_pencil<N, 1><<<dim3((N * N + 127) / 128, T), 128, 0, cs>>>(S, pl.h, nullptr);
+        tm_end(pl, cs, TK_PENCIL);
+        tm_begin(pl, cs);
+        plane_fwd<N, false>(S, pl.alpha, c0, T, nullptr, nullptr, cs);
+        tm_end(pl, cs, TK_PLANE_FWD);
+        tm_begin(pl, cs);
+        k_reduce<<<(n3 / 2 + 255) / 256, 256, 0, cs>>>(S, T, n3, acc);
+        tm_end(pl, cs, TK_REDUCE);
         nl += 4;
+    }
+    if (two) {
+        BZ_CUDA_TRY(cudaEventRecord(pl.ev_join, pl.st2));
+        BZ_CUDA_TRY(cudaStreamWaitEvent(st, pl.ev_join, 0));
+        k_acc_add<<<(n3 + 255) / 256, 256, 0, st>>>(pl.acc, pl.acc2, n3);
+        ++nl;
     }
     BZ_CUDA_TRY(cudaGetLastError());
     if (launches) *launches += nl;

@@ -80,6 +80,14 @@ struct Plan {
     float2 *part_s = nullptr;       // [fused_G][3][N][N] per-item sums X on the Nyquist planes
     float2 *S_s = nullptr;          // chunked pipeline: [chunk][3][N][N] the chunk's Nyquist sums
     double2 *acc_s = nullptr;       // chunked pipeline: [3][N][N] FP64 sum of X
+    // chunked pipeline on two streams: odd chunks run on st2 over their own scratch and
+    // accumulators, overlapping the even chunks on the caller's stream
+    cudaStream_t st2 = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    float2 *S2 = nullptr;           // [chunk][N^3]
+    float2 *S_s2 = nullptr;         // [chunk][3][N][N] (BZ_DATA_REAL)
+    double2 *acc2 = nullptr;        // [N^3]
+    double2 *acc_s2 = nullptr;      // [3][N][N] (BZ_DATA_REAL)
     float2 *fsym = nullptr;         // [N^3] Hermitian part of fhat, Nyquist planes zero (FP32)
     double2 *fsym64 = nullptr;      // [N^3] the same in FP64 (source of h)
     int *dev_err = nullptr;         // device flags: [0] a bounded wait of a kernel gave up,
