@@ -110,6 +110,7 @@ _PROFILES = {
     "mixed": ("mixed_rk4_n32.md", ("bz_mixed.cu", "bz_fft.cuh", "bz_cluster.cuh")),
     "fused_real": ("fused_real_rk4_n32.md", ("bz_fused_kernel.cuh", "bz_fft.cuh", "bz_cluster.cuh")),
     "pair3": ("pair3_rk4_n32.md", ("bz_pair3.cu", "bz_fft.cuh", "bz_cluster.cuh")),
+    "n64:pipeline": ("chunked_single_n64.md", ("bz_collide.cu", "bz_chunk64.cu", "bz_fft.cuh")),
 }
 
 
@@ -661,6 +662,29 @@ def run_sharded(args, w):
     return 0
 
 
+def _pipeline_roofline(w, ms_per_collide, peaks, src, traffic_key=None):
+    """Roofline of a whole collide on the chunked pipeline, whose kernels overlap on two streams:
+    the method's algorithmic flops (the per-term count of SURVEY-style FFT work, every term) and
+    the alpha-table bytes (8 N^3 per term) of one collide over the measured collide time,
+    against the FP32 FMA peak and the measured HBM bandwidth; the larger fraction binds."""
+    N, P = w["N"], w["N_rho"] * w["M"]
+    s = ms_per_collide / 1e3
+    alu_peak, sms, alu_src = _alu_peak(peaks)
+    alu = {"bound": "alu", "achieved": _flops_per_term(N)["fused"] * P / s / 1e12, "peak": alu_peak,
+           "unit": "TFLOP/s"}
+    hbm = {"bound": "hbm", "achieved": _bytes_per_term(N)["fused"] * P / s / 1e9, "peak": peaks["hbm_gbs"],
+           "unit": "GB/s"}
+    for r in (alu, hbm):
+        r["frac"] = r["achieved"] / r["peak"]
+    roof, other = (alu, hbm) if alu["frac"] >= hbm["frac"] else (hbm, alu)
+    roof.update({"kernel": "chunked pipeline (plane, pencil, plane, reduce on two streams)",
+                 "traffic": _profiled_traffic(traffic_key) if traffic_key else None,
+                 "peak_source": alu_src if roof is alu else src, "sm_count": sms,
+                 "avg_launch_us": ms_per_collide * 1e3, "unit_of_work": f"one collide of {P} terms",
+                 "also": {k: other[k] for k in ("bound", "achieved", "peak", "unit", "frac")}})
+    return roof
+
+
 def run_ours(args, w):
     import numpy as np
     import torch
@@ -722,8 +746,11 @@ def run_ours(args, w):
 
     peaks, src = _peaks()
     kname = pipe.get("kernel", "k_fused")
-    roof = _roofline(args, w, kern, peaks, src, "n64" if (args.workload == "single_n64" and real) else
-                     ("pair3" if kname == "k_pair3" else ("fused_real" if real else "fused")))
+    if pipe["pipeline"] == "chunked" and not is_rk:
+        roof = _pipeline_roofline(w, ms / args.steps, peaks, src,
+                                  "n64:pipeline" if (args.workload == "single_n64" and real) else None)
+    else:
+        roof = _roofline(args, w, kern, peaks, src, "pair3" if kname == "k_pair3" else ("fused_real" if real else "fused"))
     roof["kernel_name"] = kname
     if real:
         roof["executed"] = ("term pairs share every pair of 3D transforms: about half the counted FFT "
@@ -731,7 +758,7 @@ def run_ours(args, w):
 
     # the other data form on the same workload (complex beside real, and the reverse where it applies)
     other = None
-    if dim == 3 and (real or _real_supported(w)):
+    if dim == 3 and (real or _real_supported(w)) and not args.no_other_form:
         po = make_plan(bz.BZ_DATA_COMPLEX if real else bz.BZ_DATA_REAL)
         fo, qo = torch.from_numpy(f_host).to("cuda"), torch.empty_like(f)
         qa = torch.empty_like(f)
@@ -825,7 +852,7 @@ def _measure_n64(args, bz, peaks, src, barrier, with_parity):
     a = argparse.Namespace(**vars(args))
     a.steps = max(5, min(args.steps, 50))
     value, ms, kern, launches, _ = _time_plan(a, w, bz, plan, f, q, st, barrier)
-    roof = _roofline(a, w, kern, peaks, src, "n64")
+    roof = _pipeline_roofline(w, ms / a.steps, peaks, src, "n64:pipeline")
     out = {"desc": w["desc"], "value": value, "unit": "evals/s", "steps": a.steps, "ms_per_collide": ms / a.steps,
            "gpu_launches": launches * a.steps, "plan_create_s": plan_s, "roofline": roof,
            "kernels_ms": {k: v[1] / a.steps for k, v in kern.items()}, "pipeline": bz.bz_plan_pipeline(plan),
@@ -1168,6 +1195,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="rk4_n32", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n-rho", type=int, default=0,
+                    help="override the workload's radial points (a smaller case of the same kernels, for profiling)")
+    ap.add_argument("--sphere-m", type=int, default=0, help="override the workload's sphere points")
+    ap.add_argument("--no-other-form", action="store_true",
+                    help="skip timing the other data form (complex beside real) on the same workload")
     ap.add_argument("--no-n64", action="store_true",
                     help="skip the N = 64 single-collide block measured beside the default workload")
     ap.add_argument("--no-mixed", action="store_true",
@@ -1183,7 +1215,13 @@ def main():
     ap.add_argument("--h-precision", type=int, default=0, choices=[0, 1, 2],
                     help="h = IFFT(fhat) precision on the fused path: 0 auto (FP64), 1 FP64, 2 FP32")
     args = ap.parse_args()
-    w = WORKLOADS[args.workload]
+    w = dict(WORKLOADS[args.workload])
+    if args.n_rho > 0:
+        w["N_rho"] = args.n_rho
+        w["desc"] += f" [N_rho overridden: {args.n_rho}]"
+    if args.sphere_m > 0:
+        w["M"] = args.sphere_m
+        w["desc"] += f" [M overridden: {args.sphere_m}]"
     if args.impl == "reference" and args.workload in ("batch_4096", "serve"):
         # the oracle computes one collide at a time: its rate on one instance is the reference
         ws, rank, _ = _dist()
