@@ -385,16 +385,20 @@ def cpu_baseline_cores(w, L, R, f, real, target_s=15.0):
                       f"/ P; the F-table build (a one-time plan cost) is excluded"}
 
 
-def sampled_modes(q_gpu, n_top=24, n_rand=24, seed=12):
-    """Modes at which the oracle checks a collide: the n_top largest |Qhat| and n_rand seeded
-    uniform ones (array indices [S, 3])."""
+def sampled_modes(q_gpu, n_top=64, n_rand=128, n_nyq=64, seed=12):
+    """Modes at which the oracle checks a collide (array indices [S, 3]): the n_top largest
+    |Qhat|, n_rand seeded uniform ones, and n_nyq seeded ones on the Nyquist planes (an index
+    N/2 on some axis, where the real-data form and eq. realQ differ most)."""
     import numpy as np
     import bz_inputs as bi
     N = q_gpu.shape[0]
     top = np.argsort(np.abs(q_gpu).ravel())[::-1][:n_top]
-    u = bi.SplitMix64(seed).uniform(n_rand)
-    rnd = (u * N ** 3).astype(np.int64)
-    flat = np.unique(np.concatenate([top, rnd]))
+    u = bi.SplitMix64(seed).uniform(n_rand + 3 * n_nyq)
+    rnd = (u[:n_rand] * N ** 3).astype(np.int64)
+    v = (u[n_rand:].reshape(n_nyq, 3) * N).astype(np.int64)
+    v[np.arange(n_nyq), np.arange(n_nyq) % 3] = N // 2
+    nyq = (v[:, 0] * N + v[:, 1]) * N + v[:, 2]
+    flat = np.unique(np.concatenate([top, rnd, nyq]))
     return np.stack(np.unravel_index(flat, q_gpu.shape), axis=1)
 
 
