@@ -689,6 +689,29 @@ def _pipeline_roofline(w, ms_per_collide, peaks, src, traffic_key=None):
     return roof
 
 
+def _bkw_trajectory(bz, plan, w, L, steps=500):
+    """SURVEY's C2 check: RK4 of the BKW solution from t0 for `steps` steps of dt on the GPU
+    (complex128 state), against the exact BKW solution (Sec. 5.1, eq. BKW) at the final time:
+    relative L-infinity error of the coefficients, max |f_gpu - f_exact| / max |f_exact|.
+    This measures the method (quadrature, truncation) and the FP32 pipeline together."""
+    import numpy as np
+    import torch
+    import bz_inputs as bi
+    t0, dt = w["t0"], w["dt"]
+    f = torch.from_numpy(bi.bkw_fhat(w["N"], L, bi.bkw_K(t0))).to("cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    t = bz.bz_step_rk(plan, f, t0, dt, steps)
+    e1.record()
+    torch.cuda.synchronize()
+    exact = bi.bkw_fhat(w["N"], L, bi.bkw_K(t))
+    got = f.cpu().numpy()
+    start = bi.bkw_fhat(w["N"], L, bi.bkw_K(t0))
+    return {"t0": t0, "t_end": t, "steps": steps, "dt": dt, "ms": e0.elapsed_time(e1),
+            "rel_linf_vs_bkw": float(np.max(np.abs(got - exact)) / np.max(np.abs(exact))),
+            "rel_change_of_f": float(np.max(np.abs(exact - start)) / np.max(np.abs(exact)))}
+
+
 def run_ours(args, w):
     import numpy as np
     import torch
@@ -795,6 +818,16 @@ def run_ours(args, w):
                                  also_realq=real)
         parity["collide"] = "one full collide of the workload's input through bz_collide"
 
+    # SURVEY's C2: the 500-step BKW trajectory against the exact solution, s = 1/2 and 1/4
+    trajectory = None
+    if args.workload == "rk4_n32" and not args.no_trajectory:
+        trajectory = {"desc": "RK4 of the BKW solution from t=6.5 to t=11.5 (500 steps of 0.01), N=32, "
+                              "N_rho=M=32, gamma=0, against the exact solution (eq. BKW) at t=11.5",
+                      "s=0.5": _bkw_trajectory(bz, plan, w, L)}
+        p25 = bz.bz_plan_create_ex(N, L, R, w["gamma"], 0.25, w["N_rho"], w["M"], data=data_form)
+        trajectory["s=0.25"] = _bkw_trajectory(bz, p25, w, L)
+        p25.close()
+
     n64 = None
     if args.workload == "rk4_n32" and not args.no_n64:
         n64 = _measure_n64(args, bz, peaks, src, barrier, rank == 0 and not args.no_cpu_baseline)
@@ -818,6 +851,8 @@ def run_ours(args, w):
             "clocks": clocks, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
             "roofline": roof, "kernels_ms": {k: v[1] for k, v in kern.items()},
             "parity": parity, "cpu_baseline": cpu}
+    if trajectory is not None:
+        line["trajectory"] = trajectory
     if n64 is not None:
         line["n64"] = n64
     if other is not None:
@@ -919,6 +954,7 @@ def _measure_mixed(args, w, bz, plan32, f_host, L, R, st, peaks, src, barrier):
     bz.bz_plan_set_timing(pm, 0)
     value, ms = job_throughput(evals_per_step * args.steps, ms)
     errors = bz.bz_plan_device_errors(pm)
+    traj = _bkw_trajectory(bz, pm, w, L) if (is_rk and not args.no_trajectory) else None
     terms_per_launch = (w["N_rho"] * w["M"]) * evals_per_step * args.steps / max(n_launch, 1)
     avg_s = ms_k / 1e3 / max(n_launch, 1)
     tc = _tc_flops_per_term(N) * terms_per_launch / avg_s / 1e12
@@ -926,7 +962,7 @@ def _measure_mixed(args, w, bz, plan32, f_host, L, R, st, peaks, src, barrier):
     fft = _flops_per_term(N)["fused"] * terms_per_launch / avg_s / 1e12
     pm.close()
     return {"precision": "bf16x3", "value": value, "unit": "evals/s", "ms_per_step": ms / args.steps,
-            "rel_linf_vs_fp32_form": dev, "device_errors": errors,
+            "rel_linf_vs_fp32_form": dev, "device_errors": errors, "trajectory_s=0.5": traj,
             "gpu_launches": launches_per_step * args.steps,
             "roofline": {"bound": "tensor", "kernel": "k_mixed", "achieved": tc, "peak": tc_peak,
                          "unit": "TFLOP/s", "frac": tc / tc_peak,
@@ -1140,9 +1176,8 @@ def run_serve(args, w):
         return out
 
     def key(r, mixed):
-        data, prec = form(r, mixed)
-        batched = r["N"] <= 32 and (data == bz.BZ_DATA_COMPLEX or 32 % r["N"] == 0)
-        return (r["N"], r["M"], r["s"], data, prec, None if batched else r["gamma"])
+        data, prec = form(r, mixed)                      # every group is a batch: gamma per slot
+        return (r["N"], r["M"], r["s"], data, prec)
 
     passes = []
     for mixed in (False, True):
@@ -1169,7 +1204,15 @@ def run_serve(args, w):
         by_n = {}
         for (t, N) in tickets:
             by_n.setdefault(N, []).append(res[t][0].latency_s)
-        passes.append({"precision": "bf16x3 at N=32, fp32 elsewhere" if mixed else "fp32",
+        failed = {}
+        for (t, N), r in zip(tickets, trace):
+            st = res[t][0].status
+            if st != 0:
+                k = f"N={N},M={r['M']},gamma={r['gamma']},s={r['s']}"
+                failed.setdefault(k, {}).setdefault(str(st), 0)
+                failed[k][str(st)] += 1
+        passes.append({"failed": failed,
+                       "precision": "bf16x3 at N=32, fp32 elsewhere" if mixed else "fp32",
                        "requests_per_s": n_req / wall, "q_evals_per_s": 4 * steps / wall, "wall_s": wall,
                        "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99)),
                        "queue_p50_s": float(np.percentile(que, 50)), "queue_p99_s": float(np.percentile(que, 99)),
@@ -1204,6 +1247,8 @@ def main():
     ap.add_argument("--sphere-m", type=int, default=0, help="override the workload's sphere points")
     ap.add_argument("--no-other-form", action="store_true",
                     help="skip timing the other data form (complex beside real) on the same workload")
+    ap.add_argument("--no-trajectory", action="store_true",
+                    help="skip the 500-step BKW trajectory check of the default workload")
     ap.add_argument("--no-n64", action="store_true",
                     help="skip the N = 64 single-collide block measured beside the default workload")
     ap.add_argument("--no-mixed", action="store_true",

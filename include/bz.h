@@ -313,7 +313,10 @@ bz_status bz_checkpoint_read(const bz_plan *plan, const char *path, void *fhat, 
  * (host array, distinct, in [0, capacity)), so instances can join and leave between calls.
  * gamma enters only through c_p (eq. approxG): slot b uses alpha_p r_i^(gamma_b - gamma_plan).
  * An instance's result does not depend on which other slots are active in the call.
- * Requires a plan on the fused pipeline (N <= 32), else BZ_ERR_UNSUPPORTED.  The plan must
+ * On the fused pipeline (N <= 32) the active slots run as one batched kernel per RK stage; on
+ * the chunked pipeline (N = 24 real data, 48, 64, or on request) they step one after another
+ * through the plan's pipeline, each with its own gamma (padded and 2D plans, and fused
+ * real-data plans with FP32 h, give BZ_ERR_UNSUPPORTED).  The plan must
  * outlive the batch.  Not re-entrant across streams.
  * --------------------------------------------------------------------------------------- */
 typedef struct bz_batch bz_batch;

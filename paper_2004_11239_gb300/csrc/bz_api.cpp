@@ -32,12 +32,16 @@ void free_plan(bz::Plan &p) {
     cudaFree(p.rk); cudaFree(p.mom); cudaFree(p.part); cudaFree(p.fin64); cudaFree(p.scr64);
     cudaFree(p.wimg); cudaFree(p.dev_err); cudaFree(p.apair); cudaFree(p.fsym); cudaFree(p.fsym64);
     cudaFree(p.cpair); cudaFree(p.part_s); cudaFree(p.S_s); cudaFree(p.acc_s);
-    cudaFree(p.S2); cudaFree(p.S_s2); cudaFree(p.acc2); cudaFree(p.acc_s2);
+    for (int e = 0; e < bz::kExtraStreams; ++e) {
+        cudaFree(p.xS[e]); cudaFree(p.xS_s[e]); cudaFree(p.xacc[e]); cudaFree(p.xacc_s[e]);
+        if (p.xev_join[e]) cudaEventDestroy(p.xev_join[e]);
+        if (p.xst[e]) cudaStreamDestroy(p.xst[e]);
+        p.xS[e] = nullptr; p.xS_s[e] = nullptr; p.xacc[e] = nullptr; p.xacc_s[e] = nullptr;
+        p.xev_join[e] = nullptr; p.xst[e] = nullptr;
+    }
     if (p.ev_fork) cudaEventDestroy(p.ev_fork);
-    if (p.ev_join) cudaEventDestroy(p.ev_join);
-    if (p.st2) cudaStreamDestroy(p.st2);
-    p.S2 = nullptr; p.S_s2 = nullptr; p.acc2 = nullptr; p.acc_s2 = nullptr;
-    p.ev_fork = nullptr; p.ev_join = nullptr; p.st2 = nullptr;
+    p.ev_fork = nullptr;
+    p.xn = 0;
     p.wimg = nullptr; p.dev_err = nullptr; p.apair = nullptr; p.fsym = nullptr; p.fsym64 = nullptr;
     p.cpair = nullptr; p.part_s = nullptr; p.S_s = nullptr; p.acc_s = nullptr;
     p.part = nullptr; p.fin64 = nullptr; p.scr64 = nullptr; p.src = nullptr;
@@ -188,7 +192,7 @@ bz_status create(bz_plan **out, const bz_plan_desc *d) {
         // two waves of plane CTAs, within an L2-sized scratch; one wave per stream on two streams
         if (bz::collide_set_attributes(N) != cudaSuccess) { delete h; return BZ_ERR_CUDA; }
         chunk = bz::chunk_terms_for(N);
-        if (two_streams && chunk > 1) chunk /= 2;
+        if (two_streams && chunk > 1) chunk = (chunk + bz::kExtraStreams) / (1 + bz::kExtraStreams);
     }
     if (chunk > pl.P) chunk = pl.P;
     if (chunk > 65535) chunk = 65535;
@@ -263,27 +267,24 @@ bz_status create(bz_plan **out, const bz_plan_desc *d) {
         return BZ_ERR_UNSUPPORTED;
     }
     if (two_streams && !pl.use_fused) {
-        // second scratch and accumulators; without them the chunks stay on one stream
+        // the other lanes' scratch and accumulators; without them the chunks stay on one stream
         const size_t ns = (size_t)3 * N * N;
-        bool ok = dmalloc(&pl.S2, (size_t)pl.chunk * field) == BZ_OK && dmalloc(&pl.acc2, n3 * sizeof(double2)) == BZ_OK;
-        if (ok && pl.real)
-            ok = dmalloc(&pl.S_s2, (size_t)pl.chunk * ns * sizeof(float2)) == BZ_OK &&
-                 dmalloc(&pl.acc_s2, ns * sizeof(double2)) == BZ_OK;
-        ok = ok && cudaStreamCreateWithFlags(&pl.st2, cudaStreamNonBlocking) == cudaSuccess &&
-             cudaEventCreateWithFlags(&pl.ev_fork, cudaEventDisableTiming) == cudaSuccess &&
-             cudaEventCreateWithFlags(&pl.ev_join, cudaEventDisableTiming) == cudaSuccess;
-        if (ok) {
-            pl.ws_bytes += (size_t)pl.chunk * field + n3 * sizeof(double2) +
-                           (pl.real ? (size_t)pl.chunk * ns * sizeof(float2) + ns * sizeof(double2) : 0);
-        } else {
-            cudaGetLastError();
-            cudaFree(pl.S2); cudaFree(pl.acc2); cudaFree(pl.S_s2); cudaFree(pl.acc_s2);
-            if (pl.ev_fork) cudaEventDestroy(pl.ev_fork);
-            if (pl.ev_join) cudaEventDestroy(pl.ev_join);
-            if (pl.st2) cudaStreamDestroy(pl.st2);
-            pl.S2 = nullptr; pl.acc2 = nullptr; pl.S_s2 = nullptr; pl.acc_s2 = nullptr;
-            pl.ev_fork = nullptr; pl.ev_join = nullptr; pl.st2 = nullptr;
+        bool ok = cudaEventCreateWithFlags(&pl.ev_fork, cudaEventDisableTiming) == cudaSuccess;
+        for (int e = 0; ok && e < bz::kExtraStreams; ++e) {
+            ok = dmalloc(&pl.xS[e], (size_t)pl.chunk * field) == BZ_OK &&
+                 dmalloc(&pl.xacc[e], n3 * sizeof(double2)) == BZ_OK;
+            if (ok && pl.real)
+                ok = dmalloc(&pl.xS_s[e], (size_t)pl.chunk * ns * sizeof(float2)) == BZ_OK &&
+                     dmalloc(&pl.xacc_s[e], ns * sizeof(double2)) == BZ_OK;
+            ok = ok && cudaStreamCreateWithFlags(&pl.xst[e], cudaStreamNonBlocking) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&pl.xev_join[e], cudaEventDisableTiming) == cudaSuccess;
+            if (ok) {
+                pl.xn = e + 1;
+                pl.ws_bytes += (size_t)pl.chunk * field + n3 * sizeof(double2) +
+                               (pl.real ? (size_t)pl.chunk * ns * sizeof(float2) + ns * sizeof(double2) : 0);
+            }
         }
+        if (!ok) cudaGetLastError();   // the lanes that were set up stay in use
     }
     *out = h;
     return BZ_OK;

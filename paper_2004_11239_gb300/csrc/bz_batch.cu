@@ -45,6 +45,7 @@ struct bz_batch {
     cudaStream_t cap_stream = nullptr;
     std::map<double, cudaGraphExec_t> graphs;
     int last_launches = 0;
+    bool chunked = false;           // the plan runs the chunked pipeline: slots step one by one
 };
 
 namespace bz {
@@ -346,14 +347,66 @@ int autotune_tb(bz_batch &B, int trial, cudaStream_t st) {
 
 using namespace bz;
 
+namespace bz {
+namespace {
+
+bz_status check_slots(const bz_batch &B, int count, const int *slots) {
+    if (count < 0 || count > B.capacity || (count > 0 && !slots)) return BZ_ERR_ARG;
+    std::vector<char> seen(B.capacity, 0);
+    for (int b = 0; b < count; ++b) {
+        if (slots[b] < 0 || slots[b] >= B.capacity || seen[slots[b]]) return BZ_ERR_ARG;
+        seen[slots[b]] = 1;
+    }
+    return BZ_OK;
+}
+
+// Chunked plans: each active slot through the plan's pipeline with the slot's radial scale.
+bz_status chunked_collide(bz_batch &B, int count, const int *slots, const void *fhat, void *Qhat, int dtype,
+                          cudaStream_t st) {
+    bz_status s = check_slots(B, count, slots);
+    if (s != BZ_OK) return s;
+    Plan &pl = *B.pl;
+    const size_t bytes = (size_t)pl.N * pl.N * pl.N * (dtype == BZ_C128 ? sizeof(double2) : sizeof(float2));
+    int nl = 0;
+    for (int b = 0; b < count && s == BZ_OK; ++b) {
+        pl.gsc_cur = B.gsc + (size_t)slots[b] * pl.N_rho;
+        s = collide_range(pl, 0, pl.P, (const char *)fhat + slots[b] * bytes, dtype, st, &nl);
+        if (s == BZ_OK) s = write_output(pl, (char *)Qhat + slots[b] * bytes, dtype, st, &nl);
+    }
+    pl.gsc_cur = nullptr;
+    pl.src = nullptr;
+    B.last_launches = nl;
+    return s;
+}
+
+bz_status chunked_step_rk(bz_batch &B, int count, const int *slots, void *fhat, int dtype, double dt, int nsteps,
+                          cudaStream_t st) {
+    bz_status s = check_slots(B, count, slots);
+    if (s != BZ_OK) return s;
+    Plan &pl = *B.pl;
+    const size_t bytes = (size_t)pl.N * pl.N * pl.N * (dtype == BZ_C128 ? sizeof(double2) : sizeof(float2));
+    int nl = 0;
+    for (int b = 0; b < count && s == BZ_OK; ++b) {
+        pl.gsc_cur = B.gsc + (size_t)slots[b] * pl.N_rho;
+        s = rk4_steps(pl, (char *)fhat + slots[b] * bytes, dtype, dt, nsteps, st, &nl);
+    }
+    pl.gsc_cur = nullptr;
+    pl.src = nullptr;
+    B.last_launches = nl;
+    return s;
+}
+
+}  // namespace
+}  // namespace bz
+
 extern "C" {
 
 bz_status bz_batch_create(bz_batch **out, const bz_plan *plan, int capacity, int terms_per_item) {
     if (!out || !plan || capacity < 1) return BZ_ERR_ARG;
     *out = nullptr;
     Plan *pl = const_cast<Plan *>(plan_internal(plan));
-    // batches: fused kernel (N <= 32), circular; the real-data form with h formed in FP64
-    if (!pl->use_fused || pl->Nin || (pl->real && !pl->h_fp64)) return BZ_ERR_UNSUPPORTED;
+    // batches: circular 3D plans; on the fused pipeline the real-data form needs h formed in FP64
+    if (pl->Nin || pl->dim == 2 || (pl->use_fused && pl->real && !pl->h_fp64)) return BZ_ERR_UNSUPPORTED;
     bz_batch *B = new (std::nothrow) bz_batch();
     if (!B) return BZ_ERR_OOM;
     B->pl = pl;
@@ -363,6 +416,20 @@ bz_status bz_batch_create(bz_batch **out, const bz_plan *plan, int capacity, int
     const size_t n3 = (size_t)pl->N * pl->N * pl->N;
     const size_t field = n3 * sizeof(float2);
     auto fail = [&](bz_status s) { free_batch(B); delete B; return s; };
+    if (!pl->use_fused) {
+        // chunked plans step their slots one after another through the plan's own pipeline
+        // (each chunk kernel already fills the GPU); only the radial scales live in the batch
+        B->chunked = true;
+        if (cudaMalloc(&B->gsc, (size_t)capacity * pl->N_rho * sizeof(float)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(BZ_ERR_OOM);
+        }
+        if (upload_gsc(*B) != BZ_OK) return fail(BZ_ERR_CUDA);
+        B->TB = B->units;
+        B->nblk = 1;
+        *out = B;
+        return BZ_OK;
+    }
     if (cudaMalloc(&B->gsc, (size_t)capacity * pl->N_rho * sizeof(float)) != cudaSuccess ||
         cudaMalloc(&B->fin, (size_t)capacity * field) != cudaSuccess ||
         cudaMalloc(&B->f0, (size_t)capacity * n3 * sizeof(double2)) != cudaSuccess ||
@@ -440,6 +507,7 @@ bz_status bz_batch_collide(bz_batch *batch, int count, const int *slots, const v
     if (dtype != BZ_C64 && dtype != BZ_C128) return BZ_ERR_ARG;
     bz_batch &B = *batch;
     cudaStream_t st = (cudaStream_t)stream;
+    if (B.chunked) return chunked_collide(B, count, slots, fhat, Qhat, dtype, st);
     bz_status s = stage_slots(B, count, slots, st);
     if (s != BZ_OK) return s;
     const int n3 = B.pl->N * B.pl->N * B.pl->N;
@@ -468,6 +536,7 @@ bz_status bz_batch_step_rk(bz_batch *batch, int count, const int *slots, void *f
     if (dtype != BZ_C64 && dtype != BZ_C128) return BZ_ERR_ARG;
     bz_batch &B = *batch;
     cudaStream_t st = (cudaStream_t)stream;
+    if (B.chunked) return chunked_step_rk(B, count, slots, fhat, dtype, dt, nsteps, st);
     bz_status s = stage_slots(B, count, slots, st);
     if (s != BZ_OK) return s;
     const int n3 = B.pl->N * B.pl->N * B.pl->N;

@@ -16,7 +16,8 @@
 //   transform along k3 (rows) then k2 (columns), result to S[t][k1][j2][j3].
 // k_plane_fwd64: forward transform along j2 (columns, loaded from S) then j3 (rows), times the
 //   weight alpha_p (or the pair table A), whose 8 values per thread are loaded at the start so
-//   the HBM stream overlaps the transforms; result to S; the pair form also writes the Nyquist
+//   the HBM stream overlaps the transforms (a batch slot's radial scale, if given, multiplies
+//   the transformed field); result to S; the pair form also writes the Nyquist
 //   sums X = C Z of the plane (family layout [3][N][N], every entry of this k1 written).
 #include "bz_fft.cuh"
 #include "bz_internal.h"
@@ -130,7 +131,7 @@ k_plane_inv64(const float2 *__restrict__ fin, const float2 *__restrict__ tw, flo
 template <bool PAIR>
 __global__ void __launch_bounds__(T64, 2)
 k_plane_fwd64(float2 *__restrict__ S, const float2 *__restrict__ alpha, int p0, const float2 *__restrict__ cpair,
-              float2 *__restrict__ Ss) {
+              float2 *__restrict__ Ss, const float *__restrict__ gsc, int M) {
     extern __shared__ float2 sm[];
     float2 *tile = sm;
     float2 *w = sm + N64 * RP;
@@ -165,6 +166,11 @@ k_plane_fwd64(float2 *__restrict__ S, const float2 *__restrict__ alpha, int p0, 
     #pragma unroll
     for (int n1 = 0; n1 < 8; ++n1) x[n1] = tile[r * RP + 8 * n1 + n2];
     row_pass<-1>(x, tile, r, n2, w);                      // x[k2] = Z(k2 = r, k3 = n2 + 8 k2)
+    if (gsc) {                                            // a batch slot's radial scale (a pair shares its node)
+        const float sc = gsc[(PAIR ? 2 * (p0 + t) : p0 + t) / M];
+        #pragma unroll
+        for (int k2 = 0; k2 < 8; ++k2) x[k2] = cscale(x[k2], sc);
+    }
     float2 *o = pl + (size_t)r * N64 + n2;
     #pragma unroll
     for (int k2 = 0; k2 < 8; ++k2) o[8 * k2] = cmul(x[k2], a[k2]);
@@ -212,10 +218,10 @@ void plane_inv64(const float2 *fin, const float2 *tw, float2 *S, int p0, int T, 
     else k_plane_inv64<false><<<dim3(N64, T), T64, kInvSmem, st>>>(fin, tw, S, p0, use_tw);
 }
 
-void plane_fwd64(float2 *S, const float2 *alpha, int p0, int T, const float2 *cpair, float2 *Ss, bool pair,
-                 cudaStream_t st) {
-    if (pair) k_plane_fwd64<true><<<dim3(N64, T), T64, kFwdSmem, st>>>(S, alpha, p0, cpair, Ss);
-    else k_plane_fwd64<false><<<dim3(N64, T), T64, kFwdSmem, st>>>(S, alpha, p0, nullptr, nullptr);
+void plane_fwd64(float2 *S, const float2 *alpha, int p0, int T, const float2 *cpair, float2 *Ss, const float *gsc,
+                 int M, bool pair, cudaStream_t st) {
+    if (pair) k_plane_fwd64<true><<<dim3(N64, T), T64, kFwdSmem, st>>>(S, alpha, p0, cpair, Ss, gsc, M);
+    else k_plane_fwd64<false><<<dim3(N64, T), T64, kFwdSmem, st>>>(S, alpha, p0, nullptr, nullptr, gsc, M);
 }
 
 }  // namespace bz

@@ -1,8 +1,8 @@
 // The per-term pipeline of eq. realQ (Sec. 4) in FP32 with FP64 accumulation over terms.
 //
 // For each chunk of T terms, four kernels run over a scratch buffer S[T][N^3] sized to
-// stay in L2 (where the plan has a second stream, odd chunks run on it over a second scratch
-// and accumulator, overlapping the even chunks; the two sums are added at the end):
+// stay in L2 (where the plan has more streams, chunk i runs on stream i % lanes over that
+// stream's scratch and accumulator, overlapping the others; the sums are added at the end):
 //   plane_inv  (planes k1):  S = IFFT_{axes 3,2}( beta_p(m) fhat_m )       twiddle + 2 axes
 //   pencil     (lines k1):   S = FFT_1( h . IFFT_1(S) )                     product in registers
 //   plane_fwd  (planes k1):  S = alpha_p . FFT_{axes 3,2}(S)                 weight in the epilogue
@@ -122,11 +122,13 @@ k_pencil(float2 *__restrict__ S, const float2 *__restrict__ h, float2 *__restric
 // plane_fwd: forward transform along axes 2 and 3, times alpha_p, in place.
 // ---------------------------------------------------------------------------------------
 // PAIR (BZ_DATA_REAL): alpha is the pair table A, and the chunk's Nyquist sums X = C Z go to
-// Ss[t][3][N][N] (family layout; every entry written, zero where C is zero).
+// Ss[t][3][N][N] (family layout; every entry written, zero where C is zero).  gsc (or null):
+// a batch slot's radial scale r_i^(gamma_slot - gamma_plan) per radial node i of the M-point
+// sphere rule (a pair shares its node), applied to the transformed field.
 template <int N, bool PAIR = false>
 __global__ void __launch_bounds__(Cfg<N>::THREADS, Cfg<N>::MINB)
 k_plane_fwd(float2 *__restrict__ S, const float2 *__restrict__ alpha, int p0, const float2 *__restrict__ cpair = nullptr,
-            float2 *__restrict__ Ss = nullptr) {
+            float2 *__restrict__ Ss = nullptr, const float *__restrict__ gsc = nullptr, int M = 1) {
     constexpr int PPC = Cfg<N>::PPC, LD = Cfg<N>::LD;
     extern __shared__ float2 sm[];
     const int lane = threadIdx.x % N, pid = threadIdx.x / N;
@@ -150,17 +152,18 @@ k_plane_fwd(float2 *__restrict__ S, const float2 *__restrict__ alpha, int p0, co
     __syncthreads();
     #pragma unroll
     for (int i = 0; i < N; ++i) x[i] = al[i * N + lane];    // every weight load in flight at once
+    const float sc = gsc ? gsc[(PAIR ? 2 * (p0 + t) : p0 + t) / M] : 1.f;
     #pragma unroll
-    for (int i = 0; i < N; ++i) pl[i * N + lane] = cmul(s[i * LD + lane], x[i]);
+    for (int i = 0; i < N; ++i) pl[i * N + lane] = cscale(cmul(s[i * LD + lane], x[i]), sc);
     if constexpr (PAIR) {
         const float2 *cq = cpair + (size_t)(p0 + t) * 3 * N * N;
         float2 *xs = Ss + (size_t)t * 3 * N * N;
         // family k2 = -N/2 at [k1][k3 = lane]; family k3 = -N/2 at [k1][k2 = lane]
-        xs[N * N + k1 * N + lane] = cmul(s[(N / 2) * LD + lane], cq[N * N + k1 * N + lane]);
-        xs[2 * N * N + k1 * N + lane] = cmul(s[lane * LD + N / 2], cq[2 * N * N + k1 * N + lane]);
+        xs[N * N + k1 * N + lane] = cscale(cmul(s[(N / 2) * LD + lane], cq[N * N + k1 * N + lane]), sc);
+        xs[2 * N * N + k1 * N + lane] = cscale(cmul(s[lane * LD + N / 2], cq[2 * N * N + k1 * N + lane]), sc);
         if (k1 == N / 2) {                                    // the plane k1 = -N/2: [k2][k3]
             #pragma unroll 4
-            for (int i = 0; i < N; ++i) xs[i * N + lane] = cmul(s[i * LD + lane], cq[i * N + lane]);
+            for (int i = 0; i < N; ++i) xs[i * N + lane] = cscale(cmul(s[i * LD + lane], cq[i * N + lane]), sc);
         }
     }
 }
@@ -379,10 +382,11 @@ static void plane_inv(const float2 *fin, const float2 *tw, float2 *S, int p0, in
 }
 
 template <int N, bool PAIR>
-static void plane_fwd(float2 *S, const float2 *alpha, int p0, int T, const float2 *cpair, float2 *Ss, cudaStream_t st) {
+static void plane_fwd(float2 *S, const float2 *alpha, int p0, int T, const float2 *cpair, float2 *Ss, const float *gsc,
+                      int M, cudaStream_t st) {
     constexpr int PPC = Cfg<N>::PPC;
-    if constexpr (N == 64) plane_fwd64(S, alpha, p0, T, cpair, Ss, PAIR, st);
-    else k_plane_fwd<N, PAIR><<<dim3(N / PPC, T), Cfg<N>::THREADS, Cfg<N>::SMEM, st>>>(S, alpha, p0, cpair, Ss);
+    if constexpr (N == 64) plane_fwd64(S, alpha, p0, T, cpair, Ss, gsc, M, PAIR, st);
+    else k_plane_fwd<N, PAIR><<<dim3(N / PPC, T), Cfg<N>::THREADS, Cfg<N>::SMEM, st>>>(S, alpha, p0, cpair, Ss, gsc, M);
 }
 
 // BZ_DATA_REAL: the Hermitian part of the input (sym_input) feeds h and the pair passes; the
@@ -403,19 +407,23 @@ static bz_status run_chunks_real(Plan &pl, int p0, int p1, cudaStream_t st, int 
     BZ_CUDA_TRY(cudaMemsetAsync(pl.acc_s, 0, (size_t)ns * sizeof(double2), st));
     tm_end(pl, st, TK_OTHER);
     int nl = 3;
-    const bool two = pl.st2 && (u1 - u0) > chunk;
-    if (two) {
+    // lanes: as many streams as chunks, up to 1 + pl.xn
+    const int nchunks = (u1 - u0 + chunk - 1) / chunk;
+    const int lanes = 1 + (pl.xn < nchunks - 1 ? pl.xn : (nchunks > 1 ? nchunks - 1 : 0));
+    if (lanes > 1) {
         BZ_CUDA_TRY(cudaEventRecord(pl.ev_fork, st));
-        BZ_CUDA_TRY(cudaStreamWaitEvent(pl.st2, pl.ev_fork, 0));
-        BZ_CUDA_TRY(cudaMemsetAsync(pl.acc2, 0, (size_t)n3 * sizeof(double2), pl.st2));
-        BZ_CUDA_TRY(cudaMemsetAsync(pl.acc_s2, 0, (size_t)ns * sizeof(double2), pl.st2));
+        for (int e = 0; e + 1 < lanes; ++e) {
+            BZ_CUDA_TRY(cudaStreamWaitEvent(pl.xst[e], pl.ev_fork, 0));
+            BZ_CUDA_TRY(cudaMemsetAsync(pl.xacc[e], 0, (size_t)n3 * sizeof(double2), pl.xst[e]));
+            BZ_CUDA_TRY(cudaMemsetAsync(pl.xacc_s[e], 0, (size_t)ns * sizeof(double2), pl.xst[e]));
+        }
     }
     for (int c0 = u0, i = 0; c0 < u1; c0 += chunk, ++i) {
         const int T = (u1 - c0) < chunk ? (u1 - c0) : chunk;
-        const bool odd = two && (i & 1);
-        cudaStream_t cs = odd ? pl.st2 : st;
-        float2 *S = odd ? pl.S2 : pl.S, *Ss = odd ? pl.S_s2 : pl.S_s;
-        double2 *acc = odd ? pl.acc2 : pl.acc, *acc_s = odd ? pl.acc_s2 : pl.acc_s;
+        const int ln = i % lanes;
+        cudaStream_t cs = ln ? pl.xst[ln - 1] : st;
+        float2 *S = ln ? pl.xS[ln - 1] : pl.S, *Ss = ln ? pl.xS_s[ln - 1] : pl.S_s;
+        double2 *acc = ln ? pl.xacc[ln - 1] : pl.acc, *acc_s = ln ? pl.xacc_s[ln - 1] : pl.acc_s;
         tm_begin(pl, cs);
         plane_inv<N, true>(pl.fsym, pl.tw, S, c0, T, 1, cs);
         tm_end(pl, cs, TK_PLANE_INV);
@@ -423,19 +431,19 @@ static bz_status run_chunks_real(Plan &pl, int p0, int p1, cudaStream_t st, int 
         k_pencil<N, 2><<<dim3((N * N + 127) / 128, T), 128, 0, cs>>>(S, pl.h, nullptr);
         tm_end(pl, cs, TK_PENCIL);
         tm_begin(pl, cs);
-        plane_fwd<N, true>(S, pl.apair, c0, T, pl.cpair, Ss, cs);
+        plane_fwd<N, true>(S, pl.apair, c0, T, pl.cpair, Ss, pl.gsc_cur, pl.M, cs);
         tm_end(pl, cs, TK_PLANE_FWD);
         tm_begin(pl, cs);
         k_reduce<<<(n3 / 2 + ns / 2 + 255) / 256, 256, 0, cs>>>(S, T, n3, acc, Ss, ns, acc_s);
         tm_end(pl, cs, TK_REDUCE);
         nl += 4;
     }
-    if (two) {
-        // the second stream's sums join the first's in a fixed order
-        BZ_CUDA_TRY(cudaEventRecord(pl.ev_join, pl.st2));
-        BZ_CUDA_TRY(cudaStreamWaitEvent(st, pl.ev_join, 0));
-        k_acc_add<<<(n3 + 255) / 256, 256, 0, st>>>(pl.acc, pl.acc2, n3);
-        k_acc_add<<<(ns + 255) / 256, 256, 0, st>>>(pl.acc_s, pl.acc_s2, ns);
+    for (int e = 0; e + 1 < lanes; ++e) {
+        // the other lanes' sums join the first's in a fixed order
+        BZ_CUDA_TRY(cudaEventRecord(pl.xev_join[e], pl.xst[e]));
+        BZ_CUDA_TRY(cudaStreamWaitEvent(st, pl.xev_join[e], 0));
+        k_acc_add<<<(n3 + 255) / 256, 256, 0, st>>>(pl.acc, pl.xacc[e], n3);
+        k_acc_add<<<(ns + 255) / 256, 256, 0, st>>>(pl.acc_s, pl.xacc_s[e], ns);
         nl += 2;
     }
     tm_begin(pl, st);
@@ -459,18 +467,21 @@ static bz_status run_chunks(Plan &pl, int p0, int p1, cudaStream_t st, int *laun
     BZ_CUDA_TRY(cudaMemsetAsync(pl.acc, 0, (size_t)n3 * sizeof(double2), st));
     tm_end(pl, st, TK_OTHER);
     int nl = 2;
-    const bool two = pl.st2 && (p1 - p0) > pl.chunk;
-    if (two) {
+    const int nchunks = (p1 - p0 + pl.chunk - 1) / pl.chunk;
+    const int lanes = 1 + (pl.xn < nchunks - 1 ? pl.xn : (nchunks > 1 ? nchunks - 1 : 0));
+    if (lanes > 1) {
         BZ_CUDA_TRY(cudaEventRecord(pl.ev_fork, st));
-        BZ_CUDA_TRY(cudaStreamWaitEvent(pl.st2, pl.ev_fork, 0));
-        BZ_CUDA_TRY(cudaMemsetAsync(pl.acc2, 0, (size_t)n3 * sizeof(double2), pl.st2));
+        for (int e = 0; e + 1 < lanes; ++e) {
+            BZ_CUDA_TRY(cudaStreamWaitEvent(pl.xst[e], pl.ev_fork, 0));
+            BZ_CUDA_TRY(cudaMemsetAsync(pl.xacc[e], 0, (size_t)n3 * sizeof(double2), pl.xst[e]));
+        }
     }
     for (int c0 = p0, i = 0; c0 < p1; c0 += pl.chunk, ++i) {
         const int T = (p1 - c0) < pl.chunk ? (p1 - c0) : pl.chunk;
-        const bool odd = two && (i & 1);
-        cudaStream_t cs = odd ? pl.st2 : st;
-        float2 *S = odd ? pl.S2 : pl.S;
-        double2 *acc = odd ? pl.acc2 : pl.acc;
+        const int ln = i % lanes;
+        cudaStream_t cs = ln ? pl.xst[ln - 1] : st;
+        float2 *S = ln ? pl.xS[ln - 1] : pl.S;
+        double2 *acc = ln ? pl.xacc[ln - 1] : pl.acc;
         tm_begin(pl, cs);
         plane_inv<N, false>(pl.fin, pl.tw, S, c0, T, 1, cs);
         tm_end(pl, cs, TK_PLANE_INV);
@@ -478,17 +489,17 @@ static bz_status run_chunks(Plan &pl, int p0, int p1, cudaStream_t st, int *laun
         k_pencil<N, 1><<<dim3((N * N + 127) / 128, T), 128, 0, cs>>>(S, pl.h, nullptr);
         tm_end(pl, cs, TK_PENCIL);
         tm_begin(pl, cs);
-        plane_fwd<N, false>(S, pl.alpha, c0, T, nullptr, nullptr, cs);
+        plane_fwd<N, false>(S, pl.alpha, c0, T, nullptr, nullptr, pl.gsc_cur, pl.M, cs);
         tm_end(pl, cs, TK_PLANE_FWD);
         tm_begin(pl, cs);
         k_reduce<<<(n3 / 2 + 255) / 256, 256, 0, cs>>>(S, T, n3, acc);
         tm_end(pl, cs, TK_REDUCE);
         nl += 4;
     }
-    if (two) {
-        BZ_CUDA_TRY(cudaEventRecord(pl.ev_join, pl.st2));
-        BZ_CUDA_TRY(cudaStreamWaitEvent(st, pl.ev_join, 0));
-        k_acc_add<<<(n3 + 255) / 256, 256, 0, st>>>(pl.acc, pl.acc2, n3);
+    for (int e = 0; e + 1 < lanes; ++e) {
+        BZ_CUDA_TRY(cudaEventRecord(pl.xev_join[e], pl.xst[e]));
+        BZ_CUDA_TRY(cudaStreamWaitEvent(st, pl.xev_join[e], 0));
+        k_acc_add<<<(n3 + 255) / 256, 256, 0, st>>>(pl.acc, pl.xacc[e], n3);
         ++nl;
     }
     BZ_CUDA_TRY(cudaGetLastError());

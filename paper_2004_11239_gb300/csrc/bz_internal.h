@@ -9,6 +9,10 @@
 
 #include "../../include/bz.h"
 
+#ifndef EXTRA_STREAMS
+#define EXTRA_STREAMS 1
+#endif
+
 namespace bz {
 
 // One radial node's part-II theta rule (Sec. 4.1): nodes t_n on [eps, pi] with
@@ -32,6 +36,9 @@ struct Timing {
     double ms[TK_COUNT] = {0, 0, 0, 0, 0, 0};
     long n[TK_COUNT] = {0, 0, 0, 0, 0, 0};
 };
+
+// Streams of the chunked pipeline beside the caller's.
+constexpr int kExtraStreams = EXTRA_STREAMS;
 
 struct Plan {
     // parameters
@@ -80,16 +87,20 @@ struct Plan {
     float2 *part_s = nullptr;       // [fused_G][3][N][N] per-item sums X on the Nyquist planes
     float2 *S_s = nullptr;          // chunked pipeline: [chunk][3][N][N] the chunk's Nyquist sums
     double2 *acc_s = nullptr;       // chunked pipeline: [3][N][N] FP64 sum of X
-    // chunked pipeline on two streams: odd chunks run on st2 over their own scratch and
-    // accumulators, overlapping the even chunks on the caller's stream
-    cudaStream_t st2 = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-    float2 *S2 = nullptr;           // [chunk][N^3]
-    float2 *S_s2 = nullptr;         // [chunk][3][N][N] (BZ_DATA_REAL)
-    double2 *acc2 = nullptr;        // [N^3]
-    double2 *acc_s2 = nullptr;      // [3][N][N] (BZ_DATA_REAL)
+    // chunked pipeline on several streams: chunk i runs on lane i % (1 + xn), lane 0 the
+    // caller's stream over S / acc, lane e > 0 the plan's stream xst[e - 1] over its own
+    // scratch and accumulators; the lanes overlap and their sums are added at the end
+    int xn = 0;                                      // extra streams in use
+    cudaStream_t xst[kExtraStreams] = {};
+    cudaEvent_t ev_fork = nullptr, xev_join[kExtraStreams] = {};
+    float2 *xS[kExtraStreams] = {};                  // [chunk][N^3]
+    float2 *xS_s[kExtraStreams] = {};                // [chunk][3][N][N] (BZ_DATA_REAL)
+    double2 *xacc[kExtraStreams] = {};               // [N^3]
+    double2 *xacc_s[kExtraStreams] = {};             // [3][N][N] (BZ_DATA_REAL)
     float2 *fsym = nullptr;         // [N^3] Hermitian part of fhat, Nyquist planes zero (FP32)
     double2 *fsym64 = nullptr;      // [N^3] the same in FP64 (source of h)
+    const float *gsc_cur = nullptr; // chunked pipeline inside a batch call: the slot's radial scale
+                                    // r_i^(gamma_slot - gamma) per radial node (null: none)
     int *dev_err = nullptr;         // device flags: [0] a bounded wait of a kernel gave up,
                                     // [1] a result written since the last check held NaN or Inf
     size_t ws_bytes = 0;
@@ -191,8 +202,8 @@ cudaError_t collide_set_attributes(int N);
 cudaError_t chunk64_set_attributes();
 void plane_inv64(const float2 *fin, const float2 *tw, float2 *S, int p0, int T, int use_tw, bool pair,
                  cudaStream_t st);
-void plane_fwd64(float2 *S, const float2 *alpha, int p0, int T, const float2 *cpair, float2 *Ss, bool pair,
-                 cudaStream_t st);
+void plane_fwd64(float2 *S, const float2 *alpha, int p0, int T, const float2 *cpair, float2 *Ss, const float *gsc,
+                 int M, bool pair, cudaStream_t st);
 void reduce_parts(const float2 *part, int nblk, int n, double2 *acc, cudaStream_t st);
 int chunk_terms_for(int N);          // after collide_set_attributes(N)
 int supported_N(int N);

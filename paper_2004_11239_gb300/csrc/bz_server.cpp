@@ -2,9 +2,10 @@
 // operator) of mixed N, (gamma, s), data form and precision.
 //
 // A worker thread owns the device work.  Requests with the same plan geometry, data form,
-// precision and dt form a group with its own plan, stream and completion event; N <= 32 groups
-// (fused pipeline) step all their active slots with one batched call (bz_batch_step_rk), the
-// others step each request through the group's plan.  The worker loops over the groups:
+// precision and dt form a group with its own plan, batch (gamma per slot), stream and
+// completion event; a group steps all its active slots with one bz_batch_step_rk call (one
+// batched kernel per RK stage on the fused pipeline, the slots one after another on the chunked
+// one).  The worker loops over the groups:
 //   - admission, in arrival order, while the HBM budget and group slots allow (a request whose
 //     own footprint exceeds the whole budget fails with BZ_ERR_OOM; one queued longer than its
 //     max_queue_s fails with BZ_ERR_TIMEOUT); a request admitted to a group whose step is in
@@ -61,18 +62,16 @@ struct Request {
     int status = BZ_ERR_BUSY;          // BZ_ERR_BUSY while queued or running
     int slot = -1;
     struct Group *group = nullptr;
-    double *state_single = nullptr;    // large-N requests: own device state (c128)
     Clock::time_point t_submit, t_admit, t_done;
 };
 
 struct Group {
     Key key{};
     bz_plan *plan = nullptr;
-    bz_batch *batch = nullptr;         // batched groups (fused pipeline)
-    double2 *state = nullptr;          // [capacity][N^3] c128 (batched groups)
+    bz_batch *batch = nullptr;
+    double2 *state = nullptr;          // [capacity][N^3] c128
     int capacity = 0;
     std::vector<Request *> slots;      // per slot (nullptr = free)
-    std::vector<Request *> singles;    // unbatched groups: the active requests
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;        // recorded after each step's launches
     bool inflight = false;
@@ -81,7 +80,7 @@ struct Group {
     size_t bytes = 0;
     Clock::time_point last_used;
     int active() const {
-        int n = (int)singles.size();
+        int n = 0;
         for (auto *r : slots) n += r != nullptr;
         return n;
     }
@@ -109,10 +108,11 @@ struct bz_server {
 
 namespace {
 
-// Groups whose plan runs the fused pipeline step their slots as one batch.
-bool batched(const bz_request &r) {
+// Groups on the fused pipeline (N <= 32; N | 32 for the real-data form) keep per-slot working
+// arrays in their batch; on the chunked pipeline the batch holds only the slots' radial scales.
+bool fused(const bz_request &r) {
     if (r.N > 32) return false;
-    return r.data != BZ_DATA_REAL || 32 % r.N == 0;    // the real-data form is fused for N | 32
+    return r.data != BZ_DATA_REAL || 32 % r.N == 0;
 }
 
 size_t plan_bytes(const bz_request &r) {
@@ -127,11 +127,12 @@ size_t batch_bytes(const bz_request &r, int capacity) {
     const size_t n3 = (size_t)r.N * r.N * r.N;
     const size_t P = (size_t)r.N_rho * r.M;
     const size_t nblk_max = (P + 15) / 16;
-    return (size_t)capacity * n3 * (8 + 8 * nblk_max + 32 + 16 + (r.data == BZ_DATA_REAL ? 8 : 0));
+    if (!fused(r)) return (size_t)capacity * n3 * 16;                       // the slots' state
+    return (size_t)capacity * n3 * (8 + 8 * nblk_max + 32 + 16 + 16 + (r.data == BZ_DATA_REAL ? 8 : 0));
 }
 
 Key key_of(const bz_request &r) {
-    Key k{r.N, r.N_rho, r.M, r.kernel, r.data, r.precision, r.L, r.R, r.s, r.dt, batched(r) ? 0.0 : r.gamma};
+    Key k{r.N, r.N_rho, r.M, r.kernel, r.data, r.precision, r.L, r.R, r.s, r.dt, 0.0};
     return k;
 }
 
@@ -163,8 +164,8 @@ Group *get_group(bz_server *S, const bz_request &r, int *err) {
     Key k = key_of(r);
     auto it = S->groups.find(k);
     if (it != S->groups.end()) return it->second.get();
-    const int cap = batched(r) ? S->max_batch : 0;
-    const size_t need = plan_bytes(r) + (cap ? batch_bytes(r, cap) : 0);
+    const int cap = S->max_batch;
+    const size_t need = plan_bytes(r) + batch_bytes(r, cap);
     if (need > S->budget) { *err = BZ_ERR_OOM; return nullptr; }
     if (!make_room(S, need)) { *err = BZ_ERR_BUSY; return nullptr; }
     std::unique_ptr<Group> g(new Group());
@@ -183,7 +184,7 @@ Group *get_group(bz_server *S, const bz_request &r, int *err) {
         *err = BZ_ERR_CUDA;
         return nullptr;
     }
-    if (cap) {
+    {
         st = bz_batch_create(&g->batch, g->plan, cap, S->terms_per_item);
         const size_t n3 = (size_t)r.N * r.N * r.N;
         if (st == BZ_OK && cudaMalloc(&g->state, (size_t)cap * n3 * sizeof(double2)) != cudaSuccess) st = BZ_ERR_OOM;
@@ -229,36 +230,20 @@ void admit(bz_server *S) {
             continue;
         }
         const size_t n3 = (size_t)r.N * r.N * r.N;
-        if (g->batch) {
-            int slot = -1;
-            for (int i = 0; i < g->capacity; ++i)
-                if (!g->slots[i]) { slot = i; break; }
-            if (slot < 0) return;                          // group full: wait for a slot
-            if (bz_batch_set_gamma(g->batch, slot, r.gamma) != BZ_OK ||
-                cudaMemcpyAsync(g->state + (size_t)slot * n3, q->input.data(), n3 * sizeof(double2),
-                                cudaMemcpyHostToDevice, g->stream) != cudaSuccess) {
-                q->status = BZ_ERR_CUDA;
-                q->t_done = Clock::now();
-                S->queue.pop_front();
-                continue;
-            }
-            g->slots[slot] = q;
-            q->slot = slot;
-        } else {
-            const size_t bytes = n3 * sizeof(double2);
-            if (S->used + bytes > S->budget && !make_room(S, bytes)) return;
-            if (cudaMalloc(&q->state_single, bytes) != cudaSuccess ||
-                cudaMemcpyAsync(q->state_single, q->input.data(), bytes, cudaMemcpyHostToDevice, g->stream) !=
-                    cudaSuccess) {
-                cudaGetLastError();
-                q->status = BZ_ERR_OOM;
-                q->t_done = Clock::now();
-                S->queue.pop_front();
-                continue;
-            }
-            S->used += bytes;
-            g->singles.push_back(q);
+        int slot = -1;
+        for (int k = 0; k < g->capacity; ++k)
+            if (!g->slots[k]) { slot = k; break; }
+        if (slot < 0) return;                              // group full: wait for a slot
+        if (bz_batch_set_gamma(g->batch, slot, r.gamma) != BZ_OK ||
+            cudaMemcpyAsync(g->state + (size_t)slot * n3, q->input.data(), n3 * sizeof(double2),
+                            cudaMemcpyHostToDevice, g->stream) != cudaSuccess) {
+            q->status = BZ_ERR_CUDA;
+            q->t_done = Clock::now();
+            S->queue.pop_front();
+            continue;
         }
+        g->slots[slot] = q;
+        q->slot = slot;
         q->group = g;
         q->t_admit = Clock::now();
         g->last_used = q->t_admit;
@@ -272,7 +257,7 @@ void finish(bz_server *S, Request *q, int status) {
     Group *g = q->group;
     const size_t n3 = (size_t)q->req.N * q->req.N * q->req.N;
     q->output.resize(n3);
-    const void *src = g->batch ? (const void *)(g->state + (size_t)q->slot * n3) : (const void *)q->state_single;
+    const void *src = g->state + (size_t)q->slot * n3;
     if (status == BZ_OK &&
         (cudaMemcpyAsync(q->output.data(), src, n3 * sizeof(double2), cudaMemcpyDeviceToHost, g->stream) != cudaSuccess ||
          cudaStreamSynchronize(g->stream) != cudaSuccess))
@@ -283,18 +268,7 @@ void finish(bz_server *S, Request *q, int status) {
                 status = BZ_ERR_NONFINITE;
                 break;
             }
-    if (g->batch) {
-        g->slots[q->slot] = nullptr;
-    } else {
-        for (size_t i = 0; i < g->singles.size(); ++i)
-            if (g->singles[i] == q) {
-                g->singles.erase(g->singles.begin() + (long)i);
-                break;
-            }
-        cudaFree(q->state_single);
-        q->state_single = nullptr;
-        S->used -= n3 * sizeof(double2);
-    }
+    g->slots[q->slot] = nullptr;
     q->status = status;
     q->t_done = Clock::now();
     g->last_used = q->t_done;
@@ -316,24 +290,14 @@ void retire_step(bz_server *S, Group *g, cudaError_t ev) {
 
 // Launches one RK4 step of every active request of g on its stream and records its event.
 void launch_step(Group *g) {
-    int st = BZ_OK;
     g->running.clear();
-    if (g->batch) {
-        std::vector<int> sl;
-        for (int i = 0; i < g->capacity; ++i)
-            if (g->slots[i]) {
-                sl.push_back(i);
-                g->running.push_back(g->slots[i]);
-            }
-        st = bz_batch_step_rk(g->batch, (int)sl.size(), sl.data(), g->state, BZ_C128, g->key.dt, 1, g->stream);
-    } else {
-        for (Request *q : g->singles) {
-            g->running.push_back(q);
-            double t = 0.0;
-            const int s1 = bz_step_rk(g->plan, q->state_single, BZ_C128, &t, q->req.dt, 1, nullptr, g->stream);
-            if (s1 != BZ_OK && st == BZ_OK) st = s1;
+    std::vector<int> sl;
+    for (int i = 0; i < g->capacity; ++i)
+        if (g->slots[i]) {
+            sl.push_back(i);
+            g->running.push_back(g->slots[i]);
         }
-    }
+    int st = bz_batch_step_rk(g->batch, (int)sl.size(), sl.data(), g->state, BZ_C128, g->key.dt, 1, g->stream);
     if (cudaEventRecord(g->done, g->stream) != cudaSuccess && st == BZ_OK) st = BZ_ERR_CUDA;
     g->launch_status = st;
     g->inflight = true;
@@ -477,8 +441,6 @@ void bz_server_destroy(bz_server *S) {
         S->cv.notify_all();
     }
     if (S->worker.joinable()) S->worker.join();
-    for (auto &kv : S->all)
-        if (kv.second->state_single) cudaFree(kv.second->state_single);
     for (auto &kv : S->groups) destroy_group(S, kv.second.get());
     delete S;
 }

@@ -96,3 +96,50 @@ def test_batch_rejects_bad_slots(bz):
             bz.bz_batch_collide(batch, bad, fd, qd)
     batch.close()
     plan.close()
+
+
+@pytest.mark.parametrize("N,N_rho,M,data", [(48, 2, 12, 0), (64, 1, 12, 1), (24, 3, 12, 1)])
+def test_batches_of_chunked_plans(bz, N, N_rho, M, data):
+    """A batch over a plan on the chunked pipeline (N = 24 real data, 48, 64): each slot with its
+    own gamma (eq. approxG: c_p carries r^gamma) matches the oracle's operator of that gamma,
+    a slot's result is the same bits alone and among others, and a batched RK4 step equals the
+    plan's own RK4 on a plan built with that gamma within the FP32 bar."""
+    L = 10.0
+    R = bi.R_from_L(L)
+    cap = 3
+    gam = [0.0, -1.0, -2.0]
+    plan = bz.bz_plan_create_ex(N, L, R, 0.0, 0.5, N_rho, M, data=data)
+    assert bz.bz_plan_pipeline(plan)["pipeline"] == "chunked"
+    batch = bz.bz_batch_create(plan, cap, 0)
+    for slot, g in enumerate(gam):
+        bz.bz_batch_set_gamma(batch, slot, g)
+    f = np.stack([bi.random_mixture(N, L, seed=300 + slot) for slot in range(cap)])
+    fd = torch.from_numpy(f).cuda()
+    q = torch.empty_like(fd)
+    bz.bz_batch_collide(batch, [0, 1, 2], fd, q)
+    q1 = torch.zeros_like(fd)
+    bz.bz_batch_collide(batch, [2], fd, q1)
+    torch.cuda.synchronize()
+    got = q.cpu().numpy()
+    assert np.array_equal(q1.cpu().numpy()[2], got[2])           # alone = in the batch
+    fn = spectral.collide_real if data else spectral.collide
+    for slot in (1, 2):
+        op = spectral.OraclePlan(N, L, R, gam[slot], kernels.Kernel("family", 0.5), N_rho, M)
+        ref = fn(op, f[slot])
+        err = _rel(got[slot], ref)
+        print(f"chunked batch N={N} data={data} gamma={gam[slot]}: rel_Linf={err:.2e}")
+        assert err <= TOL
+    # RK4 through the batch against a plan with the slot's gamma
+    g2 = bz.bz_plan_create_ex(N, L, R, -2.0, 0.5, N_rho, M, data=data)
+    ref = fd[2].clone()
+    bz.bz_step_rk(g2, ref, 0.0, 0.05, 2)
+    cells = fd.clone()
+    bz.bz_batch_step_rk(batch, [0, 2], cells, 0.05, 2)
+    torch.cuda.synchronize()
+    d = (cells[2] - fd[2]).cpu().numpy()
+    dr = (ref - fd[2]).cpu().numpy()
+    assert _rel(d, dr) <= TOL
+    assert torch.equal(cells[1], fd[1])                           # inactive slot untouched
+    g2.close()
+    batch.close()
+    plan.close()

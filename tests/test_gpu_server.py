@@ -73,13 +73,25 @@ def test_result_alone_equals_result_in_the_mix_and_matches_oracle(bz):
     err = float(np.max(np.abs((outA - fA) - (ref - fA))) / np.max(np.abs(ref - fA)))
     print(f"served RK4: rel_Linf of the change={err:.2e}")
     assert err <= TOL
-    # the N = 48 request (own plan, chunked pipeline) equals a direct bz_step_rk
+    # the N = 48 request (chunked pipeline, gamma per slot of the group's batch) equals the same
+    # batch call made directly, bit for bit, and a plan built with its gamma within the bar
     r48 = mix[4]
-    plan = bz.bz_plan_create(48, L, R, -1.0, 0.5, 1, 12)
-    f48 = torch.from_numpy(r48["fhat0"]).cuda()
-    bz.bz_step_rk(plan, f48, 6.5, 0.025, 2)
+    plan = bz.bz_plan_create(48, L, R, 0.0, 0.5, 1, 12)
+    batch = bz.bz_batch_create(plan, 1, 0)
+    bz.bz_batch_set_gamma(batch, 0, -1.0)
+    f48 = torch.from_numpy(r48["fhat0"]).cuda().reshape(1, 48, 48, 48).contiguous()
+    for _ in range(2):
+        bz.bz_batch_step_rk(batch, [0], f48, 0.025, 1)
     torch.cuda.synchronize()
-    assert np.array_equal(res[4][1], f48.cpu().numpy())
+    assert np.array_equal(res[4][1], f48[0].cpu().numpy())
+    batch.close()
+    pg = bz.bz_plan_create(48, L, R, -1.0, 0.5, 1, 12)
+    fg = torch.from_numpy(r48["fhat0"]).cuda()
+    bz.bz_step_rk(pg, fg, 6.5, 0.025, 2)
+    torch.cuda.synchronize()
+    d0 = fg.cpu().numpy() - r48["fhat0"]
+    assert float(np.max(np.abs(res[4][1] - r48["fhat0"] - d0)) / np.max(np.abs(d0))) <= TOL
+    pg.close()
     st = bz.bz_server_stats(server)
     assert st["completed"] == 7 and st["queued"] == 0 and st["active"] == 0
     plan.close()
