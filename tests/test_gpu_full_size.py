@@ -95,3 +95,25 @@ def test_sampled_terms_n64_p4096(bz):
     torch.cuda.synchronize()
     assert _rel((a + b).cpu().numpy(), full.cpu().numpy()) <= 1e-6
     plan.close()
+
+
+@pytest.mark.parametrize("data", [0, 1])
+def test_whole_collide_n64_moderate_P_every_mode(bz, data):
+    """A whole N = 64 collide (the C3 data and operator, N_rho = 4, M = 12: P = 48, the full
+    radial range [0, R]; two chunks, so both streams run) through the bench's chunked pipeline,
+    against the oracle at every mode with the max |Qhat| bar, complex and real-data forms.  (The
+    bench checks one full P = 4096 collide against the oracle at sampled modes.)"""
+    N, L = 64, 10.0
+    R = bi.R_from_L(L)
+    fhat = bi.bigaussian_noise_c3(N, L)
+    plan = bz.bz_plan_create_ex(N, L, R, -1.0, 0.5, 4, 12, data=data)
+    f = torch.from_numpy(fhat).cuda()
+    q = torch.empty_like(f)
+    bz.bz_collide(plan, f, q)
+    torch.cuda.synchronize()
+    op = spectral.OraclePlan(N, L, R, -1.0, kernels.Kernel("family", 0.5), 4, 12)
+    ref = (spectral.collide_real if data else spectral.collide)(op, fhat)
+    err = _rel(q.cpu().numpy(), ref)
+    print(f"N=64 P=48 data={data} every mode: rel_Linf={err:.2e}")
+    assert err <= TOL
+    plan.close()
