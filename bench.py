@@ -668,7 +668,7 @@ def run_sharded(args, w):
 
 def _pipeline_roofline(w, ms_per_collide, peaks, src, traffic_key=None):
     """Roofline of a whole collide on the chunked pipeline, whose kernels overlap on two streams:
-    the method's algorithmic flops (the per-term count of SURVEY-style FFT work, every term) and
+    the method's algorithmic flops (the per-term count of `_flops_per_term`, every term) and
     the alpha-table bytes (8 N^3 per term) of one collide over the measured collide time,
     against the FP32 FMA peak and the measured HBM bandwidth; the larger fraction binds."""
     N, P = w["N"], w["N_rho"] * w["M"]
@@ -690,7 +690,7 @@ def _pipeline_roofline(w, ms_per_collide, peaks, src, traffic_key=None):
 
 
 def _bkw_trajectory(bz, plan, w, L, steps=500):
-    """SURVEY's C2 check: RK4 of the BKW solution from t0 for `steps` steps of dt on the GPU
+    """The BKW trajectory check: RK4 of the BKW solution from t0 for `steps` steps of dt on the GPU
     (complex128 state), against the exact BKW solution (Sec. 5.1, eq. BKW) at the final time:
     relative L-infinity error of the coefficients, max |f_gpu - f_exact| / max |f_exact|.
     This measures the method (quadrature, truncation) and the FP32 pipeline together."""
@@ -818,7 +818,7 @@ def run_ours(args, w):
                                  also_realq=real)
         parity["collide"] = "one full collide of the workload's input through bz_collide"
 
-    # SURVEY's C2: the 500-step BKW trajectory against the exact solution, s = 1/2 and 1/4
+    # the 500-step BKW trajectory (t = 6.5 -> 11.5) against the exact solution, s = 1/2 and 1/4
     trajectory = None
     if args.workload == "rk4_n32" and not args.no_trajectory:
         trajectory = {"desc": "RK4 of the BKW solution from t=6.5 to t=11.5 (500 steps of 0.01), N=32, "

@@ -99,7 +99,7 @@ def test_sampled_terms_n64_p4096(bz):
 
 @pytest.mark.parametrize("data", [0, 1])
 def test_whole_collide_n64_moderate_P_every_mode(bz, data):
-    """A whole N = 64 collide (the C3 data and operator, N_rho = 4, M = 12: P = 48, the full
+    """A whole N = 64 collide (the bench's N = 64 data and operator, N_rho = 4, M = 12: P = 48, the full
     radial range [0, R]; two chunks, so both streams run) through the bench's chunked pipeline,
     against the oracle at every mode with the max |Qhat| bar, complex and real-data forms.  (The
     bench checks one full P = 4096 collide against the oracle at sampled modes.)"""
