@@ -801,6 +801,22 @@ def run_ours(args, w):
                  "roofline": _roofline(args, w, kerno, peaks, src, "fused" if real else "fused_real")}
         po.close()
 
+    # the same workload with h formed in FP32 too: FP64 only in the weight tables, the RK state
+    # and the moments
+    pure = None
+    if args.workload == "rk4_n32" and real and args.h_precision != 2 and not args.no_other_form:
+        pp = bz.bz_plan_create_ex(N, L, R, w["gamma"], w["s"], w["N_rho"], w["M"], h_precision=2, data=data_form)
+        fp, qp = torch.from_numpy(f_host).to("cuda"), torch.empty_like(f)
+        vp, msp, kernp, lp, _ = _time_plan(args, w, bz, pp, fp, qp, st, barrier)
+        bz.bz_collide(pp, torch.from_numpy(f_host).to("cuda"), qp, st)
+        torch.cuda.synchronize()
+        pure = {"h_precision": "fp32", "value": vp, "unit": "evals/s", "ms_per_step": msp / args.steps,
+                "kernel": bz.bz_plan_pipeline(pp)["kernel"], "gpu_launches": lp * args.steps}
+        if rank == 0 and not args.no_cpu_baseline:
+            pure["parity"] = error_vs_oracle(w, L, R, f_host, qp.cpu().numpy().astype(np.complex128), real=True,
+                                             also_realq=True)
+        pp.close()
+
     mixed = None
     if N == 32 and dim == 3 and not args.no_mixed:
         pc = plan if not real else make_plan(bz.BZ_DATA_COMPLEX)
@@ -853,6 +869,8 @@ def run_ours(args, w):
             "parity": parity, "cpu_baseline": cpu}
     if trajectory is not None:
         line["trajectory"] = trajectory
+    if pure is not None:
+        line["fp32_h"] = pure
     if n64 is not None:
         line["n64"] = n64
     if other is not None:
@@ -1221,6 +1239,25 @@ def run_serve(args, w):
                        "warm_s": warm_s, "clocks": clk.summary()})
         if args.no_mixed:
             break
+    sweep = []
+    if args.rates:
+        # a rate sweep on the first requests of the trace (FP32): p50 / p99 latency per rate
+        sub = trace[:args.sweep_requests]
+        for rt in [float(x) for x in args.rates.split(",")]:
+            arr = bi.poisson_arrivals(len(sub), rt, seed=79)
+            t0 = time.perf_counter()
+            tickets = []
+            for r, ta in zip(sub, arr):
+                delay = t0 + ta - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+                tickets.append((submit(r, t_end, False), r["N"]))
+            res = wait(tickets)
+            wall = time.perf_counter() - t0
+            lat = np.array([res[t][0].latency_s for t, _ in tickets])
+            sweep.append({"rate": rt, "requests": len(sub), "requests_per_s": len(sub) / wall,
+                          "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99)),
+                          "all_ok": all(res[t][0].status == 0 for t, _ in tickets)})
     server.close()
     head = passes[0]
     line = {"metric": "served requests/s", "value": head["requests_per_s"], "unit": "requests/s", "n_gpus": 1,
@@ -1230,6 +1267,8 @@ def run_serve(args, w):
             "latency_s": {"p50": head["latency_p50_s"], "p99": head["latency_p99_s"]},
             "queue_s": {"p50": head["queue_p50_s"], "p99": head["queue_p99_s"]},
             "q_evals_per_s": head["q_evals_per_s"], "passes": passes}
+    if sweep:
+        line["rate_sweep"] = sweep
     print(json.dumps(line))
     return 0
 
@@ -1254,6 +1293,9 @@ def main():
     ap.add_argument("--no-mixed", action="store_true",
                     help="skip the split-BF16 tensor-core form (measured beside the FP32 form at N = 32)")
     ap.add_argument("--serve-requests", type=int, default=256, help="serve workload: requests in the trace")
+    ap.add_argument("--rates", default=None,
+                    help="serve workload: comma-separated arrival rates (req/s) of a sweep after the trace")
+    ap.add_argument("--sweep-requests", type=int, default=64, help="serve workload: requests per rate of the sweep")
     ap.add_argument("--data", default="auto", choices=["auto", "real", "complex"],
                     help="data form of the headline plan: auto = real where the plan supports it "
                          "(3D, N in {8, 16, 32}, M even; the workloads' f are real), else complex")

@@ -155,9 +155,10 @@ typedef struct {
                          eqs. ApproximatedDebyecutoff and b3cutoff; 0 = none, else eps <= theta0 < pi.
                          With a cutoff there is no Taylor part; the theta rule starts at theta0. */
     int data;         /* BZ_DATA_*                                                         */
-    int ctas_per_sm;  /* fused pipeline, BZ_DATA_REAL at N = 32 with FP64 h: 2 runs k_fused, 3 the
-                         three-CTA-per-SM pair kernel k_pair3 (sum over pairs and fhat column in
-                         tensor memory); <= 0 times both at creation and keeps the faster.  Any
+    int ctas_per_sm;  /* fused pipeline, BZ_DATA_REAL at N = 32: 2 runs k_fused, 3 the three-CTA-
+                         per-SM pair kernel k_pair3 (sum over pairs and fhat column in tensor
+                         memory; with BZ_H_FP32 its h comes from one FP32 plane pass and one
+                         pencil pass); <= 0 times both at creation and keeps the faster.  Any
                          other plan: must be <= 0 or 2, else BZ_ERR_UNSUPPORTED.              */
 } bz_plan_desc;
 

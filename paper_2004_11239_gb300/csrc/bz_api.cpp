@@ -80,8 +80,8 @@ bz_status select_fused(bz::Plan &pl, int forced, int ctas) {
     const bool mixed = pl.precision == BZ_PREC_BF16X3;
     int nc = mixed ? 1 : bz::fused_candidates(pl.N, cs);
     if (mixed) cs[0] = 8;
-    // the real-data form at N = 32 (FP64 h) also times the three-CTA pair kernel, k_pair3 (C = 8)
-    const int pair3_c = (pl.real && pl.N == 32 && pl.h_fp64 && ctas != 2) ? nc : -1;
+    // the real-data form at N = 32 also times the three-CTA pair kernel, k_pair3 (C = 8)
+    const int pair3_c = (pl.real && pl.N == 32 && ctas != 2) ? nc : -1;
     if (pair3_c >= 0) cs[nc++] = 8;
     const size_t field = (size_t)pl.N * pl.N * pl.N * sizeof(float2);
     const size_t fields = (size_t)3 * pl.N * pl.N * sizeof(float2);   // BZ_DATA_REAL: Nyquist-plane sums
@@ -159,7 +159,7 @@ bz_status create(bz_plan **out, const bz_plan_desc *d) {
     if (real && (dim != 3 || d->precision != BZ_PREC_FP32 || padded || d->M % 2 != 0 ||
                  (d->pipeline == BZ_PIPE_FUSED && 32 % d->N != 0)))
         return BZ_ERR_UNSUPPORTED;
-    if (d->ctas_per_sm == 3 && !(real && d->N == 32 && d->h_precision != BZ_H_FP32)) return BZ_ERR_UNSUPPORTED;
+    if (d->ctas_per_sm == 3 && !(real && d->N == 32)) return BZ_ERR_UNSUPPORTED;
     if (d->ctas_per_sm > 0 && d->ctas_per_sm != 2 && d->ctas_per_sm != 3) return BZ_ERR_UNSUPPORTED;
     if (dim == 3 && !((d->kernel >= BZ_KERNEL_FAMILY && d->kernel <= BZ_KERNEL_B8) || d->kernel == BZ_KERNEL_DEBYE))
         return BZ_ERR_ARG;

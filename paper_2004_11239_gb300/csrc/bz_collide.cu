@@ -507,6 +507,22 @@ static bz_status run_chunks(Plan &pl, int p0, int p1, cudaStream_t st, int *laun
     return BZ_OK;
 }
 
+template <int N> static void h_fp32_n(Plan &pl, const float2 *fin, cudaStream_t st) {
+    plane_inv<N, false>(fin, pl.tw, pl.S, 0, 1, 0, st);
+    k_pencil<N, 0><<<dim3((N * N + 127) / 128, 1), 128, 0, st>>>(pl.S, nullptr, pl.h);
+}
+
+bz_status h_fp32(Plan &pl, const float2 *fin, cudaStream_t st) {
+    switch (pl.N) {
+        case 8: h_fp32_n<8>(pl, fin, st); break;
+        case 16: h_fp32_n<16>(pl, fin, st); break;
+        case 32: h_fp32_n<32>(pl, fin, st); break;
+        default: return BZ_ERR_UNSUPPORTED;
+    }
+    BZ_CUDA_TRY(cudaGetLastError());
+    return BZ_OK;
+}
+
 bz_status load_input(Plan &pl, const void *fhat, int dtype, cudaStream_t st, int *launches) {
     const int n3 = (int)modes(pl);
     if (dtype != BZ_C64 && dtype != BZ_C128) return BZ_ERR_ARG;

@@ -432,6 +432,14 @@ bz_status collide_fused(Plan &pl, int p0, int p1, cudaStream_t st, int *launches
         if (s != BZ_OK) return s;
         tm_end(pl, st, TK_OTHER);
         nl += h64_launches(pl.N);
+    } else if (pl.pair3) {
+        // the pair kernel reads h: formed in FP32 from the symmetrised input by one plane pass
+        // and one pencil pass of the chunked pipeline
+        tm_begin(pl, st);
+        s = h_fp32(pl, pl.fsym, st);
+        if (s != BZ_OK) return s;
+        tm_end(pl, st, TK_OTHER);
+        nl += 2;
     } else {
         a.hg = nullptr;                                   // h formed in FP32 in the item prologue
     }

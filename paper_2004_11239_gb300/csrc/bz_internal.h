@@ -149,6 +149,8 @@ bz_status collide_range(Plan &pl, int p0, int p1, const void *fhat, int in_dtype
 bz_status write_output(Plan &pl, void *Qhat, int dtype, cudaStream_t st, int *launches);
 bz_status load_input(Plan &pl, const void *fhat, int dtype, cudaStream_t st, int *launches);
 bz_status collide_core(Plan &pl, int p0, int p1, cudaStream_t st, int *launches);
+// pl.h = IFFT(fin) in FP32 (one plane pass and one pencil pass through pl.S; N = 8, 16, 32)
+bz_status h_fp32(Plan &pl, const float2 *fin, cudaStream_t st);
 
 // bz_fused.cu
 // Arguments of the fused item kernel (see k_fused): item w = (instance w / nblk, term block

@@ -15,7 +15,8 @@
 //     their result to the host (BZ_ERR_NONFINITE if it holds NaN or Inf, BZ_ERR_CUDA if the
 //     step failed) and free their slots,
 //   - an idle group with active requests launches its next step and records its event.
-// Groups therefore run ahead independently and overlap on the device.  State stays on the
+// Groups therefore run ahead independently and overlap on the device; a group's stream
+// priority falls with its N, so the short steps of light groups are scheduled first.  State stays on the
 // device from admission to completion; results do not depend on the other requests in flight
 // (batched results are per-instance invariant).  Idle plans and batches stay cached until the
 // budget needs their memory.
@@ -176,7 +177,14 @@ Group *get_group(bz_server *S, const bz_request &r, int *err) {
     d.kernel = r.kernel; d.precision = r.precision; d.data = r.data;
     int st = bz_plan_create_ex(&g->plan, &d);
     if (st != BZ_OK) { *err = st; return nullptr; }
-    if (cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking) != cudaSuccess ||
+    // lighter groups get higher stream priority, so that their short steps are not queued
+    // behind the heavy chunked kernels of large N (whose groups keep the default, lowest)
+    int least = 0, greatest = 0;
+    cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    const int heavy = r.N <= 16 ? 0 : r.N <= 24 ? 1 : r.N <= 32 ? 2 : r.N <= 48 ? 3 : 4;
+    int prio = greatest + heavy;
+    if (prio > least) prio = least;
+    if (cudaStreamCreateWithPriority(&g->stream, cudaStreamNonBlocking, prio) != cudaSuccess ||
         cudaEventCreateWithFlags(&g->done, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         if (g->stream) cudaStreamDestroy(g->stream);

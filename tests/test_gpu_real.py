@@ -294,3 +294,31 @@ def test_real_fused_with_fp32_h(bz):
     with pytest.raises(bz.BzError):                              # batches need h in FP64
         bz.bz_batch_create(plan, 2, 0)
     plan.close()
+
+
+def test_pair_kernel_with_fp32_h(bz):
+    """k_pair3 (three CTAs per SM) with h formed in FP32 by a plane and a pencil pass
+    (BZ_H_FP32): the pure-FP32 real-data form at N = 32 within the FP32 bar of the oracle, and
+    its RK4 step within the bar of the FP64-h form's change."""
+    N = 32
+    R = 6.0
+    L = bi.L_from_R(R)
+    fhat = bi.bkw_fhat(N, L, bi.bkw_K(6.5))
+    plan = _real_plan(bz, N, L, R, 0.0, 0.5, 4, 12, h_precision=bz.BZ_H_FP32, ctas_per_sm=3)
+    assert bz.bz_plan_pipeline(plan)["kernel"] == "k_pair3"
+    got = _collide(bz, plan, fhat)
+    op = spectral.OraclePlan(N, L, R, 0.0, kernels.Kernel("family", 0.5), 4, 12)
+    err = _rel(got, spectral.collide_real(op, fhat))
+    print(f"k_pair3 FP32 h: rel_Linf={err:.2e}")
+    assert err <= TOL
+    ref = _real_plan(bz, N, L, R, 0.0, 0.5, 4, 12, ctas_per_sm=3)
+    f1 = torch.from_numpy(fhat).cuda()
+    f2 = f1.clone()
+    bz.bz_step_rk(plan, f1, 6.5, 0.05, 2)
+    bz.bz_step_rk(ref, f2, 6.5, 0.05, 2)
+    torch.cuda.synchronize()
+    d1 = f1.cpu().numpy() - fhat
+    d2 = f2.cpu().numpy() - fhat
+    assert _rel(d1, d2) <= TOL
+    ref.close()
+    plan.close()
