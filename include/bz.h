@@ -363,14 +363,15 @@ bz_status bz_inhom_step(bz_batch *batch, int nx, double Lx, void *fcells, int dt
 /* ---------------------------------------------------------------------------------------
  * Serving: a worker thread runs homogeneous relaxation solves (RK4 on d fhat/dt = Q) for
  * submitted requests with continuous batching.  Requests with equal geometry, data form,
- * precision and dt form a group with its own plan, stream and completion event; groups on the
- * fused pipeline (N <= 32; N | 32 for BZ_DATA_REAL) step all their requests with one batched
- * call, the others step each request through the group's plan.  The worker admits queued
- * requests in arrival order while the HBM budget and group slots allow; a group whose step has
- * completed (polled with cudaEventQuery: no group waits for another) advances its requests by
- * one RK4 step, retires the finished ones and launches its next step, which requests admitted
- * meanwhile join.  State stays on the device from admission to completion.  A request's result
- * does not depend on the other requests in flight.
+ * precision and dt form a group with its own plan, batch (gamma per slot), stream and
+ * completion event.  The worker admits queued requests in arrival order while the HBM budget
+ * and group slots allow; a group whose step has completed (polled with cudaEventQuery: no group
+ * waits for another) advances its requests by one RK4 step, retires the finished ones and
+ * launches its next step, which requests admitted meanwhile join.  Groups on the fused pipeline
+ * (N <= 32; N | 32 for BZ_DATA_REAL) step whenever idle; of the others (chunked pipeline) one
+ * step is in flight at a time, the group with the shortest remaining work first (aged by its
+ * wait).  State stays on the device from admission to completion.  A request's result does not
+ * depend on the other requests in flight.
  * --------------------------------------------------------------------------------------- */
 typedef struct bz_server bz_server;
 

@@ -13,6 +13,7 @@
 // the active count and slot list are read from device memory at run time.
 #include <cmath>
 #include <map>
+#include <tuple>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -46,6 +47,10 @@ struct bz_batch {
     std::map<double, cudaGraphExec_t> graphs;
     int last_launches = 0;
     bool chunked = false;           // the plan runs the chunked pipeline: slots step one by one
+    // chunked plans: one captured RK4 step per (slot, dt, dtype, array) -- the slot's input,
+    // four stages and its output as one graph launch
+    std::map<std::tuple<int, double, int, const void *>, cudaGraphExec_t> slot_graphs;
+    int slot_graph_launches = 0;    // kernel launches inside one such graph
 };
 
 namespace bz {
@@ -291,6 +296,8 @@ bz_status stage_slots(bz_batch &B, int count, const int *slots, cudaStream_t st)
 void free_batch(bz_batch *B) {
     for (auto &g : B->graphs) cudaGraphExecDestroy(g.second);
     B->graphs.clear();
+    for (auto &g : B->slot_graphs) cudaGraphExecDestroy(g.second);
+    B->slot_graphs.clear();
     cudaFree(B->gsc); cudaFree(B->fin); cudaFree(B->part); cudaFree(B->f0); cudaFree(B->fsum);
     cudaFree(B->fin64); cudaFree(B->scr64); cudaFree(B->h); cudaFree(B->fsym); cudaFree(B->part_s);
     cudaFree(B->slots_dev); cudaFree(B->count_dev);
@@ -379,6 +386,39 @@ bz_status chunked_collide(bz_batch &B, int count, const int *slots, const void *
     return s;
 }
 
+// One RK4 step of one slot captured as a graph (the host then launches one graph per slot and
+// step instead of some hundred kernels).
+bz_status slot_graph(bz_batch &B, int slot, void *fhat_slot, int dtype, double dt, cudaGraphExec_t *out) {
+    Plan &pl = *B.pl;
+    const auto key = std::make_tuple(slot, dt, dtype, (const void *)fhat_slot);
+    auto it = B.slot_graphs.find(key);
+    if (it != B.slot_graphs.end()) {
+        *out = it->second;
+        return BZ_OK;
+    }
+    cudaGraph_t g = nullptr;
+    BZ_CUDA_TRY(cudaStreamBeginCapture(B.cap_stream, cudaStreamCaptureModeThreadLocal));
+    pl.gsc_cur = B.gsc + (size_t)slot * pl.N_rho;
+    int nl = 0;
+    const bz_status cs = rk4_steps(pl, fhat_slot, dtype, dt, 1, B.cap_stream, &nl);
+    pl.gsc_cur = nullptr;
+    pl.src = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(B.cap_stream, &g);
+    if (cs != BZ_OK || ce != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return cs != BZ_OK ? cs : BZ_ERR_CUDA;
+    }
+    cudaGraphExec_t ex = nullptr;
+    const cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) return BZ_ERR_CUDA;
+    B.slot_graphs.emplace(key, ex);
+    B.slot_graph_launches = nl;
+    *out = ex;
+    return BZ_OK;
+}
+
 bz_status chunked_step_rk(bz_batch &B, int count, const int *slots, void *fhat, int dtype, double dt, int nsteps,
                           cudaStream_t st) {
     bz_status s = check_slots(B, count, slots);
@@ -386,12 +426,25 @@ bz_status chunked_step_rk(bz_batch &B, int count, const int *slots, void *fhat, 
     Plan &pl = *B.pl;
     const size_t bytes = (size_t)pl.N * pl.N * pl.N * (dtype == BZ_C128 ? sizeof(double2) : sizeof(float2));
     int nl = 0;
-    for (int b = 0; b < count && s == BZ_OK; ++b) {
-        pl.gsc_cur = B.gsc + (size_t)slots[b] * pl.N_rho;
-        s = rk4_steps(pl, (char *)fhat + slots[b] * bytes, dtype, dt, nsteps, st, &nl);
+    if (pl.tm.on) {
+        // per-kernel timing brackets every launch with events: no graphs
+        for (int b = 0; b < count && s == BZ_OK; ++b) {
+            pl.gsc_cur = B.gsc + (size_t)slots[b] * pl.N_rho;
+            s = rk4_steps(pl, (char *)fhat + slots[b] * bytes, dtype, dt, nsteps, st, &nl);
+        }
+        pl.gsc_cur = nullptr;
+        pl.src = nullptr;
+        B.last_launches = nl;
+        return s;
     }
-    pl.gsc_cur = nullptr;
-    pl.src = nullptr;
+    for (int b = 0; b < count && s == BZ_OK; ++b) {
+        cudaGraphExec_t ex = nullptr;
+        s = slot_graph(B, slots[b], (char *)fhat + slots[b] * bytes, dtype, dt, &ex);
+        for (int k = 0; k < nsteps && s == BZ_OK; ++k) {
+            if (cudaGraphLaunch(ex, st) != cudaSuccess) s = BZ_ERR_CUDA;
+            nl += B.slot_graph_launches;
+        }
+    }
     B.last_launches = nl;
     return s;
 }
@@ -420,7 +473,8 @@ bz_status bz_batch_create(bz_batch **out, const bz_plan *plan, int capacity, int
         // chunked plans step their slots one after another through the plan's own pipeline
         // (each chunk kernel already fills the GPU); only the radial scales live in the batch
         B->chunked = true;
-        if (cudaMalloc(&B->gsc, (size_t)capacity * pl->N_rho * sizeof(float)) != cudaSuccess) {
+        if (cudaMalloc(&B->gsc, (size_t)capacity * pl->N_rho * sizeof(float)) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&B->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
             cudaGetLastError();
             return fail(BZ_ERR_OOM);
         }

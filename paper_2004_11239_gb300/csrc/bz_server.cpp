@@ -15,8 +15,13 @@
 //     their result to the host (BZ_ERR_NONFINITE if it holds NaN or Inf, BZ_ERR_CUDA if the
 //     step failed) and free their slots,
 //   - an idle group with active requests launches its next step and records its event.
-// Groups therefore run ahead independently and overlap on the device; a group's stream
-// priority falls with its N, so the short steps of light groups are scheduled first.  State stays on the
+// Groups therefore run ahead independently and overlap on the device, except that at most one
+// heavy (chunked-pipeline) step is in flight at a time -- concurrent chunked pipelines evict
+// each other's L2-resident scratch -- chosen by shortest remaining work (the group that can
+// finish a request soonest), aged by the time since the group last stepped so that none waits
+// for ever.  (All
+// streams keep the default priority: giving light groups a higher one starved the heavy ones
+// under load.)  State stays on the
 // device from admission to completion; results do not depend on the other requests in flight
 // (batched results are per-instance invariant).  Idle plans and batches stay cached until the
 // budget needs their memory.
@@ -76,6 +81,8 @@ struct Group {
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;        // recorded after each step's launches
     bool inflight = false;
+    bool heavy = false;                // chunked pipeline: its scratch fills L2 (one such step at a time)
+    Clock::time_point last_step;       // launch time of its latest step (ages the heavy choice)
     int launch_status = BZ_OK;         // status of the in-flight step's launches
     std::vector<Request *> running;    // participants of the in-flight step
     size_t bytes = 0;
@@ -177,14 +184,7 @@ Group *get_group(bz_server *S, const bz_request &r, int *err) {
     d.kernel = r.kernel; d.precision = r.precision; d.data = r.data;
     int st = bz_plan_create_ex(&g->plan, &d);
     if (st != BZ_OK) { *err = st; return nullptr; }
-    // lighter groups get higher stream priority, so that their short steps are not queued
-    // behind the heavy chunked kernels of large N (whose groups keep the default, lowest)
-    int least = 0, greatest = 0;
-    cudaDeviceGetStreamPriorityRange(&least, &greatest);
-    const int heavy = r.N <= 16 ? 0 : r.N <= 24 ? 1 : r.N <= 32 ? 2 : r.N <= 48 ? 3 : 4;
-    int prio = greatest + heavy;
-    if (prio > least) prio = least;
-    if (cudaStreamCreateWithPriority(&g->stream, cudaStreamNonBlocking, prio) != cudaSuccess ||
+    if (cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&g->done, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         if (g->stream) cudaStreamDestroy(g->stream);
@@ -207,6 +207,7 @@ Group *get_group(bz_server *S, const bz_request &r, int *err) {
         }
         g->capacity = cap;
         g->slots.assign(cap, nullptr);
+        g->heavy = !fused(r);
     }
     g->bytes = need;
     g->last_used = Clock::now();
@@ -309,6 +310,7 @@ void launch_step(Group *g) {
     if (cudaEventRecord(g->done, g->stream) != cudaSuccess && st == BZ_OK) st = BZ_ERR_CUDA;
     g->launch_status = st;
     g->inflight = true;
+    g->last_step = Clock::now();
 }
 
 void worker_main(bz_server *S) {
@@ -316,7 +318,7 @@ void worker_main(bz_server *S) {
     std::unique_lock<std::mutex> lk(S->mu);
     while (!S->stop) {
         admit(S);
-        bool progressed = false, inflight = false;
+        bool progressed = false, inflight = false, heavy_busy = false;
         auto t0 = Clock::now();
         for (auto &kv : S->groups) {
             Group *g = kv.second.get();
@@ -324,13 +326,42 @@ void worker_main(bz_server *S) {
                 const cudaError_t ev = cudaEventQuery(g->done);
                 if (ev == cudaErrorNotReady) {
                     inflight = true;
+                    heavy_busy = heavy_busy || g->heavy;
                     continue;
                 }
                 retire_step(S, g, ev);
                 progressed = true;
             }
-            if (g->active() > 0) {
+            if (g->active() > 0 && !g->heavy) {        // light groups: as soon as they are idle
                 launch_step(g);
+                inflight = true;
+                progressed = true;
+            }
+        }
+        if (!heavy_busy) {
+            // one heavy step at a time (concurrent chunked pipelines evict each other's scratch
+            // from L2): the heavy group that finishes a request soonest first (shortest remaining
+            // work: its fewest remaining steps times the work of one of its steps)
+            Group *next = nullptr;
+            double best = 0.0;
+            for (auto &kv : S->groups) {
+                Group *g = kv.second.get();
+                if (!g->heavy || g->inflight || g->active() == 0) continue;
+                int left = 1 << 30;
+                for (Request *q : g->slots)
+                    if (q && q->steps_total - q->steps_done < left) left = q->steps_total - q->steps_done;
+                const double n3 = (double)g->key.N * g->key.N * g->key.N;
+                // aged: a group left waiting for seconds comes back into turn
+                const double age = std::chrono::duration<double>(Clock::now() - g->last_step).count();
+                const double work = (double)left * g->active() * n3 * std::log2((double)g->key.N) *
+                                    g->key.N_rho * g->key.M / (1.0 + age * age);
+                if (!next || work < best) {
+                    next = g;
+                    best = work;
+                }
+            }
+            if (next) {
+                launch_step(next);
                 inflight = true;
                 progressed = true;
             }
