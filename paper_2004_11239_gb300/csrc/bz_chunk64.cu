@@ -1,4 +1,5 @@
-// The two plane passes of the chunked pipeline (Sec. 4, eq. realQ) at N = 64, one plane per CTA.
+// The plane and pencil passes of the chunked pipeline (Sec. 4, eq. realQ) at N = 64: one plane
+// per CTA, or 32 lines along axis 1 per CTA.
 //
 // A 64-point transform is split as 64 = 8 x 8 (n = 8 n1 + n2, k = k1 + 8 k2):
 //     X[k1 + 8 k2] = sum_n2 W8^(n2 k2) [ W64^(n2 k1) sum_n1 x[8 n1 + n2] W8^(n1 k1) ],
@@ -50,6 +51,18 @@ template <int SIGN> __device__ __forceinline__ void stage1(float2 (&x)[8], int n
     fft_inplace<8, SIGN>(x);
     #pragma unroll
     for (int k1 = 1; k1 < 8; ++k1) x[k1] = cmul(x[k1], w64<SIGN>(w, n2 * k1));
+}
+
+// stage1 where n2 = q is the same across the warp: the twiddles come from the constant table
+// as broadcasts instead of from shared memory.
+template <int SIGN> __device__ __forceinline__ void stage1u(float2 (&x)[8], int q) {
+    fft_inplace<8, SIGN>(x);
+    #pragma unroll
+    for (int k1 = 1; k1 < 8; ++k1) {
+        float2 w = c_tw.v[tw_off<64>() + ((q * k1) & 63)];
+        if (SIGN < 0) w.y = -w.y;
+        x[k1] = cmul(x[k1], w);
+    }
 }
 
 // Row pass of the plane held in `tile` (natural order) or, for the first pass of plane_inv, in
@@ -116,7 +129,7 @@ k_plane_inv64(const float2 *__restrict__ fin, const float2 *__restrict__ tw, flo
     const int c = tid & 63, m2 = tid >> 6;
     #pragma unroll
     for (int n1 = 0; n1 < 8; ++n1) x[n1] = tile[(8 * n1 + m2) * RP + c];
-    stage1<+1>(x, m2, w);
+    stage1u<+1>(x, m2);
     #pragma unroll
     for (int k1 = 0; k1 < 8; ++k1) tile[(8 * k1 + m2) * RP + c] = x[k1];   // the rows it read: no hazard
     __syncthreads();
@@ -151,7 +164,7 @@ k_plane_fwd64(float2 *__restrict__ S, const float2 *__restrict__ alpha, int p0, 
     load_w64(w);
     __syncthreads();
     // axis 2: j2 -> k2 on column c
-    stage1<-1>(x, m2, w);
+    stage1u<-1>(x, m2);
     #pragma unroll
     for (int k1 = 0; k1 < 8; ++k1) tile[(8 * k1 + m2) * RP + c] = x[k1];
     __syncthreads();
@@ -196,6 +209,65 @@ k_plane_fwd64(float2 *__restrict__ S, const float2 *__restrict__ alpha, int p0, 
     }
 }
 
+// The pencil pass at N = 64: 32 lines (j2, j3), (j2, j3 + 1), ... of one term per 256-thread
+// CTA, each 64-point transform along axis 1 split 8 x 8 as in the plane passes: warp q holds
+// the elements 8 n1 + q of its lane's line, and the 8 x 8 transposes go through shared memory
+// (every warp access is 32 consecutive slots: no bank conflict).  The inverse transform leaves
+// warp q with j1 = q + 8 k2, which is the order the forward transform's first stage takes
+// (n2 = q, n1 = k2), so the product with h needs no transpose in between.
+//   MODE 0: out = IFFT_1(S)               (forms h)
+//   MODE 1: S = FFT_1(h . IFFT_1(S))      (in place)
+//   MODE 2: as MODE 1 with the real part of h (BZ_DATA_REAL)
+constexpr int PL = 32;                 // lines per CTA, one per lane
+constexpr int TP = 256;                // threads per CTA: warp q = n2 in stage 1, k1 in stage 2
+
+// x[k1] = Y[q][k1] on entry; x[k2] = X[q + 8 k2] on exit (tile free again once every thread
+// has passed the caller's next barrier)
+template <int SIGN> __device__ __forceinline__ void pencil_stage2(float2 (&x)[8], float2 *tile, int q, int lane) {
+    #pragma unroll
+    for (int k1 = 0; k1 < 8; ++k1) tile[(8 * k1 + q) * PL + lane] = x[k1];
+    __syncthreads();
+    #pragma unroll
+    for (int m = 0; m < 8; ++m) x[m] = tile[(8 * q + m) * PL + lane];
+    fft_inplace<8, SIGN>(x);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(TP, 4)
+k_pencil64(float2 *__restrict__ S, const float2 *__restrict__ h, float2 *__restrict__ out) {
+    constexpr int N2 = N64 * N64;
+    __shared__ float2 tile[N64 * PL];
+    const int lane = threadIdx.x & 31, q = threadIdx.x >> 5;
+    const int g = blockIdx.x * PL + lane;                 // line (j2, j3) = g
+    float2 *base = S + (size_t)blockIdx.y * N64 * N2 + g;
+    float2 x[8];
+    #pragma unroll
+    for (int n1 = 0; n1 < 8; ++n1) x[n1] = base[(size_t)(8 * n1 + q) * N2];
+    stage1u<+1>(x, q);                                    // axis 1: k1 -> j1
+    pencil_stage2<+1>(x, tile, q, lane);                  // x[k2] = line at j1 = q + 8 k2
+    if constexpr (MODE == 0) {
+        #pragma unroll
+        for (int k2 = 0; k2 < 8; ++k2) out[(size_t)(q + 8 * k2) * N2 + g] = x[k2];
+    } else {
+        #pragma unroll
+        for (int k2 = 0; k2 < 8; ++k2) {
+            const size_t j = (size_t)(q + 8 * k2) * N2 + g;
+            if constexpr (MODE == 2) {
+                const float hv = h[j].x;
+                x[k2].x *= hv;
+                x[k2].y *= hv;
+            } else {
+                x[k2] = cmul(x[k2], h[j]);
+            }
+        }
+        stage1u<-1>(x, q);                                // axis 1: j1 -> k1 (n1 = k2, n2 = q)
+        __syncthreads();                                  // every read of the first transpose is done
+        pencil_stage2<-1>(x, tile, q, lane);              // x[k2] = k1 = q + 8 k2
+        #pragma unroll
+        for (int k2 = 0; k2 < 8; ++k2) base[(size_t)(q + 8 * k2) * N2] = x[k2];
+    }
+}
+
 }  // namespace
 
 cudaError_t chunk64_set_attributes() {
@@ -222,6 +294,13 @@ void plane_fwd64(float2 *S, const float2 *alpha, int p0, int T, const float2 *cp
                  int M, bool pair, cudaStream_t st) {
     if (pair) k_plane_fwd64<true><<<dim3(N64, T), T64, kFwdSmem, st>>>(S, alpha, p0, cpair, Ss, gsc, M);
     else k_plane_fwd64<false><<<dim3(N64, T), T64, kFwdSmem, st>>>(S, alpha, p0, nullptr, nullptr, gsc, M);
+}
+
+void pencil64(float2 *S, const float2 *h, float2 *out, int T, int mode, cudaStream_t st) {
+    const dim3 grid(N64 * N64 / PL, T);
+    if (mode == 0) k_pencil64<0><<<grid, TP, 0, st>>>(S, nullptr, out);
+    else if (mode == 1) k_pencil64<1><<<grid, TP, 0, st>>>(S, h, nullptr);
+    else k_pencil64<2><<<grid, TP, 0, st>>>(S, h, nullptr);
 }
 
 }  // namespace bz

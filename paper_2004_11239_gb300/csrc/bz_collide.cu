@@ -5,8 +5,9 @@
 // stream's scratch and accumulator, overlapping the others; the sums are added at the end):
 //   plane_inv  (planes k1):  S = IFFT_{axes 3,2}( beta_p(m) fhat_m )       twiddle + 2 axes
 //   pencil     (lines k1):   S = FFT_1( h . IFFT_1(S) )                     product in registers
+// (at N = 64 the plane and pencil passes are the radix-8 x 8 kernels of bz_chunk64.cu)
 //   plane_fwd  (planes k1):  S = alpha_p . FFT_{axes 3,2}(S)                 weight in the epilogue
-//   reduce     (modes k):    acc += sum_t S[t]  (compensated FP32 over t, then FP64)
+//   reduce     (modes k):    acc += sum_t S[t]  (compensated FP32 over every term, FP64 at the end)
 // h = IFFT(fhat) is formed once per call by plane_inv without twiddles plus an
 // inverse-only pencil pass.  Inverse transforms are unnormalised; alpha carries N^-3.
 #include <algorithm>
@@ -169,16 +170,19 @@ k_plane_fwd(float2 *__restrict__ S, const float2 *__restrict__ alpha, int p0, co
 }
 
 // ---------------------------------------------------------------------------------------
-// reduce: acc[k] += sum_t S[t][k], Kahan-compensated in FP32 over the chunk's terms (in
-// term order), then added to the FP64 accumulator.  Each thread takes two adjacent modes
-// (16-byte loads) and issues the loads of up to kRedBatch terms before it adds them, so the
-// chunk's loads are in flight together.  A second array (S2, n2 modes, acc2) may follow the
-// first in the same launch: thread pairs past n3 / 2 take it.
+// reduce: acc[k] += sum_t S[t][k], one Kahan-compensated FP32 sum over every term of the
+// collide in term order (per lane), carried from chunk to chunk in the accumulator's memory
+// and turned into FP64 after the last chunk.  Each thread takes two adjacent modes (16-byte
+// loads) and issues the loads of up to kRedBatch terms before it adds them, so the chunk's
+// loads are in flight together.  A second array (S2, n2 modes, acc2) may follow the first in
+// the same launch: thread pairs past n3 / 2 take it.
 // ---------------------------------------------------------------------------------------
 constexpr int kRedBatch = 8;
 
 struct Kahan4 {
-    float s[4] = {0.f, 0.f, 0.f, 0.f}, c[4] = {0.f, 0.f, 0.f, 0.f};
+    float s[4], c[4];
+    __device__ __forceinline__ Kahan4(float4 s0, float4 c0)
+        : s{s0.x, s0.y, s0.z, s0.w}, c{c0.x, c0.y, c0.z, c0.w} {}
     __device__ __forceinline__ void add(float4 v) {
         const float x[4] = {v.x, v.y, v.z, v.w};
         #pragma unroll
@@ -190,22 +194,28 @@ struct Kahan4 {
     }
 };
 
+// acc += sum over the chunk's T terms, compensated in FP32 across every chunk of the collide:
+// while the chunks run, the 32 bytes of acc[2 k2], acc[2 k2 + 1] (FP64 modes 2 k2, 2 k2 + 1)
+// hold the running sums s and compensations c of the pair's four components as two float4
+// (zero bytes are the empty sum), and k_kahan_fold turns them into FP64 once at the end.  The
+// per-chunk pass thus runs no FP64 arithmetic, whose rate on this part is a small fraction of
+// FP32's.  S2 / n2 / acc2 (or null): a second field summed the same way (the Nyquist sums).
 __global__ void __launch_bounds__(256)
 k_reduce(const float2 *__restrict__ S, int T, int n3, double2 *__restrict__ acc,
          const float2 *__restrict__ S2 = nullptr, int n2 = 0, double2 *__restrict__ acc2 = nullptr) {
     int k2 = blockIdx.x * blockDim.x + threadIdx.x;          // mode pair index
     const float4 *src = (const float4 *)S;
     int n = n3;
-    double2 *dst = acc;
+    float4 *dst = (float4 *)acc;
     if (k2 >= n3 / 2) {
         k2 -= n3 / 2;
         if (!S2 || k2 >= n2 / 2) return;
         src = (const float4 *)S2;
         n = n2;
-        dst = acc2;
+        dst = (float4 *)acc2;
     }
     const size_t stride = (size_t)n / 2;                     // float4 per term
-    Kahan4 sum;
+    Kahan4 sum(dst[2 * k2], dst[2 * k2 + 1]);
     for (int t0 = 0; t0 < T; t0 += kRedBatch) {
         float4 v[kRedBatch];
         #pragma unroll
@@ -215,13 +225,22 @@ k_reduce(const float2 *__restrict__ S, int T, int n3, double2 *__restrict__ acc,
         for (int i = 0; i < kRedBatch; ++i)
             if (t0 + i < T) sum.add(v[i]);
     }
-    double2 a = dst[2 * k2], b = dst[2 * k2 + 1];
-    a.x += (double)sum.s[0] - (double)sum.c[0];
-    a.y += (double)sum.s[1] - (double)sum.c[1];
-    b.x += (double)sum.s[2] - (double)sum.c[2];
-    b.y += (double)sum.s[3] - (double)sum.c[3];
-    dst[2 * k2] = a;
-    dst[2 * k2 + 1] = b;
+    dst[2 * k2] = make_float4(sum.s[0], sum.s[1], sum.s[2], sum.s[3]);
+    dst[2 * k2 + 1] = make_float4(sum.c[0], sum.c[1], sum.c[2], sum.c[3]);
+}
+
+// In place, after the last chunk: the compensated state of k_reduce to FP64, s - c per component.
+__global__ void k_kahan_fold(double2 *__restrict__ acc, int n, double2 *__restrict__ acc2 = nullptr, int n2 = 0) {
+    int k2 = blockIdx.x * blockDim.x + threadIdx.x;
+    double2 *a = acc;
+    if (k2 >= n / 2) {
+        k2 -= n / 2;
+        if (!acc2 || k2 >= n2 / 2) return;
+        a = acc2;
+    }
+    const float4 s = ((const float4 *)a)[2 * k2], c = ((const float4 *)a)[2 * k2 + 1];
+    a[2 * k2] = make_double2((double)s.x - (double)c.x, (double)s.y - (double)c.y);
+    a[2 * k2 + 1] = make_double2((double)s.z - (double)c.z, (double)s.w - (double)c.w);
 }
 
 __global__ void k_c128_to_c64(const double2 *__restrict__ in, float2 *__restrict__ out, int n) {
@@ -389,6 +408,12 @@ static void plane_fwd(float2 *S, const float2 *alpha, int p0, int T, const float
     else k_plane_fwd<N, PAIR><<<dim3(N / PPC, T), Cfg<N>::THREADS, Cfg<N>::SMEM, st>>>(S, alpha, p0, cpair, Ss, gsc, M);
 }
 
+template <int N, int MODE>
+static void pencil(float2 *S, const float2 *h, float2 *out, int T, cudaStream_t st) {
+    if constexpr (N == 64) pencil64(S, h, out, T, MODE, st);
+    else k_pencil<N, MODE><<<dim3((N * N + 127) / 128, T), 128, 0, st>>>(S, h, out);
+}
+
 // BZ_DATA_REAL: the Hermitian part of the input (sym_input) feeds h and the pair passes; the
 // chunks run over term pairs [p0 / 2, p1 / 2) with the pair table A, the Nyquist sums X are
 // reduced beside V, and Q is symmetrised after the last chunk.
@@ -402,7 +427,7 @@ static bz_status run_chunks_real(Plan &pl, int p0, int p1, cudaStream_t st, int 
     bz_status s = sym_input(pl, pl.src ? pl.src : (const void *)pl.fin, pl.src ? pl.src_dtype : BZ_C64, st);
     if (s != BZ_OK) return s;
     plane_inv<N, false>(pl.fsym, pl.tw, pl.S, 0, 1, 0, st);
-    k_pencil<N, 0><<<dim3((N * N + 127) / 128, 1), 128, 0, st>>>(pl.S, nullptr, pl.h);
+    pencil<N, 0>(pl.S, nullptr, pl.h, 1, st);
     BZ_CUDA_TRY(cudaMemsetAsync(pl.acc, 0, (size_t)n3 * sizeof(double2), st));
     BZ_CUDA_TRY(cudaMemsetAsync(pl.acc_s, 0, (size_t)ns * sizeof(double2), st));
     tm_end(pl, st, TK_OTHER);
@@ -428,7 +453,7 @@ static bz_status run_chunks_real(Plan &pl, int p0, int p1, cudaStream_t st, int 
         plane_inv<N, true>(pl.fsym, pl.tw, S, c0, T, 1, cs);
         tm_end(pl, cs, TK_PLANE_INV);
         tm_begin(pl, cs);
-        k_pencil<N, 2><<<dim3((N * N + 127) / 128, T), 128, 0, cs>>>(S, pl.h, nullptr);
+        pencil<N, 2>(S, pl.h, nullptr, T, cs);
         tm_end(pl, cs, TK_PENCIL);
         tm_begin(pl, cs);
         plane_fwd<N, true>(S, pl.apair, c0, T, pl.cpair, Ss, pl.gsc_cur, pl.M, cs);
@@ -437,6 +462,12 @@ static bz_status run_chunks_real(Plan &pl, int p0, int p1, cudaStream_t st, int 
         k_reduce<<<(n3 / 2 + ns / 2 + 255) / 256, 256, 0, cs>>>(S, T, n3, acc, Ss, ns, acc_s);
         tm_end(pl, cs, TK_REDUCE);
         nl += 4;
+    }
+    for (int ln = 0; ln < lanes; ++ln) {
+        cudaStream_t cs = ln ? pl.xst[ln - 1] : st;
+        k_kahan_fold<<<(n3 / 2 + ns / 2 + 255) / 256, 256, 0, cs>>>(ln ? pl.xacc[ln - 1] : pl.acc, n3,
+                                                                   ln ? pl.xacc_s[ln - 1] : pl.acc_s, ns);
+        ++nl;
     }
     for (int e = 0; e + 1 < lanes; ++e) {
         // the other lanes' sums join the first's in a fixed order
@@ -463,7 +494,7 @@ static bz_status run_chunks(Plan &pl, int p0, int p1, cudaStream_t st, int *laun
     // h = IFFT(fhat): planes without twiddles into S[0], then an inverse-only pencil pass
     tm_begin(pl, st);
     plane_inv<N, false>(pl.fin, pl.tw, pl.S, 0, 1, 0, st);
-    k_pencil<N, 0><<<dim3((N * N + 127) / 128, 1), 128, 0, st>>>(pl.S, nullptr, pl.h);
+    pencil<N, 0>(pl.S, nullptr, pl.h, 1, st);
     BZ_CUDA_TRY(cudaMemsetAsync(pl.acc, 0, (size_t)n3 * sizeof(double2), st));
     tm_end(pl, st, TK_OTHER);
     int nl = 2;
@@ -486,7 +517,7 @@ static bz_status run_chunks(Plan &pl, int p0, int p1, cudaStream_t st, int *laun
         plane_inv<N, false>(pl.fin, pl.tw, S, c0, T, 1, cs);
         tm_end(pl, cs, TK_PLANE_INV);
         tm_begin(pl, cs);
-        k_pencil<N, 1><<<dim3((N * N + 127) / 128, T), 128, 0, cs>>>(S, pl.h, nullptr);
+        pencil<N, 1>(S, pl.h, nullptr, T, cs);
         tm_end(pl, cs, TK_PENCIL);
         tm_begin(pl, cs);
         plane_fwd<N, false>(S, pl.alpha, c0, T, nullptr, nullptr, pl.gsc_cur, pl.M, cs);
@@ -495,6 +526,10 @@ static bz_status run_chunks(Plan &pl, int p0, int p1, cudaStream_t st, int *laun
         k_reduce<<<(n3 / 2 + 255) / 256, 256, 0, cs>>>(S, T, n3, acc);
         tm_end(pl, cs, TK_REDUCE);
         nl += 4;
+    }
+    for (int ln = 0; ln < lanes; ++ln) {
+        k_kahan_fold<<<(n3 / 2 + 255) / 256, 256, 0, ln ? pl.xst[ln - 1] : st>>>(ln ? pl.xacc[ln - 1] : pl.acc, n3);
+        ++nl;
     }
     for (int e = 0; e + 1 < lanes; ++e) {
         BZ_CUDA_TRY(cudaEventRecord(pl.xev_join[e], pl.xst[e]));
@@ -658,6 +693,7 @@ bz_status run_noalloc(const Plan &pl, const void *fhat, void *Qhat, int dtype, u
         k_plane_fwd<N><<<dim3(N / PPC, Tc), Cfg<N>::THREADS, Cfg<N>::SMEM, st>>>(S, pl.alpha, c0);
         k_reduce<<<(n3 / 2 + 255) / 256, 256, 0, st>>>(S, Tc, n3, acc);
     }
+    k_kahan_fold<<<(n3 / 2 + 255) / 256, 256, 0, st>>>(acc, n3);
     if (dtype == BZ_C128) {
         BZ_CUDA_TRY(cudaMemcpyAsync(Qhat, acc, (size_t)n3 * sizeof(double2), cudaMemcpyDeviceToDevice, st));
     } else {

@@ -200,12 +200,14 @@ bz_status launch_mixed(const Plan &pl, const ItemArgs &a, cudaStream_t st);
 // one bounded wait that nothing completes, giving up after `limit` clocks (bz_plan_wait_selftest)
 bz_status wait_selftest(const Plan &pl, long long limit, cudaStream_t st);
 cudaError_t collide_set_attributes(int N);
-// bz_chunk64.cu: the plane passes of the chunked pipeline at N = 64 (radix 8 x 8, one plane per CTA)
+// bz_chunk64.cu: the plane and pencil passes of the chunked pipeline at N = 64 (radix 8 x 8)
 cudaError_t chunk64_set_attributes();
 void plane_inv64(const float2 *fin, const float2 *tw, float2 *S, int p0, int T, int use_tw, bool pair,
                  cudaStream_t st);
 void plane_fwd64(float2 *S, const float2 *alpha, int p0, int T, const float2 *cpair, float2 *Ss, const float *gsc,
                  int M, bool pair, cudaStream_t st);
+// pencil pass (axis 1) over T terms: mode 0 out = IFFT_1(S); 1 S = FFT_1(h . IFFT_1(S)); 2 as 1 with Re h
+void pencil64(float2 *S, const float2 *h, float2 *out, int T, int mode, cudaStream_t st);
 void reduce_parts(const float2 *part, int nblk, int n, double2 *acc, cudaStream_t st);
 int chunk_terms_for(int N);          // after collide_set_attributes(N)
 int supported_N(int N);
