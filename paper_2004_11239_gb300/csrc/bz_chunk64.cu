@@ -217,7 +217,8 @@ k_plane_fwd64(float2 *__restrict__ S, const float2 *__restrict__ alpha, int p0, 
 // (n2 = q, n1 = k2), so the product with h needs no transpose in between.
 //   MODE 0: out = IFFT_1(S)               (forms h)
 //   MODE 1: S = FFT_1(h . IFFT_1(S))      (in place)
-//   MODE 2: as MODE 1 with the real part of h (BZ_DATA_REAL)
+//   MODE 2: as MODE 1 with h real, read as N^3 packed floats (BZ_DATA_REAL)
+//   MODE 3: out = Re IFFT_1(S) as N^3 packed floats (forms the real h of MODE 2)
 constexpr int PL = 32;                 // lines per CTA, one per lane
 constexpr int TP = 256;                // threads per CTA: warp q = n2 in stage 1, k1 in stage 2
 
@@ -248,12 +249,15 @@ k_pencil64(float2 *__restrict__ S, const float2 *__restrict__ h, float2 *__restr
     if constexpr (MODE == 0) {
         #pragma unroll
         for (int k2 = 0; k2 < 8; ++k2) out[(size_t)(q + 8 * k2) * N2 + g] = x[k2];
+    } else if constexpr (MODE == 3) {
+        #pragma unroll
+        for (int k2 = 0; k2 < 8; ++k2) ((float *)out)[(size_t)(q + 8 * k2) * N2 + g] = x[k2].x;
     } else {
         #pragma unroll
         for (int k2 = 0; k2 < 8; ++k2) {
             const size_t j = (size_t)(q + 8 * k2) * N2 + g;
             if constexpr (MODE == 2) {
-                const float hv = h[j].x;
+                const float hv = ((const float *)h)[j];
                 x[k2].x *= hv;
                 x[k2].y *= hv;
             } else {
@@ -300,7 +304,8 @@ void pencil64(float2 *S, const float2 *h, float2 *out, int T, int mode, cudaStre
     const dim3 grid(N64 * N64 / PL, T);
     if (mode == 0) k_pencil64<0><<<grid, TP, 0, st>>>(S, nullptr, out);
     else if (mode == 1) k_pencil64<1><<<grid, TP, 0, st>>>(S, h, nullptr);
-    else k_pencil64<2><<<grid, TP, 0, st>>>(S, h, nullptr);
+    else if (mode == 2) k_pencil64<2><<<grid, TP, 0, st>>>(S, h, nullptr);
+    else k_pencil64<3><<<grid, TP, 0, st>>>(S, nullptr, out);
 }
 
 }  // namespace bz

@@ -200,7 +200,7 @@ struct Kahan4 {
 // (zero bytes are the empty sum), and k_kahan_fold turns them into FP64 once at the end.  The
 // per-chunk pass thus runs no FP64 arithmetic, whose rate on this part is a small fraction of
 // FP32's.  S2 / n2 / acc2 (or null): a second field summed the same way (the Nyquist sums).
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)        // <= 64 registers: a launch at N = 64 fits one wave
 k_reduce(const float2 *__restrict__ S, int T, int n3, double2 *__restrict__ acc,
          const float2 *__restrict__ S2 = nullptr, int n2 = 0, double2 *__restrict__ acc2 = nullptr) {
     int k2 = blockIdx.x * blockDim.x + threadIdx.x;          // mode pair index
@@ -427,7 +427,9 @@ static bz_status run_chunks_real(Plan &pl, int p0, int p1, cudaStream_t st, int 
     bz_status s = sym_input(pl, pl.src ? pl.src : (const void *)pl.fin, pl.src ? pl.src_dtype : BZ_C64, st);
     if (s != BZ_OK) return s;
     plane_inv<N, false>(pl.fsym, pl.tw, pl.S, 0, 1, 0, st);
-    pencil<N, 0>(pl.S, nullptr, pl.h, 1, st);
+    // h is real: at N = 64 it is stored as N^3 packed floats (half the bytes the pair pencils read)
+    if constexpr (N == 64) pencil64(pl.S, nullptr, pl.h, 1, 3, st);
+    else pencil<N, 0>(pl.S, nullptr, pl.h, 1, st);
     BZ_CUDA_TRY(cudaMemsetAsync(pl.acc, 0, (size_t)n3 * sizeof(double2), st));
     BZ_CUDA_TRY(cudaMemsetAsync(pl.acc_s, 0, (size_t)ns * sizeof(double2), st));
     tm_end(pl, st, TK_OTHER);

@@ -206,7 +206,8 @@ void plane_inv64(const float2 *fin, const float2 *tw, float2 *S, int p0, int T, 
                  cudaStream_t st);
 void plane_fwd64(float2 *S, const float2 *alpha, int p0, int T, const float2 *cpair, float2 *Ss, const float *gsc,
                  int M, bool pair, cudaStream_t st);
-// pencil pass (axis 1) over T terms: mode 0 out = IFFT_1(S); 1 S = FFT_1(h . IFFT_1(S)); 2 as 1 with Re h
+// pencil pass (axis 1) over T terms: mode 0 out = IFFT_1(S); 1 S = FFT_1(h . IFFT_1(S)); 2 as 1 with
+// h real (N^3 packed floats); 3 out = Re IFFT_1(S) as N^3 packed floats
 void pencil64(float2 *S, const float2 *h, float2 *out, int T, int mode, cudaStream_t st);
 void reduce_parts(const float2 *part, int nblk, int n, double2 *acc, cudaStream_t st);
 int chunk_terms_for(int N);          // after collide_set_attributes(N)
