@@ -63,7 +63,8 @@ struct Plan {
     float2 *S = nullptr;            // [chunk][N^3]
     float2 *h = nullptr;            // [N^3]
     float2 *fin = nullptr;          // [N^3] FP32 input
-    double2 *acc = nullptr;         // [N^3] FP64 accumulator
+    double2 *acc = nullptr;         // [N^3] FP64 accumulator (while a chunked collide runs, the same
+                                    // bytes hold k_reduce's compensated FP32 state: s, c per mode pair)
     double2 *rk = nullptr;          // [3][N^3] RK4 state (f0, fsum) + spare
     double *mom = nullptr;          // moments scratch
     // fused cluster pipeline (N <= 32)
